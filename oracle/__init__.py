@@ -1,0 +1,305 @@
+"""FP64 CPU oracle for the cone-beam CT hot path -- TEST INFRASTRUCTURE ONLY.
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  It shares no code with the CUDA
+library (``paper_1905_03748_gb300``) and never imports it.
+
+Operators (``oracle.c``, plain C, FP64, OpenMP over independent rays/voxels):
+    forward, forward_rays          interpolated ray-driven projector (Sec. 2.1)
+    backward, backward_voxels      voxel-driven BP, FDK / matched weights (Sec. 2.2)
+    adjoint, adjoint_voxels        exact transpose of the projector
+    tv_value, tv_grad, tv_steps    gradient-descent TV (Sec. 2.3)
+Solvers (this file, numpy FP64, written as the textbook iterations):
+    sirt, os_sart (with optional TV after each iteration), cgls.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+BP_MATCHED = 0
+BP_FDK = 1
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into liboracle.so next to it (gcc, -O2, OpenMP)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-std=c99",
+                               _SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB)
+            P = ctypes.c_void_p
+            I = ctypes.c_int64
+            sig = {
+                "oracle_forward": [P, P, I, P, P],
+                "oracle_forward_rays": [P, P, P, P, I, P],
+                "oracle_sample_count": [P, P, I],
+                "oracle_ray_params": [P, P, P, I, P],
+                "oracle_backward": [P, P, I, P, P, ctypes.c_int],
+                "oracle_backward_voxels": [P, P, I, P, P, I, P, ctypes.c_int],
+                "oracle_adjoint": [P, P, I, P, P],
+                "oracle_adjoint_voxels": [P, P, I, P, P, I, P],
+                "oracle_tv_value": [P, I, I, I, ctypes.c_double],
+                "oracle_tv_grad": [P, I, I, I, ctypes.c_double, P],
+                "oracle_tv_grad_voxels": [P, I, I, I, ctypes.c_double, P, I, P],
+                "oracle_tv_steps": [P, I, I, I, ctypes.c_int, ctypes.c_double, ctypes.c_double],
+            }
+            for name, args in sig.items():
+                f = getattr(lib, name)
+                f.argtypes = args
+                f.restype = None
+            lib.oracle_sample_count.restype = ctypes.c_int64
+            lib.oracle_tv_value.restype = ctypes.c_double
+            _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _geo_array(geo: dict) -> np.ndarray:
+    return np.array([geo["DSO"], geo["DSD"], *geo["n_voxel"], *geo["d_voxel"],
+                     *geo["off_origin"], *geo["n_det"], *geo["d_det"], *geo["off_det"],
+                     geo["accuracy"]], dtype=np.float64)
+
+
+def _shapes(geo):
+    nx, ny, nz = geo["n_voxel"]
+    nu, nv = geo["n_det"]
+    return (nz, ny, nx), (nv, nu)
+
+
+# ----------------------------------------------------------------- operators
+
+def forward(geo: dict, angles, vol) -> np.ndarray:
+    """A x: proj (A, nv, nu) from vol (nz, ny, nx)."""
+    lib = _load()
+    vshape, dshape = _shapes(geo)
+    ang = _f64(angles)
+    v = _f64(vol).reshape(vshape)
+    out = np.empty((len(ang),) + dshape, dtype=np.float64)
+    lib.oracle_forward(_ptr(_geo_array(geo)), _ptr(ang), len(ang), _ptr(v), _ptr(out))
+    return out
+
+
+def forward_rays(geo: dict, angles, vol, rays) -> np.ndarray:
+    """A x at selected rays given as (a, q, p) rows."""
+    lib = _load()
+    vshape, _ = _shapes(geo)
+    v = _f64(vol).reshape(vshape)
+    idx = np.ascontiguousarray(rays, dtype=np.int64)
+    out = np.empty(len(idx), dtype=np.float64)
+    lib.oracle_forward_rays(_ptr(_geo_array(geo)), _ptr(_f64(angles)), _ptr(v), _ptr(idx),
+                            len(idx), _ptr(out))
+    return out
+
+
+def sample_count(geo: dict, angles) -> int:
+    """Total quadrature samples of one forward projection (sum of K)."""
+    ang = _f64(angles)
+    return int(_load().oracle_sample_count(_ptr(_geo_array(geo)), _ptr(ang), len(ang)))
+
+
+def ray_params(geo: dict, angles, rays) -> np.ndarray:
+    """(K, len_mm, t_in, t_out) per selected ray; zeros for rays that miss."""
+    idx = np.ascontiguousarray(rays, dtype=np.int64)
+    out = np.empty((len(idx), 4), dtype=np.float64)
+    _load().oracle_ray_params(_ptr(_geo_array(geo)), _ptr(_f64(angles)), _ptr(idx), len(idx),
+                              _ptr(out))
+    return out
+
+
+def backward(geo: dict, angles, proj, mode: int = BP_MATCHED) -> np.ndarray:
+    """Voxel-driven weighted backprojection (mode BP_MATCHED or BP_FDK)."""
+    lib = _load()
+    vshape, dshape = _shapes(geo)
+    ang = _f64(angles)
+    p = _f64(proj).reshape((len(ang),) + dshape)
+    out = np.empty(vshape, dtype=np.float64)
+    lib.oracle_backward(_ptr(_geo_array(geo)), _ptr(ang), len(ang), _ptr(p), _ptr(out), int(mode))
+    return out
+
+
+def backward_voxels(geo: dict, angles, proj, voxels, mode: int = BP_MATCHED) -> np.ndarray:
+    """Backprojection at selected voxels given as (i, j, k) rows."""
+    lib = _load()
+    _, dshape = _shapes(geo)
+    ang = _f64(angles)
+    p = _f64(proj).reshape((len(ang),) + dshape)
+    idx = np.ascontiguousarray(voxels, dtype=np.int64)
+    out = np.empty(len(idx), dtype=np.float64)
+    lib.oracle_backward_voxels(_ptr(_geo_array(geo)), _ptr(ang), len(ang), _ptr(p), _ptr(idx),
+                               len(idx), _ptr(out), int(mode))
+    return out
+
+
+def adjoint(geo: dict, angles, proj) -> np.ndarray:
+    """Exact transpose of forward (serial scatter)."""
+    lib = _load()
+    vshape, dshape = _shapes(geo)
+    ang = _f64(angles)
+    p = _f64(proj).reshape((len(ang),) + dshape)
+    out = np.empty(vshape, dtype=np.float64)
+    lib.oracle_adjoint(_ptr(_geo_array(geo)), _ptr(ang), len(ang), _ptr(p), _ptr(out))
+    return out
+
+
+def adjoint_voxels(geo: dict, angles, proj, voxels) -> np.ndarray:
+    """Exact transpose of forward evaluated at selected voxels."""
+    lib = _load()
+    _, dshape = _shapes(geo)
+    ang = _f64(angles)
+    p = _f64(proj).reshape((len(ang),) + dshape)
+    idx = np.ascontiguousarray(voxels, dtype=np.int64)
+    out = np.empty(len(idx), dtype=np.float64)
+    lib.oracle_adjoint_voxels(_ptr(_geo_array(geo)), _ptr(ang), len(ang), _ptr(p), _ptr(idx),
+                              len(idx), _ptr(out))
+    return out
+
+
+def tv_value(vol, eps: float) -> float:
+    v = _f64(vol)
+    nz, ny, nx = v.shape
+    return float(_load().oracle_tv_value(_ptr(v), nx, ny, nz, float(eps)))
+
+
+def tv_grad(vol, eps: float) -> np.ndarray:
+    v = _f64(vol)
+    nz, ny, nx = v.shape
+    g = np.empty_like(v)
+    _load().oracle_tv_grad(_ptr(v), nx, ny, nz, float(eps), _ptr(g))
+    return g
+
+
+def tv_grad_voxels(vol, eps: float, voxels) -> np.ndarray:
+    v = _f64(vol)
+    nz, ny, nx = v.shape
+    idx = np.ascontiguousarray(voxels, dtype=np.int64)
+    out = np.empty(len(idx), dtype=np.float64)
+    _load().oracle_tv_grad_voxels(_ptr(v), nx, ny, nz, float(eps), _ptr(idx), len(idx), _ptr(out))
+    return out
+
+
+def tv_steps(vol, n_steps: int, alpha: float, eps: float) -> np.ndarray:
+    """n_steps of x <- x - alpha g/||g|| (Sec. 2.3 gradient descent)."""
+    v = _f64(vol).copy()
+    nz, ny, nx = v.shape
+    _load().oracle_tv_steps(_ptr(v), nx, ny, nz, int(n_steps), float(alpha), float(eps))
+    return v
+
+
+# ------------------------------------------------------------------- solvers
+
+def _guarded_reciprocal(a: np.ndarray, floor: float = 1e-12) -> np.ndarray:
+    out = np.zeros_like(a)
+    np.divide(1.0, a, out=out, where=a > floor)
+    return out
+
+
+def sirt(geo, angles, b, n_iter, lam=1.0, nonneg=False, x0=None, mode=BP_MATCHED):
+    """SIRT: x <- x + lam V A^T W (b - A x), W = 1/(A 1), V = 1/(A^T 1).
+
+    Returns (x, resid) with resid[k] = ||b - A x_k||_2 before update k.
+    """
+    vshape, _ = _shapes(geo)
+    b = _f64(b)
+    x = np.zeros(vshape) if x0 is None else _f64(x0).reshape(vshape).copy()
+    W = _guarded_reciprocal(forward(geo, angles, np.ones(vshape)))
+    V = _guarded_reciprocal(backward(geo, angles, np.ones(b.shape), mode))
+    resid = []
+    for _ in range(n_iter):
+        r = b - forward(geo, angles, x)
+        resid.append(float(np.linalg.norm(r)))
+        x = x + lam * V * backward(geo, angles, W * r, mode)
+        if nonneg:
+            x = np.maximum(x, 0.0)
+    return x, np.array(resid)
+
+
+def os_sart(geo, angles, b, n_iter, subset=20, lam=1.0, nonneg=False, x0=None,
+            tv_steps_n=0, tv_alpha=0.002, tv_eps=1e-8, mode=BP_MATCHED):
+    """OS-SART over contiguous subsets of `subset` angles, visited in order;
+    optional gradient-descent TV after each full iteration with step
+    alpha * ||x_after_data - x_before_data||_2.
+
+    Returns (x, resid) with resid[k] = sqrt(sum_s ||b_s - A_s x||^2) over the
+    subset residuals computed during iteration k.
+    """
+    vshape, _ = _shapes(geo)
+    ang = _f64(angles)
+    b = _f64(b)
+    x = np.zeros(vshape) if x0 is None else _f64(x0).reshape(vshape).copy()
+    blocks = [np.arange(s, min(s + subset, len(ang))) for s in range(0, len(ang), subset)]
+    Ws, Vs = [], []
+    for blk in blocks:
+        Ws.append(_guarded_reciprocal(forward(geo, ang[blk], np.ones(vshape))))
+        Vs.append(_guarded_reciprocal(backward(geo, ang[blk], np.ones((len(blk),) + b.shape[1:]),
+                                               mode)))
+    resid = []
+    for _ in range(n_iter):
+        x_prev = x.copy()
+        rr = 0.0
+        for blk, W, V in zip(blocks, Ws, Vs):
+            r = b[blk] - forward(geo, ang[blk], x)
+            rr += float(np.sum(r * r))
+            x = x + lam * V * backward(geo, ang[blk], W * r, mode)
+            if nonneg:
+                x = np.maximum(x, 0.0)
+        resid.append(np.sqrt(rr))
+        if tv_steps_n > 0:
+            step = tv_alpha * float(np.linalg.norm(x - x_prev))
+            x = tv_steps(x, tv_steps_n, step, tv_eps)
+    return x, np.array(resid)
+
+
+def cgls(geo, angles, b, n_iter, x0=None, bp="matched"):
+    """CGLS (conjugate gradients on A^T A x = A^T b), FP64 scalars.
+
+    bp = "matched" (voxel-driven pseudo-matched backprojector) or "adjoint"
+    (exact transpose).  Returns (x, resid) with resid[k] = ||r_k||_2 after
+    iteration k.
+    """
+    vshape, _ = _shapes(geo)
+    b = _f64(b)
+    At = (lambda y: adjoint(geo, angles, y)) if bp == "adjoint" else \
+        (lambda y: backward(geo, angles, y, BP_MATCHED))
+    x = np.zeros(vshape) if x0 is None else _f64(x0).reshape(vshape).copy()
+    r = b - forward(geo, angles, x) if x0 is not None else b.copy()
+    p = At(r)
+    gamma = float(np.sum(p * p))
+    resid = []
+    for _ in range(n_iter):
+        q = forward(geo, angles, p)
+        alpha = gamma / float(np.sum(q * q))
+        x = x + alpha * p
+        r = r - alpha * q
+        resid.append(float(np.linalg.norm(r)))
+        s = At(r)
+        gamma_new = float(np.sum(s * s))
+        p = s + (gamma_new / gamma) * p
+        gamma = gamma_new
+    return x, np.array(resid)

@@ -1,0 +1,375 @@
+"""Pins of the FP64 oracle against results fixed by the mathematics.
+
+Every test here runs on the CPU and touches only ``oracle`` and the
+independent computations in ``pins``; none uses the CUDA library.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1905_03748_gb300 import synth
+from tests import pins
+
+
+def tiny_geo(nx=10, ny=9, nz=8, nu=15, nv=11, d=(1.0, 1.1, 0.9), du=(1.3, 1.2),
+             off_origin=(0.3, -0.2, 0.4), off_det=(0.7, -0.5), accuracy=0.5):
+    """Anisotropic, offset, non-square geometry: index mix-ups show up here."""
+    return synth.geometry((nx, ny, nz), d, (nu, nv), du, dso=60.0, dsd=95.0,
+                          off_origin=off_origin, off_det=off_det, accuracy=accuracy)
+
+
+# ------------------------------------------------------------ forward Ax
+
+@pytest.mark.parametrize("n", [7, 8, 16])
+def test_constant_volume_central_ray_is_exact(n):
+    """A constant volume c and the central ray (odd detector, theta = 0 and
+    90 deg): the interpolant ramps linearly over the outer half-voxels, so the
+    line integral is c * n * d, and midpoint quadrature with the kinks on
+    its grid reproduces it exactly."""
+    c = 0.37
+    geo = synth.geometry(n, 1.25, 9, 1.0, dso=50.0, dsd=80.0)
+    vol = np.full((n, n, n), c)
+    ang = np.array([0.0, math.pi / 2, math.pi])
+    proj = oracle.forward(geo, ang, vol)
+    for a in range(3):
+        assert proj[a, 4, 4] == pytest.approx(c * n * 1.25, rel=1e-12)
+
+
+def test_midpoint_converges_to_exact_integral_second_order():
+    """Ax(h) -> the exact integral of the trilinear interpolant (computed by
+    splitting at voxel planes + Gauss-Legendre), with error O(h^2)."""
+    geo = tiny_geo()
+    rng = np.random.default_rng(0)
+    vol = rng.random((8, 9, 10))
+    ang = np.array([0.3, 1.9, 4.0])
+    rays = [(a, q, p) for a in range(3) for q in (1, 5, 9) for p in (2, 6, 7, 12)]
+    exact = np.array([pins.exact_ray_integral(geo, vol, ang[a], p, q) for a, q, p in rays])
+    assert np.count_nonzero(exact) > len(rays) // 2
+    errs = []
+    for acc in (0.2, 0.1, 0.05):
+        g = dict(geo, accuracy=acc)
+        approx = oracle.forward_rays(g, ang, vol, np.array(rays))
+        errs.append(np.linalg.norm(approx - exact) / np.linalg.norm(exact))
+    assert errs[0] < 2e-3
+    for e0, e1 in zip(errs, errs[1:]):
+        assert 2.5 < e0 / e1 < 6.0, errs
+    fine = oracle.forward_rays(dict(geo, accuracy=0.002), ang, vol, np.array(rays))
+    assert np.linalg.norm(fine - exact) / np.linalg.norm(exact) < 1e-5
+
+
+def test_brute_force_fine_sampling_8cubed():
+    """8^3 volume, every ray of two angles: oracle at 1e-3 voxel steps equals
+    the exact integral of the interpolant."""
+    geo = synth.geometry(8, 1.0, (12, 10), 1.1, dso=40.0, dsd=70.0, accuracy=0.001)
+    vol = np.random.default_rng(3).random((8, 8, 8))
+    ang = np.array([0.4, 2.2])
+    proj = oracle.forward(geo, ang, vol)
+    exact = np.array([[[pins.exact_ray_integral(geo, vol, ang[a], p, q) for p in range(12)]
+                       for q in range(10)] for a in range(2)])
+    assert np.abs(proj - exact).max() <= 1e-6 * np.abs(exact).max()
+
+
+def test_rotation_by_90_degrees_is_a_transpose():
+    """Projecting at theta + 90 deg the volume rotated by +90 deg about z
+    equals projecting the original at theta."""
+    n = 12
+    geo = synth.geometry((n, n, 7), (0.8, 0.8, 1.1), (17, 9), (1.0, 1.2), dso=45.0, dsd=70.0,
+                         off_det=(0.3, 0.2))
+    vol = np.random.default_rng(1).random((7, n, n))
+    rot = vol[:, ::-1, :].transpose(0, 2, 1)
+    th = np.array([0.25, 1.0, 2.5])
+    a = oracle.forward(geo, th, vol)
+    b = oracle.forward(geo, th + math.pi / 2, rot)
+    np.testing.assert_allclose(b, a, rtol=1e-9, atol=1e-12)
+
+
+@pytest.mark.parametrize("theta", [0.0, math.pi / 2, 0.9, 3.7])
+def test_single_voxel_lands_where_the_frame_says(theta):
+    """A lone voxel projects around the detector point that the
+    source->voxel line meets: the centroid of its footprint, sampled by
+    pixels 8x finer than the footprint, sits within 0.02 px of it (perspective
+    and pixel sampling move it by less than 0.01 px here)."""
+    geo = tiny_geo(nx=16, ny=16, nz=12, nu=161, nv=121, d=(1.0, 1.0, 1.0), du=(0.225, 0.225))
+    vol = np.zeros((12, 16, 16))
+    i, j, k = 11, 4, 8
+    vol[k, j, i] = 1.0
+    proj = oracle.forward(dict(geo, accuracy=0.05), np.array([theta]), vol)[0]
+    q_idx, p_idx = np.mgrid[0:121, 0:161]
+    m = proj.sum()
+    pc, qc = (proj * p_idx).sum() / m, (proj * q_idx).sum() / m
+    p, q, _ = pins.detector_hit(geo, theta, pins.voxel_centre(geo, i, j, k))
+    assert abs(pc - p) < 0.02 and abs(qc - q) < 0.02
+    # a mirrored frame (e_u flipped) would put it 2|p - centre| px away
+    assert abs(p - 80.0 - geo["off_det"][0] / 0.225) > 2.0
+
+
+def test_voxelised_ellipsoids_converge_to_analytic_chords():
+    """Ax of the point-sampled phantom approaches sum(density x chord) as the
+    grid refines (same phantom in mm)."""
+    fov = 64.0
+    rng = np.random.default_rng(7)
+    ells = []
+    for _ in range(3):
+        ells.append(synth.Ellipsoid(tuple(rng.uniform(-8, 8, 3)), tuple(rng.uniform(6, 14, 3)),
+                                    synth._random_rotation(rng), float(rng.uniform(0.2, 1.0))))
+    ang = np.array([0.2, 1.3, 2.9])
+    errs = []
+    for n in (16, 32, 64):
+        d = fov / n
+        geo = synth.geometry(n, d, (24, 20), 3.0, dso=200.0, dsd=300.0)
+        vol = synth.voxelize(ells, (n, n, n), (d, d, d), dtype=np.float64)
+        proj = oracle.forward(geo, ang, vol)
+        ref = np.zeros_like(proj)
+        for a, th in enumerate(ang):
+            S = pins.frame(geo, th)[0]
+            for q in range(20):
+                for p in range(24):
+                    P = pins.pixel_centre(geo, th, p, q)
+                    ref[a, q, p] = sum(e.density * pins.ellipsoid_chord(S, P, e.centre, e.axes,
+                                                                        e.rot) for e in ells)
+        errs.append(np.linalg.norm(proj - ref) / np.linalg.norm(ref))
+    # boundary voxelisation error shrinks about linearly with the voxel size
+    assert errs[0] > errs[1] > errs[2]
+    assert errs[0] / errs[2] > 2.5 and errs[2] < 0.05, errs
+
+
+# -------------------------------------------------------- exact adjoint
+
+def test_exact_adjoint_dot_product():
+    """<A x, y> = <x, A^T y> to rounding."""
+    geo = tiny_geo()
+    rng = np.random.default_rng(11)
+    ang = np.array([0.1, 0.9, 2.0, 3.3, 5.5])
+    x = rng.random((8, 9, 10))
+    y = rng.random((5, 11, 15))
+    lhs = np.sum(oracle.forward(geo, ang, x) * y)
+    rhs = np.sum(x * oracle.adjoint(geo, ang, y))
+    assert lhs == pytest.approx(rhs, rel=1e-12)
+
+
+def test_exact_adjoint_equals_dense_transpose():
+    """A^T y equals the transpose of the matrix built column by column from
+    Ax applied to unit vectors."""
+    geo = tiny_geo(nx=4, ny=3, nz=3, nu=6, nv=5)
+    ang = np.array([0.2, 1.7, 4.1])
+    N = 4 * 3 * 3
+    A = np.stack([oracle.forward(geo, ang, np.eye(N)[c].reshape(3, 3, 4)).ravel()
+                  for c in range(N)], axis=1)
+    y = np.random.default_rng(2).random(A.shape[0])
+    np.testing.assert_allclose(oracle.adjoint(geo, ang, y.reshape(3, 5, 6)).ravel(), A.T @ y,
+                               rtol=1e-12, atol=1e-14)
+
+
+def test_adjoint_at_selected_voxels_matches_full_scatter():
+    geo = tiny_geo()
+    ang = np.array([0.1, 2.0, 4.4])
+    y = np.random.default_rng(5).random((3, 11, 15))
+    full = oracle.adjoint(geo, ang, y)
+    vox = synth.random_voxels(10, 9, 8, 40, seed=9)
+    sel = oracle.adjoint_voxels(geo, ang, y, vox)
+    np.testing.assert_allclose(sel, full[vox[:, 2], vox[:, 1], vox[:, 0]], rtol=1e-12,
+                               atol=1e-14)
+
+
+# ------------------------------------------------------ backprojection
+
+@pytest.mark.parametrize("theta", [0.0, 0.7, 2.9])
+def test_fdk_backprojection_of_one_pixel(theta):
+    """Backprojecting an image that is 1 at pixel (p0, q0): each voxel gets
+    w_FDK * tent(p - p0) * tent(q - q0), with (p, q) the detector hit of the
+    source->voxel line (plane intersection) and w = (DSO/depth)^2."""
+    geo = tiny_geo(nx=12, ny=12, nz=10, nu=21, nv=17, du=(0.8, 0.8))
+    img = np.zeros((1, 17, 21))
+    p0, q0 = 10, 9
+    img[0, q0, p0] = 1.0
+    bp = oracle.backward(geo, np.array([theta]), img, oracle.BP_FDK)
+    ref = np.zeros_like(bp)
+    for k in range(10):
+        for j in range(12):
+            for i in range(12):
+                p, q, depth = pins.detector_hit(geo, theta, pins.voxel_centre(geo, i, j, k))
+                tent = max(0.0, 1 - abs(p - p0)) * max(0.0, 1 - abs(q - q0))
+                ref[k, j, i] = (geo["DSO"] / depth) ** 2 * tent
+    assert np.count_nonzero(ref) > 10
+    np.testing.assert_allclose(bp, ref, rtol=1e-10, atol=1e-13)
+
+
+def test_fdk_backprojection_of_ones_at_isocentre():
+    """The isocentre voxel projects to the detector centre with weight 1 at
+    every angle, so backprojecting ones gives the number of angles."""
+    geo = synth.geometry(9, 1.0, 15, 1.0, dso=50.0, dsd=80.0)
+    ang = synth.angles(13)
+    bp = oracle.backward(geo, ang, np.ones((13, 15, 15)), oracle.BP_FDK)
+    assert bp[4, 4, 4] == pytest.approx(13.0, rel=1e-13)
+
+
+def test_matched_backprojection_approximates_exact_adjoint():
+    """The pseudo-matched weights make the voxel-driven BP approximate the
+    transpose of the ray-driven projector: on smooth data the two agree to a
+    few percent inside the field of view (the weights' derivation: voxel
+    volume over the ray tube's cross-section at the voxel)."""
+    n = 24
+    geo = synth.geometry(n, 1.0, 48, 0.75, dso=100.0, dsd=150.0)
+    ang = synth.angles(24)
+    q_idx, p_idx = np.mgrid[0:48, 0:48]
+    y = np.stack([1.0 + 0.3 * np.sin(0.07 * p_idx + 0.05 * q_idx + a) for a in range(24)])
+    m = oracle.backward(geo, ang, y, oracle.BP_MATCHED)
+    e = oracle.adjoint(geo, ang, y)
+    core = (slice(4, n - 4),) * 3
+    rel = np.linalg.norm(m[core] - e[core]) / np.linalg.norm(e[core])
+    assert rel < 0.03, rel
+    # the FDK-weighted BP is a different operator (no voxel-volume factor)
+    f = oracle.backward(geo, ang, y, oracle.BP_FDK)
+    assert np.linalg.norm(f[core] - e[core]) / np.linalg.norm(e[core]) > 0.2
+
+
+def test_backprojection_at_selected_voxels_matches_full():
+    geo = tiny_geo()
+    ang = np.array([0.3, 1.1, 5.0])
+    y = np.random.default_rng(4).random((3, 11, 15))
+    vox = synth.random_voxels(10, 9, 8, 30, seed=1)
+    for mode in (oracle.BP_MATCHED, oracle.BP_FDK):
+        full = oracle.backward(geo, ang, y, mode)
+        sel = oracle.backward_voxels(geo, ang, y, vox, mode)
+        np.testing.assert_allclose(sel, full[vox[:, 2], vox[:, 1], vox[:, 0]], rtol=1e-14)
+
+
+def test_forward_at_selected_rays_matches_full():
+    geo = tiny_geo()
+    ang = np.array([0.3, 1.1, 5.0])
+    vol = np.random.default_rng(4).random((8, 9, 10))
+    full = oracle.forward(geo, ang, vol)
+    rays = synth.random_rays(3, 11, 15, 50, seed=2)
+    np.testing.assert_allclose(oracle.forward_rays(geo, ang, vol, rays),
+                               full[rays[:, 0], rays[:, 1], rays[:, 2]], rtol=1e-14)
+
+
+# ------------------------------------------------------------------ TV
+
+def tv_numpy(f, eps):
+    """TV_eps by array differencing (independent of the oracle's loops)."""
+    dx = np.diff(f, axis=2, prepend=f[:, :, :1])
+    dy = np.diff(f, axis=1, prepend=f[:, :1, :])
+    dz = np.diff(f, axis=0, prepend=f[:1, :, :])
+    return float(np.sum(np.sqrt(dx * dx + dy * dy + dz * dz + eps)))
+
+
+def test_tv_value_matches_array_differencing():
+    f = np.random.default_rng(0).random((5, 6, 7))
+    assert oracle.tv_value(f, 1e-3) == pytest.approx(tv_numpy(f, 1e-3), rel=1e-13)
+
+
+def test_tv_gradient_matches_central_differences():
+    f = np.random.default_rng(1).random((5, 6, 7))
+    eps = 1e-2
+    g = oracle.tv_grad(f, eps)
+    h = 1e-6
+    fd = np.empty_like(f)
+    for idx in np.ndindex(f.shape):
+        fp = f.copy()
+        fm = f.copy()
+        fp[idx] += h
+        fm[idx] -= h
+        fd[idx] = (tv_numpy(fp, eps) - tv_numpy(fm, eps)) / (2 * h)
+    np.testing.assert_allclose(g, fd, rtol=1e-6, atol=1e-7)
+
+
+def test_tv_gradient_zero_on_constant_and_steps_decrease_tv():
+    c = np.full((4, 5, 6), 0.3)
+    assert np.abs(oracle.tv_grad(c, 1e-8)).max() == 0.0
+    assert np.array_equal(oracle.tv_steps(c, 3, 0.1, 1e-8), c)
+    f = np.random.default_rng(2).random((6, 6, 6))
+    tv0 = oracle.tv_value(f, 1e-8)
+    f1 = oracle.tv_steps(f, 5, 0.05, 1e-8)
+    assert oracle.tv_value(f1, 1e-8) < tv0
+
+
+def test_tv_gradient_at_selected_voxels():
+    f = np.random.default_rng(3).random((6, 7, 8))
+    g = oracle.tv_grad(f, 1e-4)
+    vox = synth.random_voxels(8, 7, 6, 25, seed=3)
+    np.testing.assert_allclose(oracle.tv_grad_voxels(f, 1e-4, vox),
+                               g[vox[:, 2], vox[:, 1], vox[:, 0]], rtol=1e-14)
+
+
+# -------------------------------------------------------------- solvers
+
+def dense_operators(geo, ang):
+    nx, ny, nz = geo["n_voxel"]
+    nu, nv = geo["n_det"]
+    N, M = nx * ny * nz, len(ang) * nu * nv
+    A = np.stack([oracle.forward(geo, ang, np.eye(N)[c].reshape(nz, ny, nx)).ravel()
+                  for c in range(N)], axis=1)
+    Bm = np.stack([oracle.backward(geo, ang, np.eye(M)[c].reshape(len(ang), nv, nu)).ravel()
+                   for c in range(M)], axis=1)
+    return A, Bm
+
+
+def test_sirt_equals_dense_iteration():
+    geo = tiny_geo(nx=4, ny=4, nz=3, nu=6, nv=5)
+    ang = synth.angles(5)
+    A, Bm = dense_operators(geo, ang)
+    b = A @ np.random.default_rng(0).random(A.shape[1])
+    row, col = A @ np.ones(A.shape[1]), Bm @ np.ones(A.shape[0])
+    assert np.any(row == 0.0)           # some rays miss: the zero guard matters
+    W = np.where(row > 1e-12, 1.0 / np.where(row > 1e-12, row, 1.0), 0.0)
+    V = np.where(col > 1e-12, 1.0 / np.where(col > 1e-12, col, 1.0), 0.0)
+    x = np.zeros(A.shape[1])
+    for _ in range(6):
+        x = x + V * (Bm @ (W * (b - A @ x)))
+    xo, res = oracle.sirt(geo, ang, b.reshape(5, 5, 6), 6)
+    np.testing.assert_allclose(xo.ravel(), x, rtol=1e-11, atol=1e-13)
+    assert np.all(np.diff(res) < 0)
+
+
+def test_os_sart_with_one_subset_is_sirt():
+    geo = tiny_geo(nx=5, ny=4, nz=3, nu=7, nv=5)
+    ang = synth.angles(6)
+    vol = np.random.default_rng(1).random((3, 4, 5))
+    b = oracle.forward(geo, ang, vol)
+    x1, r1 = oracle.sirt(geo, ang, b, 4)
+    x2, r2 = oracle.os_sart(geo, ang, b, 4, subset=6)
+    np.testing.assert_allclose(x2, x1, rtol=1e-13, atol=1e-14)
+    np.testing.assert_allclose(r2, r1, rtol=1e-13)
+
+
+def test_os_sart_subsets_reduce_error_on_noiseless_data():
+    geo = synth.geometry(12, 1.0, 20, 1.0, dso=60.0, dsd=90.0)
+    ang = synth.angles(20)
+    truth = synth.voxelize(synth.random_ellipsoids(12, 1.0, 4, seed=5, r_vox=(100, 200)),
+                           (12, 12, 12), (1.0, 1.0, 1.0), dtype=np.float64)
+    b = oracle.forward(geo, ang, truth)
+    errs = []
+    for it in (1, 3, 6):
+        x, _ = oracle.os_sart(geo, ang, b, it, subset=5)
+        errs.append(np.linalg.norm(x - truth))
+    assert errs[0] > errs[1] > errs[2]
+
+
+def test_cgls_with_exact_adjoint_reaches_least_squares():
+    """With the exact transpose, CGLS is CG on the normal equations: the
+    residual norm decreases monotonically and it reaches lstsq."""
+    geo = tiny_geo(nx=3, ny=3, nz=2, nu=6, nv=4)
+    ang = synth.angles(4)
+    A, _ = dense_operators(geo, ang)
+    rng = np.random.default_rng(6)
+    b = A @ rng.random(A.shape[1]) + 0.01 * rng.standard_normal(A.shape[0])
+    x_ls = np.linalg.lstsq(A, b, rcond=None)[0]
+    x, res = oracle.cgls(geo, ang, b.reshape(4, 4, 6), 40, bp="adjoint")
+    assert np.all(np.diff(res) <= 1e-12 * res[0])
+    np.testing.assert_allclose(x.ravel(), x_ls, rtol=1e-6, atol=1e-8)
+    # textbook CG on A^T A x = A^T b from zero: same first iterates
+    xc = np.zeros(A.shape[1])
+    r = A.T @ b
+    pdir = r.copy()
+    for _ in range(3):
+        Ap = A.T @ (A @ pdir)
+        al = (r @ r) / (pdir @ Ap)
+        xc = xc + al * pdir
+        rn = r - al * Ap
+        pdir = rn + (rn @ rn) / (r @ r) * pdir
+        r = rn
+    x3, _ = oracle.cgls(geo, ang, b.reshape(4, 4, 6), 3, bp="adjoint")
+    np.testing.assert_allclose(x3.ravel(), xc, rtol=1e-9, atol=1e-12)
