@@ -1,0 +1,184 @@
+/*
+ * tigre103.h -- C ABI of the GB300 (sm_103a) cone-beam CT library.
+ *
+ * The operators of iterative cone-beam CT (paper Eq. 1: A x = b + e, with A
+ * the ray/element intersection operator; every iterative method applies A
+ * and A^T at least once per iteration, Sec. 2):
+ *
+ *   tigre_forward   interpolated ray-driven forward projection  A x  (Sec. 2.1)
+ *   tigre_backward  voxel-driven weighted backprojection A^T y (Sec. 2.2),
+ *                   FDK or pseudo-matched weights, or the exact transpose of
+ *                   tigre_forward
+ *   tigre_tv_step   gradient-descent total-variation steps (Sec. 2.3)
+ *   tigre_sirt / tigre_sart / tigre_cgls
+ *                   SIRT, OS-SART (+TV), CGLS drivers (Sec. 3.2 uses CGLS
+ *                   and OS-SART) with every iterate resident on the device
+ *
+ * Conventions (all lengths mm, angles rad):
+ *   volume  vol[k][j][i], shape (nz, ny, nx), x fastest, contiguous;
+ *           voxel centre X = ((i-(nx-1)/2) dx, (j-(ny-1)/2) dy,
+ *                             (k-(nz-1)/2) dz) + off_origin
+ *   orbit   source S = DSO (cos t, sin t, 0), detector centre
+ *           D = -(DSD-DSO)(cos t, sin t, 0), e_u = (-sin t, cos t, 0),
+ *           e_v = (0, 0, 1); pixel (p, q) centre
+ *           D + ((p-(nu-1)/2) du + off_u) e_u + ((q-(nv-1)/2) dv + off_v) e_v
+ *   projections proj[a][q][p], shape (n_angles, nv, nu), u fastest.
+ *
+ * Forward projection: the trilinear interpolant of the volume (zero outside,
+ * i.e. virtual zero voxels at index -1 and n) is integrated along the ray
+ * source -> pixel centre by the midpoint rule: the ray is clipped to the
+ * support [-1, n] per axis, K = ceil(len / (accuracy * min d)) samples of
+ * step h = len / K at the midpoints; proj = h * sum f(sample), mm x density.
+ *
+ * Backprojection (voxel-driven): for each voxel centre X and angle, s =
+ * X.(cos t, sin t, 0); the line source->X meets the detector at
+ * (u, v) = (X.e_u, X_z) * DSD/(DSO - s); the projection is interpolated
+ * bilinearly there (zero outside the detector) and weighted by
+ *   TIGRE_BP_FDK:      (DSO/(DSO - s))^2
+ *   TIGRE_BP_MATCHED:  (dx dy dz)/(du dv) * |X - S| * DSD^2 / (DSO - s)^3
+ *                      (voxel volume over the ray tube cross-section of one
+ *                      pixel at X: approximates the transpose of A)
+ *   TIGRE_BP_EXACT_ADJOINT: the exact transpose of tigre_forward (each
+ *                      sample scatters h * trilinear weight * y).
+ *
+ * Memory: the caller owns every volume / projection buffer.  Unless a
+ * function says otherwise they are DEVICE pointers (e.g. PyTorch tensors),
+ * contiguous, in the stated dtype.  The library owns only workspaces, which
+ * it caches inside the geometry handle and frees in tigre_geometry_destroy.
+ * A geometry handle is used by one host thread / one stream at a time.
+ *
+ * Errors: every function returns a tigre_status and never throws or aborts.
+ * On failure tigre_last_error() returns a message for the calling thread.
+ */
+#ifndef TIGRE103_H
+#define TIGRE103_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define TIGRE_API __attribute__((visibility("default")))
+#else
+#define TIGRE_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TIGRE_OK = 0,
+    TIGRE_ERR_INVALID_ARG = 1, /* bad pointer, size, dtype or geometry */
+    TIGRE_ERR_OOM = 2,         /* device or pinned allocation failed / over budget */
+    TIGRE_ERR_CUDA = 3,        /* CUDA runtime error; see tigre_last_error() */
+    TIGRE_ERR_TIMEOUT = 4,     /* a host wait exceeded opts.timeout_ms */
+    TIGRE_ERR_UNSUPPORTED = 5  /* valid request this build does not implement */
+} tigre_status;
+
+/* Storage type of a volume / projection buffer.  Arithmetic is FP32 along
+ * every ray and voxel sum whatever the storage type; solver scalars FP64. */
+typedef enum { TIGRE_F32 = 0, TIGRE_BF16 = 1, TIGRE_F16 = 2 } tigre_dtype;
+
+typedef enum {
+    TIGRE_BP_MATCHED = 0,
+    TIGRE_BP_FDK = 1,
+    TIGRE_BP_EXACT_ADJOINT = 2
+} tigre_bp_weight;
+
+/* Circular cone-beam geometry (Sec. 3.1 experiments: N^3 voxels, N^2 pixels,
+ * N angles).  accuracy = forward-projection ray step in voxels (0.5 typical). */
+typedef struct {
+    double DSO, DSD;       /* source-origin and source-detector distance */
+    int64_t n_voxel[3];    /* nx, ny, nz */
+    double d_voxel[3];     /* dx, dy, dz */
+    double off_origin[3];  /* volume centre offset */
+    int64_t n_det[2];      /* nu, nv */
+    double d_det[2];       /* du, dv */
+    double off_det[2];     /* detector offset along e_u, e_v */
+    double accuracy;
+} tigre_geometry_desc;
+
+typedef struct tigre_geometry* tigre_geometry_t;
+
+/* Validate the description and copy the angles (host array of n_angles
+ * doubles).  Requires DSO > 0, DSD > DSO, all sizes > 0, finite values, and a
+ * source orbit outside the volume.  Invalid arguments are rejected before any
+ * CUDA call; a valid geometry is bound to the current device and its
+ * per-angle parameters are uploaded synchronously (so create handles before
+ * any stream capture).  *out must be released by tigre_geometry_destroy. */
+TIGRE_API tigre_status tigre_geometry_create(const tigre_geometry_desc* desc, const double* angles,
+                                   int64_t n_angles, tigre_geometry_t* out);
+TIGRE_API tigre_status tigre_geometry_destroy(tigre_geometry_t geo);
+
+/* proj[0 .. angle_count) = A vol for angles angle_begin .. +angle_count.
+ * vol: device (nz, ny, nx) in vol_dtype; proj: device (angle_count, nv, nu) in
+ * proj_dtype, overwritten.  Asynchronous on cuda_stream (a cudaStream_t; NULL
+ * = legacy default stream). */
+TIGRE_API tigre_status tigre_forward(tigre_geometry_t geo, const void* vol, tigre_dtype vol_dtype,
+                           void* proj, tigre_dtype proj_dtype, int64_t angle_begin,
+                           int64_t angle_count, void* cuda_stream);
+
+/* vol = sum over angles angle_begin .. +angle_count of the weighted
+ * backprojection of proj (device (angle_count, nv, nu), proj_dtype).  vol:
+ * device (nz, ny, nx) in vol_dtype, overwritten.  Asynchronous. */
+TIGRE_API tigre_status tigre_backward(tigre_geometry_t geo, const void* proj, tigre_dtype proj_dtype,
+                            void* vol, tigre_dtype vol_dtype, int64_t angle_begin,
+                            int64_t angle_count, tigre_bp_weight weight, void* cuda_stream);
+
+/* n_steps of x <- x - alpha g / ||g||_2, g the gradient of
+ * TV_eps(x) = sum sqrt(Dx^2 + Dy^2 + Dz^2 + eps) with backward differences
+ * (zero across the low boundary); a step with ||g|| = 0 leaves x unchanged.
+ * vol: device (nz, ny, nx), updated in place.  ||g|| is reduced in FP64.
+ * Uses a scratch volume (FP32) allocated per call.  Asynchronous. */
+TIGRE_API tigre_status tigre_tv_step(const int64_t n_voxel[3], void* vol, tigre_dtype dtype, int n_steps,
+                           double alpha, double eps, void* cuda_stream);
+
+/* Solver flags. */
+#define TIGRE_HOST_RESIDENT 0x1u /* proj / vol are host pointers (out-of-core mode) */
+#define TIGRE_GRAPH 0x2u         /* capture each iteration in a CUDA graph */
+
+typedef struct {
+    int n_iter;                 /* iterations (default 10) */
+    double lambda;              /* SIRT / OS-SART relaxation (default 1) */
+    int subset_size;            /* OS-SART angles per subset (default 20) */
+    int tv_steps;               /* OS-SART: TV steps after each iteration (0 = off) */
+    double tv_alpha;            /* TV step = tv_alpha * ||x_after - x_before|| */
+    double tv_eps;              /* TV smoothing (default 1e-8) */
+    tigre_bp_weight bp_weight;  /* backprojector (default MATCHED) */
+    int nonneg;                 /* clamp x >= 0 after each update (SIRT/OS-SART) */
+    tigre_dtype storage;        /* storage type of the iterates (default F32) */
+    int64_t device_budget_bytes;/* 0 = free device memory; used by out-of-core */
+    int64_t timeout_ms;         /* host waits (default 0 = none) */
+    uint32_t flags;             /* TIGRE_HOST_RESIDENT, TIGRE_GRAPH */
+    void* cuda_stream;          /* stream for all work (NULL = default) */
+} tigre_solver_opts;
+
+/* Fill *opts with the defaults listed above. */
+TIGRE_API tigre_status tigre_solver_opts_default(tigre_solver_opts* opts);
+
+/* SIRT (x <- x + lambda V A_w^T W (b - A x), W = 1/(A 1), V = 1/(A_w^T 1),
+ * reciprocals of values <= 1e-12 set to 0).  proj: b (n_angles, nv, nu) F32;
+ * vol: (nz, ny, nx) F32 initial guess in, result out.  resid_hist (host,
+ * n_iter doubles, may be NULL) receives ||b - A x_k|| before update k. */
+TIGRE_API tigre_status tigre_sirt(tigre_geometry_t geo, const void* proj, void* vol,
+                        const tigre_solver_opts* opts, double* resid_hist);
+
+/* OS-SART: the SIRT update applied per subset of subset_size consecutive
+ * angles, subsets in order; with tv_steps > 0, tigre_tv_step after each full
+ * iteration with alpha = tv_alpha * ||x - x_prev||.  resid_hist[k] =
+ * sqrt(sum over subsets of ||b_s - A_s x||^2) during iteration k. */
+TIGRE_API tigre_status tigre_sart(tigre_geometry_t geo, const void* proj, void* vol,
+                        const tigre_solver_opts* opts, double* resid_hist);
+
+/* CGLS with FP64 inner products computed on the device; x0 = vol on entry
+ * (r0 = b - A x0).  resid_hist[k] = ||r|| after iteration k. */
+TIGRE_API tigre_status tigre_cgls(tigre_geometry_t geo, const void* proj, void* vol,
+                        const tigre_solver_opts* opts, double* resid_hist);
+
+/* Message describing the last failure on the calling thread ("" if none). */
+TIGRE_API const char* tigre_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TIGRE103_H */

@@ -1,0 +1,383 @@
+// Backprojection A^T y (paper Sec. 2.2).
+//
+// Voxel-driven (FDK or pseudo-matched weights): each thread owns one (x, y)
+// column and NZ consecutive voxels of it, as in the paper's organisation
+// (Fig. 4: each thread updates N_z voxels), and loops over all angles of the
+// call.  Per angle the detector column coordinate u and the FDK weight are
+// the same for the whole z-column; only the row coordinate v moves, linearly
+// in z.  Per voxel and angle:
+//   s = X.(cos t, sin t, 0), mag = DSD/(DSO - s),
+//   (u, v) = ((X.e_u) mag, X_z mag) -> bilinear tap of the projection,
+//   FDK:     w = (DSO/(DSO - s))^2
+//   matched: w = (dx dy dz)/(du dv) * |X - S| * DSD^2/(DSO - s)^3.
+// The projections are first copied into a buffer with a two-pixel zero
+// border, so clamped coordinates read zeros and the loop has no branches.
+// Grid order: x-tiles fastest, z-chunks slowest, so resident blocks share one
+// band of detector rows per angle in L2.
+//
+// Exact adjoint: the transpose of the forward projector, each ray scattering
+// h * trilinear weight * y into the 8 corner voxels of each of its samples
+// (FP32 atomics into padded accumulators in the same two layouts as the
+// forward projector, so a warp's atomics hit adjacent addresses).
+#include <algorithm>
+
+#include "ray.cuh"
+
+namespace tigre {
+
+struct BpConst {
+    int nx, ny, nz, nu, nv;
+    float x0, y0, z0;  // world position (mm) of voxel (0, 0, 0)
+    float dx, dy, dz;
+    float DSO, DSD;
+    float inv_du, inv_dv;
+    float pu_off, pv_off;  // pixel index = coordinate / pitch + offset
+    float wscale;          // (dx dy dz)/(du dv) * DSD^2
+};
+
+template <typename T>
+__device__ __forceinline__ float ldp(const T* p)
+{
+    return to_f32<T>(__ldg(p));
+}
+
+// SART == true: also accumulate the backprojection of the all-ones
+// projections (the normaliser V^-1 = A_w^T 1, from the same weights and
+// interpolation) and finish with vol += lambda * num / den (den > 1e-12),
+// clamped at zero when nonneg.
+template <typename TP, typename TV, int NZ, int MODE, bool SART = false>
+__global__ void __launch_bounds__(256) bp_voxel_kernel(const TP* __restrict__ pp,
+                                                       TV* __restrict__ vol,
+                                                       const BpAngle* __restrict__ params,
+                                                       BpConst c, int a_first, int na,
+                                                       int accumulate, float lambda = 0.0f,
+                                                       int nonneg = 0)
+{
+    const int x = blockIdx.x * 32 + threadIdx.x;
+    const int y = blockIdx.y * 8 + threadIdx.y;
+    const int zb = blockIdx.z * NZ;
+    if (x >= c.nx || y >= c.ny) return;
+    const float X = fmaf((float)x, c.dx, c.x0);
+    const float Y = fmaf((float)y, c.dy, c.y0);
+    const float Zb = fmaf((float)zb, c.dz, c.z0);
+    const int PU = c.nu + 2 * kPad;
+    const int64_t PA = (int64_t)PU * (c.nv + 2 * kPad);
+    const float pu_hi = (float)c.nu + 0.5f, pv_hi = (float)c.nv + 0.5f;
+
+    float acc[NZ];
+    float nrm[SART ? NZ : 1];
+#pragma unroll
+    for (int k = 0; k < NZ; ++k) acc[k] = 0.0f;
+#pragma unroll
+    for (int k = 0; k < (SART ? NZ : 1); ++k) nrm[k] = 0.0f;
+
+    for (int a = 0; a < na; ++a) {
+        const BpAngle A = params[a_first + a];
+        const float s = fmaf(X, A.c, Y * A.s);
+        const float inv_den = 1.0f / (c.DSO - s);
+        const float mag = c.DSD * inv_den;
+        const float u = fmaf(Y, A.c, -X * A.s) * mag;
+        // Clamp far outside the detector onto the zero border, then pad.
+        const float pu = fminf(fmaxf(fmaf(u, c.inv_du, c.pu_off), -1.5f), pu_hi) + (float)kPad;
+        int ip;
+        float fu;
+        split_floor(pu, ip, fu);
+        const TP* col = pp + (int64_t)a * PA + ip;
+        const float pv0 = fmaf(Zb * mag, c.inv_dv, c.pv_off);
+        const float dpv = c.dz * mag * c.inv_dv;
+        // Bilinear weight of the all-ones image (zero outside the detector).
+        float tu = 0.0f;
+        if (SART)
+            tu = ((unsigned)(ip - kPad) < (unsigned)c.nu ? 1.0f - fu : 0.0f) +
+                 ((unsigned)(ip - kPad + 1) < (unsigned)c.nu ? fu : 0.0f);
+        float w, lxy2 = 0.0f;
+        if (MODE == TIGRE_BP_FDK) {
+            const float t = c.DSO * inv_den;
+            w = t * t;
+        } else {
+            const float ex = X - A.srcx, ey = Y - A.srcy;
+            lxy2 = fmaf(ex, ex, ey * ey);
+            w = c.wscale * inv_den * inv_den * inv_den;
+        }
+#pragma unroll
+        for (int k = 0; k < NZ; ++k) {
+            const float pv =
+                fminf(fmaxf(fmaf((float)k, dpv, pv0), -1.5f), pv_hi) + (float)kPad;
+            int iq;
+            float fv;
+            split_floor(pv, iq, fv);
+            const TP* r0 = col + iq * PU;
+            const float a00 = ldp(r0), a01 = ldp(r0 + 1);
+            const float a10 = ldp(r0 + PU), a11 = ldp(r0 + PU + 1);
+            const float top = fmaf(fu, a01 - a00, a00);
+            const float bot = fmaf(fu, a11 - a10, a10);
+            const float val = fmaf(fv, bot - top, top);
+            float wk = w;
+            if (MODE != TIGRE_BP_FDK) {
+                const float Z = fmaf((float)k, c.dz, Zb);
+                const float l2 = fmaf(Z, Z, lxy2);
+                wk = w * (l2 * rsqrtf(l2));
+            }
+            acc[k] = fmaf(wk, val, acc[k]);
+            if (SART) {
+                const float tv = ((unsigned)(iq - kPad) < (unsigned)c.nv ? 1.0f - fv : 0.0f) +
+                                 ((unsigned)(iq - kPad + 1) < (unsigned)c.nv ? fv : 0.0f);
+                nrm[k] = fmaf(wk, tu * tv, nrm[k]);
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < NZ; ++k) {
+        const int z = zb + k;
+        if (z < c.nz) {
+            TV* o = vol + ((int64_t)z * c.ny + y) * c.nx + x;
+            if (SART) {
+                const float den = nrm[k];
+                float v = to_f32<TV>(*o);
+                if (den > 1e-12f) v = fmaf(lambda, acc[k] / den, v);
+                if (nonneg) v = fmaxf(v, 0.0f);
+                *o = from_f32<TV>(v);
+            } else {
+                const float prev = accumulate ? to_f32<TV>(*o) : 0.0f;
+                *o = from_f32<TV>(prev + acc[k]);
+            }
+        }
+    }
+}
+
+// Copy projections into the zero-bordered buffer: out[a][q+P][p+P] = in[a][q][p].
+template <typename TP>
+__global__ void pad_proj_kernel(const TP* __restrict__ in, TP* __restrict__ out, int nu, int nv)
+{
+    const int q = blockIdx.y, a = blockIdx.z;
+    const int PU = nu + 2 * kPad, PV = nv + 2 * kPad;
+    const TP* src = in + ((int64_t)a * nv + q) * nu;
+    TP* dst = out + ((int64_t)a * PV + q + kPad) * PU + kPad;
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < nu; p += gridDim.x * blockDim.x)
+        dst[p] = src[p];
+}
+
+// Exact adjoint: scatter every sample of each ray.
+template <typename TP>
+__global__ void __launch_bounds__(256) adj_scatter_kernel(const TP* __restrict__ proj,
+                                                          float* __restrict__ acc_xy,
+                                                          float* __restrict__ acc_yx,
+                                                          const FwdAngle* __restrict__ params,
+                                                          FwdConst c, int a_first)
+{
+    const int p = blockIdx.x * 32 + threadIdx.x;
+    const int q = blockIdx.z * blockDim.y + threadIdx.y;
+    const int a = blockIdx.y;
+    if (p >= c.nu || q >= c.nv) return;
+    const float yv = to_f32<TP>(proj[((int64_t)a * c.nv + q) * c.nu + p]);
+    if (yv == 0.0f) return;
+    Ray R;
+    setup_ray(params + a_first + a, c, p, q, R);
+    if (!R.ok || R.K == 0) return;
+    float* __restrict__ acc = R.layout ? acc_yx : acc_xy;
+    const int PF = R.nf + 2 * kPad;
+    const int PFM = PF * (R.nm + 2 * kPad);
+    const float hy = R.h * yv;
+    float kf = 0.0f;
+    for (int k = 0; k < R.K; ++k, kf += 1.0f) {
+        int i_f, i_m, i_s;
+        float af, am, as;
+        split_floor(fmaf(kf, R.d[0], R.x0[0]), i_f, af);
+        split_floor(fmaf(kf, R.d[1], R.x0[1]), i_m, am);
+        split_floor(fmaf(kf, R.d[2], R.x0[2]), i_s, as);
+        float* b = acc + (i_s * PFM + i_m * PF + i_f);
+        const float s0 = hy * (1.0f - as), s1 = hy * as;
+        const float m00 = s0 * (1.0f - am), m01 = s0 * am, m10 = s1 * (1.0f - am), m11 = s1 * am;
+        atomicAdd(b, m00 * (1.0f - af));
+        atomicAdd(b + 1, m00 * af);
+        atomicAdd(b + PF, m01 * (1.0f - af));
+        atomicAdd(b + PF + 1, m01 * af);
+        atomicAdd(b + PFM, m10 * (1.0f - af));
+        atomicAdd(b + PFM + 1, m10 * af);
+        atomicAdd(b + PFM + PF, m11 * (1.0f - af));
+        atomicAdd(b + PFM + PF + 1, m11 * af);
+    }
+}
+
+// vol[z][y][x] (+)= acc_xy[z+P][y+P][x+P] + acc_yx[z+P][x+P][y+P].
+template <typename TV>
+__global__ void adj_finish_kernel(const float* __restrict__ acc_xy,
+                                  const float* __restrict__ acc_yx, TV* __restrict__ vol, int nx,
+                                  int ny, int nz, int accumulate)
+{
+    __shared__ float tile[32][33];
+    const int z = blockIdx.z;
+    const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 32;
+    const int64_t zp = z + kPad;
+    if (acc_yx) {
+        const int PF = ny + 2 * kPad, PM = nx + 2 * kPad;
+        for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+            const int y = y0 + threadIdx.x, x = x0 + i;
+            tile[i][threadIdx.x] =
+                (x < nx && y < ny) ? acc_yx[(zp * PM + x + kPad) * PF + y + kPad] : 0.0f;
+        }
+    }
+    __syncthreads();
+    const int PF = nx + 2 * kPad, PM = ny + 2 * kPad;
+    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+        const int x = x0 + threadIdx.x, y = y0 + j;
+        if (x >= nx || y >= ny) continue;
+        float v = acc_xy ? acc_xy[(zp * PM + y + kPad) * PF + x + kPad] : 0.0f;
+        if (acc_yx) v += tile[threadIdx.x][j];
+        TV* o = vol + ((int64_t)z * ny + y) * nx + x;
+        if (accumulate) v += to_f32<TV>(*o);
+        *o = from_f32<TV>(v);
+    }
+}
+
+static BpConst make_bp_const(const tigre_geometry_desc& d)
+{
+    BpConst c;
+    c.nx = (int)d.n_voxel[0];
+    c.ny = (int)d.n_voxel[1];
+    c.nz = (int)d.n_voxel[2];
+    c.nu = (int)d.n_det[0];
+    c.nv = (int)d.n_det[1];
+    c.x0 = (float)(-0.5 * (double)(d.n_voxel[0] - 1) * d.d_voxel[0] + d.off_origin[0]);
+    c.y0 = (float)(-0.5 * (double)(d.n_voxel[1] - 1) * d.d_voxel[1] + d.off_origin[1]);
+    c.z0 = (float)(-0.5 * (double)(d.n_voxel[2] - 1) * d.d_voxel[2] + d.off_origin[2]);
+    c.dx = (float)d.d_voxel[0];
+    c.dy = (float)d.d_voxel[1];
+    c.dz = (float)d.d_voxel[2];
+    c.DSO = (float)d.DSO;
+    c.DSD = (float)d.DSD;
+    c.inv_du = (float)(1.0 / d.d_det[0]);
+    c.inv_dv = (float)(1.0 / d.d_det[1]);
+    c.pu_off = (float)(0.5 * (double)(d.n_det[0] - 1) - d.off_det[0] / d.d_det[0]);
+    c.pv_off = (float)(0.5 * (double)(d.n_det[1] - 1) - d.off_det[1] / d.d_det[1]);
+    c.wscale = (float)(d.d_voxel[0] * d.d_voxel[1] * d.d_voxel[2] / (d.d_det[0] * d.d_det[1]) *
+                       d.DSD * d.DSD);
+    return c;
+}
+
+constexpr int kBpNZ = 16;
+
+template <typename TP, typename TV>
+static tigre_status launch_voxel_bp(tigre_geometry* g, const TP* proj, TV* vol, int64_t a0,
+                                    int64_t na, tigre_bp_weight w, int accumulate,
+                                    cudaStream_t st, bool sart = false, float lambda = 0.0f,
+                                    int nonneg = 0)
+{
+    const tigre_geometry_desc& d = g->desc;
+    const BpConst c = make_bp_const(d);
+    const size_t pelems = (size_t)na * (size_t)(c.nu + 2 * kPad) * (size_t)(c.nv + 2 * kPad);
+    const uint64_t tag = 0x9000000000000000ull ^ ((uint64_t)sizeof(TP) << 56) ^
+                         ((uint64_t)na << 40) ^ ((uint64_t)c.nu << 20) ^ (uint64_t)c.nv;
+    if (g->proj_pad.bytes < pelems * sizeof(TP) || g->proj_pad.tag != tag) {
+        TIGRE_TRY(g->proj_pad.ensure(pelems * sizeof(TP)));
+        TIGRE_CUDA(cudaMemsetAsync(g->proj_pad.ptr, 0, pelems * sizeof(TP), st));
+        g->proj_pad.tag = tag;
+    }
+    for (int64_t s = 0; s < na; s += 65535) {
+        const int64_t cnt = std::min<int64_t>(65535, na - s);
+        dim3 grid((unsigned)((c.nu + 255) / 256), (unsigned)c.nv, (unsigned)cnt);
+        pad_proj_kernel<TP><<<grid, 256, 0, st>>>(
+            proj + s * (int64_t)c.nu * c.nv,
+            (TP*)g->proj_pad.ptr + s * (int64_t)(c.nu + 2 * kPad) * (c.nv + 2 * kPad), c.nu, c.nv);
+        TIGRE_LAUNCHED("pad_proj_kernel");
+    }
+    dim3 grid((unsigned)((c.nx + 31) / 32), (unsigned)((c.ny + 7) / 8),
+              (unsigned)((c.nz + kBpNZ - 1) / kBpNZ));
+    if (grid.y > 65535 || grid.z > 65535) return fail(TIGRE_ERR_UNSUPPORTED, "volume too large");
+    const BpAngle* params = (const BpAngle*)g->bp_params.ptr;
+    const TP* pp = (const TP*)g->proj_pad.ptr;
+    const dim3 block(32, 8);
+    if (sart) {
+        if (w == TIGRE_BP_FDK)
+            bp_voxel_kernel<TP, TV, kBpNZ, TIGRE_BP_FDK, true><<<grid, block, 0, st>>>(
+                pp, vol, params, c, (int)a0, (int)na, 0, lambda, nonneg);
+        else
+            bp_voxel_kernel<TP, TV, kBpNZ, TIGRE_BP_MATCHED, true><<<grid, block, 0, st>>>(
+                pp, vol, params, c, (int)a0, (int)na, 0, lambda, nonneg);
+    } else if (w == TIGRE_BP_FDK) {
+        bp_voxel_kernel<TP, TV, kBpNZ, TIGRE_BP_FDK><<<grid, block, 0, st>>>(
+            pp, vol, params, c, (int)a0, (int)na, accumulate);
+    } else {
+        bp_voxel_kernel<TP, TV, kBpNZ, TIGRE_BP_MATCHED><<<grid, block, 0, st>>>(
+            pp, vol, params, c, (int)a0, (int)na, accumulate);
+    }
+    TIGRE_LAUNCHED("bp_voxel_kernel");
+    return TIGRE_OK;
+}
+
+tigre_status sart_update_impl(tigre_geometry* g, const float* r, float* x, int64_t a0, int64_t na,
+                              tigre_bp_weight w, float lambda, int nonneg, cudaStream_t st)
+{
+    TIGRE_TRY(check_geometry(g));
+    TIGRE_TRY(check_range(g, a0, na));
+    if (w == TIGRE_BP_EXACT_ADJOINT)
+        return fail(TIGRE_ERR_UNSUPPORTED, "SIRT/OS-SART use the voxel-driven backprojector");
+    return launch_voxel_bp<float, float>(g, r, x, a0, na, w, 0, st, true, lambda, nonneg);
+}
+
+template <typename TP, typename TV>
+static tigre_status launch_adjoint(tigre_geometry* g, const TP* proj, TV* vol, int64_t a0,
+                                   int64_t na, int accumulate, cudaStream_t st)
+{
+    const tigre_geometry_desc& d = g->desc;
+    if (padded_elems(d) >= (size_t)INT32_MAX)
+        return fail(TIGRE_ERR_UNSUPPORTED, "exact adjoint needs (nx+4)(ny+4)(nz+4) < 2^31");
+    const FwdConst c = make_fwd_const(d);
+    bool need[2] = {false, false};
+    for (int64_t a = a0; a < a0 + na; ++a) need[g->layout[(size_t)a]] = true;
+    DeviceBuffer* bufs[2] = {&g->adj_xy, &g->adj_yx};
+    const size_t bytes = padded_elems(d) * sizeof(float);
+    for (int l = 0; l < 2; ++l) {
+        if (!need[l]) continue;
+        TIGRE_TRY(bufs[l]->ensure(bytes));
+        bufs[l]->tag = 0;  // contents are accumulator data, not a zero-bordered layout
+        TIGRE_CUDA(cudaMemsetAsync(bufs[l]->ptr, 0, bytes, st));
+    }
+    float* axy = need[0] ? (float*)g->adj_xy.ptr : nullptr;
+    float* ayx = need[1] ? (float*)g->adj_yx.ptr : nullptr;
+    for (int64_t s = 0; s < na; s += 65535) {
+        const int64_t cnt = std::min<int64_t>(65535, na - s);
+        dim3 grid((unsigned)((c.nu + 31) / 32), (unsigned)cnt, (unsigned)((c.nv + 7) / 8));
+        adj_scatter_kernel<TP><<<grid, dim3(32, 8), 0, st>>>(
+            proj + s * (int64_t)c.nu * c.nv, axy, ayx, (const FwdAngle*)g->fwd_params.ptr, c,
+            (int)(a0 + s));
+        TIGRE_LAUNCHED("adj_scatter_kernel");
+    }
+    dim3 grid((unsigned)((c.nx + 31) / 32), (unsigned)((c.ny + 31) / 32), (unsigned)c.nz);
+    adj_finish_kernel<TV><<<grid, dim3(32, 8), 0, st>>>(axy, ayx, vol, c.nx, c.ny, c.nz,
+                                                        accumulate);
+    TIGRE_LAUNCHED("adj_finish_kernel");
+    return TIGRE_OK;
+}
+
+tigre_status backward_impl(tigre_geometry* g, const void* proj, tigre_dtype pt, void* vol,
+                           tigre_dtype vt, int64_t a0, int64_t na, tigre_bp_weight w,
+                           int accumulate, cudaStream_t st)
+{
+    TIGRE_TRY(check_geometry(g));
+    TIGRE_TRY(check_range(g, a0, na));
+    if (!vol || !proj) return fail(TIGRE_ERR_INVALID_ARG, "null vol or proj pointer");
+    if (!dtype_ok(vt) || !dtype_ok(pt)) return fail(TIGRE_ERR_INVALID_ARG, "bad dtype");
+    if (w != TIGRE_BP_MATCHED && w != TIGRE_BP_FDK && w != TIGRE_BP_EXACT_ADJOINT)
+        return fail(TIGRE_ERR_INVALID_ARG, "bad backprojection weight");
+    return dispatch_dtype(pt, [&](auto ptag) -> tigre_status {
+        using TP = decltype(ptag);
+        return dispatch_dtype(vt, [&](auto vtag) -> tigre_status {
+            using TV = decltype(vtag);
+            if (w == TIGRE_BP_EXACT_ADJOINT)
+                return launch_adjoint<TP, TV>(g, (const TP*)proj, (TV*)vol, a0, na, accumulate, st);
+            return launch_voxel_bp<TP, TV>(g, (const TP*)proj, (TV*)vol, a0, na, w, accumulate, st);
+        });
+    });
+}
+
+}  // namespace tigre
+
+extern "C" tigre_status tigre_backward(tigre_geometry_t geo, const void* proj,
+                                       tigre_dtype proj_dtype, void* vol, tigre_dtype vol_dtype,
+                                       int64_t angle_begin, int64_t angle_count,
+                                       tigre_bp_weight weight, void* cuda_stream)
+{
+    return tigre::backward_impl(geo, proj, proj_dtype, vol, vol_dtype, angle_begin, angle_count,
+                                weight, 0, (cudaStream_t)cuda_stream);
+}

@@ -1,0 +1,166 @@
+// Internal declarations shared by the translation units of libtigre103.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/tigre103.h"
+
+namespace tigre {
+
+// ------------------------------------------------------------------ errors
+
+void set_error(const std::string& msg);
+tigre_status fail(tigre_status st, const std::string& msg);
+tigre_status cuda_fail(cudaError_t err, const char* what);
+
+#define TIGRE_CUDA(call)                                             \
+    do {                                                             \
+        cudaError_t e_ = (call);                                     \
+        if (e_ != cudaSuccess) return ::tigre::cuda_fail(e_, #call); \
+    } while (0)
+
+#define TIGRE_TRY(call)                            \
+    do {                                           \
+        tigre_status s_ = (call);                  \
+        if (s_ != TIGRE_OK) return s_;             \
+    } while (0)
+
+// Check for a launch error right after a kernel launch.
+#define TIGRE_LAUNCHED(name)                                           \
+    do {                                                               \
+        cudaError_t e_ = cudaGetLastError();                           \
+        if (e_ != cudaSuccess) return ::tigre::cuda_fail(e_, name);    \
+    } while (0)
+
+inline size_t dtype_size(tigre_dtype t) { return t == TIGRE_F32 ? 4 : 2; }
+inline bool dtype_ok(tigre_dtype t) { return t == TIGRE_F32 || t == TIGRE_BF16 || t == TIGRE_F16; }
+
+// ------------------------------------------------------------- conversions
+
+template <typename T> __device__ __forceinline__ float to_f32(T v);
+template <> __device__ __forceinline__ float to_f32<float>(float v) { return v; }
+template <> __device__ __forceinline__ float to_f32<__nv_bfloat16>(__nv_bfloat16 v) { return __bfloat162float(v); }
+template <> __device__ __forceinline__ float to_f32<__half>(__half v) { return __half2float(v); }
+
+template <typename T> __device__ __forceinline__ T from_f32(float v);
+template <> __device__ __forceinline__ float from_f32<float>(float v) { return v; }
+template <> __device__ __forceinline__ __nv_bfloat16 from_f32<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+template <> __device__ __forceinline__ __half from_f32<__half>(float v) { return __float2half_rn(v); }
+
+// Dispatch a functor templated on the storage type of one buffer.
+template <typename F>
+tigre_status dispatch_dtype(tigre_dtype t, F&& f)
+{
+    switch (t) {
+    case TIGRE_F32: return f(float{});
+    case TIGRE_BF16: return f(__nv_bfloat16{});
+    case TIGRE_F16: return f(__half{});
+    }
+    return fail(TIGRE_ERR_INVALID_ARG, "unknown dtype");
+}
+
+// ---------------------------------------------------------- device buffers
+
+// A grow-only device buffer owned by a geometry handle.
+struct DeviceBuffer {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+    uint64_t tag = 0;  // what the buffer's zero border was laid out for (0 = nothing)
+    tigre_status ensure(size_t need);
+    void release();
+};
+
+// Per-angle parameters of the forward projector, expressed in the index
+// coordinates of the padded volume layout the angle uses.  "f", "m", "s" are
+// the fastest, middle and slowest memory axes of that layout.
+struct FwdAngle {
+    float src[3];   // source position (f, m, s), unpadded index units
+    float base[3];  // (P - S)/d for pixel (0, 0)
+    float dp[3];    // change of (P - S)/d per pixel along u
+    float dq[3];    // change of (P - S)/d per pixel along v
+    int layout;     // 0: x fastest (vol as given), 1: y fastest (transposed)
+    int pad_[3];
+};
+static_assert(sizeof(FwdAngle) == 64, "FwdAngle must stay 64 bytes");
+
+// Per-angle parameters of the voxel-driven backprojector.
+struct BpAngle {
+    float c, s;       // cos, sin of the angle
+    float srcx, srcy; // source position (mm)
+};
+
+}  // namespace tigre
+
+// The opaque handle of the C ABI.
+struct tigre_geometry {
+    tigre_geometry_desc desc;
+    std::vector<double> angles;
+    int device = -1;
+    bool uploaded = false;
+    tigre::DeviceBuffer fwd_params;   // FwdAngle[n_angles]
+    tigre::DeviceBuffer bp_params;    // BpAngle[n_angles]
+    tigre::DeviceBuffer vol_xy;       // padded volume, x fastest
+    tigre::DeviceBuffer vol_yx;       // padded volume, y fastest
+    tigre::DeviceBuffer proj_pad;     // zero-bordered projections for the backprojector
+    tigre::DeviceBuffer adj_xy;       // FP32 padded accumulators of the exact adjoint
+    tigre::DeviceBuffer adj_yx;
+    tigre::DeviceBuffer scratch_vol;  // FP32 volume-sized scratch
+    tigre::DeviceBuffer scratch_red;  // reduction partials / device scalars
+    std::vector<int> layout;          // forward-projector layout per angle (host copy)
+};
+
+namespace tigre {
+
+constexpr int kPad = 2;  // zero voxels around the volume in the padded layouts
+
+tigre_status upload_params(tigre_geometry* g);
+size_t padded_elems(const tigre_geometry_desc& d);
+tigre_status ensure_padded(DeviceBuffer& buf, const tigre_geometry_desc& d, size_t elem, int layout,
+                           cudaStream_t st);
+tigre_status check_geometry(tigre_geometry* g);
+tigre_status check_range(const tigre_geometry* g, int64_t begin, int64_t count);
+
+inline int64_t n_vox(const tigre_geometry* g)
+{
+    return g->desc.n_voxel[0] * g->desc.n_voxel[1] * g->desc.n_voxel[2];
+}
+inline int64_t n_pix(const tigre_geometry* g) { return g->desc.n_det[0] * g->desc.n_det[1]; }
+
+// ------------------------------------------------------ internal operators
+
+// Forward projection with FP32 accumulation (see tigre_forward).
+tigre_status forward_impl(tigre_geometry* g, const void* vol, tigre_dtype vt, void* proj,
+                          tigre_dtype pt, int64_t a0, int64_t na, cudaStream_t st);
+// Backprojection; accumulate != 0 adds into vol instead of overwriting.
+tigre_status backward_impl(tigre_geometry* g, const void* proj, tigre_dtype pt, void* vol,
+                           tigre_dtype vt, int64_t a0, int64_t na, tigre_bp_weight w,
+                           int accumulate, cudaStream_t st);
+tigre_status tv_impl(const int64_t n[3], void* vol, tigre_dtype t, int n_steps, double alpha,
+                     double eps, const double* d_alpha_scale, void* scratch_g,
+                     double* d_red, cudaStream_t st);
+
+// ------------------------------------------------------------ vector ops
+// All reductions are deterministic: a fixed grid writes per-block FP64
+// partial sums, then one block adds them in a fixed order.
+
+constexpr int kRedBlocks = 608;      // 152 SMs x 4
+constexpr int kRedThreads = 256;
+
+// out[0] = sum_i a_i * b_i (FP64) over n elements of float arrays.
+tigre_status dot_f64(const float* a, const float* b, int64_t n, double* d_partials, double* d_out,
+                     cudaStream_t st);
+
+// SART-type update fused into the voxel-driven backprojector:
+// x += lambda * (sum_a w_a bil_a(r)) / (sum_a w_a bil_a(1)) over the angle
+// range (no update where the denominator is <= 1e-12), then x = max(x, 0) if
+// nonneg.  r: device F32 (na, nv, nu); x: device F32 volume.
+tigre_status sart_update_impl(tigre_geometry* g, const float* r, float* x, int64_t a0, int64_t na,
+                              tigre_bp_weight w, float lambda, int nonneg, cudaStream_t st);
+
+}  // namespace tigre

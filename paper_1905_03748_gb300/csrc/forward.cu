@@ -1,0 +1,239 @@
+// Interpolated ray-driven forward projector A x (paper Sec. 2.1, interpolated
+// projection; one thread per detector pixel as in the paper's kernel
+// organisation, Fig. 2).
+//
+// proj[a][q][p] = h * sum_{k<K} f~(src + t_k (P - S)/d), f~ the trilinear
+// interpolant of the volume with zero outside, t_k the midpoints of K equal
+// steps over the part of the ray inside the interpolant's support [-1, n],
+// K = ceil(len / (accuracy * min d)), h = len / K.
+//
+// GB300 design:
+//  * The volume is copied once per call into two zero-padded layouts (x
+//    fastest, and y fastest).  Each angle reads the layout whose fastest axis
+//    is closest to e_u, so the 32 rays of a warp (adjacent pixels of one
+//    detector row) gather from adjacent addresses: each tap load touches 1-2
+//    cache lines per warp.  The two-voxel zero border removes every bounds
+//    check from the sample loop.
+//  * Grid order: u-tiles fastest, then angles, then detector row bands.  The
+//    blocks resident at any time belong to one row band and many angles; they
+//    all read the same z-slab of the volume, which stays in the 126 MB L2, so
+//    HBM reads the volume about once per call.
+//  * floor() without conversion instructions (split_floor).
+#include <algorithm>
+#include <cmath>
+
+#include "ray.cuh"
+
+namespace tigre {
+
+FwdConst make_fwd_const(const tigre_geometry_desc& d)
+{
+    FwdConst c;
+    c.nx = (int)d.n_voxel[0];
+    c.ny = (int)d.n_voxel[1];
+    c.nz = (int)d.n_voxel[2];
+    c.nu = (int)d.n_det[0];
+    c.nv = (int)d.n_det[1];
+    c.u0 = (float)(-0.5 * (double)(d.n_det[0] - 1) * d.d_det[0] + d.off_det[0]);
+    c.v0 = (float)(-0.5 * (double)(d.n_det[1] - 1) * d.d_det[1] + d.off_det[1]);
+    c.du = (float)d.d_det[0];
+    c.dv = (float)d.d_det[1];
+    c.dsd2 = (float)(d.DSD * d.DSD);
+    const double dmin = std::min(d.d_voxel[0], std::min(d.d_voxel[1], d.d_voxel[2]));
+    const double step = d.accuracy * dmin;
+    c.inv_step = (float)(1.0 / step);
+    double diag2 = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        const double e = (double)(d.n_voxel[a] + 1) * d.d_voxel[a];
+        diag2 += e * e;
+    }
+    c.kmax = (int)std::min(std::ceil(std::sqrt(diag2) / step) + 4.0, 1.0e8);
+    return c;
+}
+
+template <typename T>
+__device__ __forceinline__ float ld(const T* p)
+{
+    return to_f32<T>(__ldg(p));
+}
+
+template <typename TV, typename TP>
+__global__ void __launch_bounds__(256) fwd_l1_kernel(const TV* __restrict__ vxy,
+                                                     const TV* __restrict__ vyx,
+                                                     TP* __restrict__ proj,
+                                                     const FwdAngle* __restrict__ params,
+                                                     FwdConst c, int a_first)
+{
+    const int p = blockIdx.x * 32 + threadIdx.x;
+    const int q = blockIdx.z * blockDim.y + threadIdx.y;
+    const int a = blockIdx.y;
+    if (p >= c.nu || q >= c.nv) return;
+
+    Ray R;
+    setup_ray(params + a_first + a, c, p, q, R);
+    float out = 0.0f;
+    if (!R.ok) {
+        out = __int_as_float(0x7fc00000);  // NaN: the ray failed the bounds proof
+    } else if (R.K > 0) {
+        const TV* __restrict__ vol = R.layout ? vyx : vxy;
+        const int PF = R.nf + 2 * kPad;
+        const int PFM = PF * (R.nm + 2 * kPad);
+        float acc = 0.0f;
+        float kf = 0.0f;
+#pragma unroll 2
+        for (int k = 0; k < R.K; ++k, kf += 1.0f) {
+            int i_f, i_m, i_s;
+            float af, am, as;
+            split_floor(fmaf(kf, R.d[0], R.x0[0]), i_f, af);
+            split_floor(fmaf(kf, R.d[1], R.x0[1]), i_m, am);
+            split_floor(fmaf(kf, R.d[2], R.x0[2]), i_s, as);
+            const TV* b = vol + (i_s * PFM + i_m * PF + i_f);
+            const float v000 = ld(b), v100 = ld(b + 1);
+            const float v010 = ld(b + PF), v110 = ld(b + PF + 1);
+            const float v001 = ld(b + PFM), v101 = ld(b + PFM + 1);
+            const float v011 = ld(b + PFM + PF), v111 = ld(b + PFM + PF + 1);
+            const float c00 = fmaf(af, v100 - v000, v000);
+            const float c10 = fmaf(af, v110 - v010, v010);
+            const float c01 = fmaf(af, v101 - v001, v001);
+            const float c11 = fmaf(af, v111 - v011, v011);
+            const float c0 = fmaf(am, c10 - c00, c00);
+            const float c1 = fmaf(am, c11 - c01, c01);
+            acc += fmaf(as, c1 - c0, c0);
+        }
+        out = acc * R.h;
+    }
+    proj[((int64_t)a * c.nv + q) * c.nu + p] = from_f32<TP>(out);
+}
+
+// out (padded, x fastest): out[z+P][y+P][x+P] = vol[z][y][x].
+template <typename T>
+__global__ void pad_xy_kernel(const T* __restrict__ vol, T* __restrict__ out, int nx, int ny,
+                              int nz)
+{
+    const int y = blockIdx.y, z = blockIdx.z;
+    const int PF = nx + 2 * kPad, PM = ny + 2 * kPad;
+    const T* src = vol + ((int64_t)z * ny + y) * nx;
+    T* dst = out + ((int64_t)(z + kPad) * PM + (y + kPad)) * PF + kPad;
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < nx; x += gridDim.x * blockDim.x)
+        dst[x] = src[x];
+}
+
+// out (padded, y fastest): out[z+P][x+P][y+P] = vol[z][y][x], 32x32 tiles.
+template <typename T>
+__global__ void pad_yx_kernel(const T* __restrict__ vol, T* __restrict__ out, int nx, int ny,
+                              int nz)
+{
+    __shared__ T tile[32][33];
+    const int z = blockIdx.z;
+    const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 32;
+    const T* src = vol + (int64_t)z * ny * nx;
+    for (int j = threadIdx.y; j < 32; j += blockDim.y) {
+        const int x = x0 + threadIdx.x, y = y0 + j;
+        if (x < nx && y < ny) tile[j][threadIdx.x] = src[(int64_t)y * nx + x];
+    }
+    __syncthreads();
+    const int PF = ny + 2 * kPad, PM = nx + 2 * kPad;
+    T* dst = out + (int64_t)(z + kPad) * PM * PF;
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int y = y0 + threadIdx.x, x = x0 + i;
+        if (x < nx && y < ny) dst[(int64_t)(x + kPad) * PF + (y + kPad)] = tile[threadIdx.x][i];
+    }
+}
+
+size_t padded_elems(const tigre_geometry_desc& d)
+{
+    return (size_t)(d.n_voxel[0] + 2 * kPad) * (size_t)(d.n_voxel[1] + 2 * kPad) *
+           (size_t)(d.n_voxel[2] + 2 * kPad);
+}
+
+// Tag identifying a zero-bordered padded layout (element size, dims, layout).
+static uint64_t layout_tag(const tigre_geometry_desc& d, size_t elem, int layout)
+{
+    return 1ull + (uint64_t)elem + 16ull * (uint64_t)layout +
+           64ull * ((uint64_t)d.n_voxel[0] + 1048583ull * ((uint64_t)d.n_voxel[1] +
+                                                           1048583ull * (uint64_t)d.n_voxel[2]));
+}
+
+// Size `buf` for a padded layout and zero it (border included) whenever the
+// layout it holds changes; the interior is overwritten by every call.
+tigre_status ensure_padded(DeviceBuffer& buf, const tigre_geometry_desc& d, size_t elem,
+                           int layout, cudaStream_t st)
+{
+    const size_t bytes = padded_elems(d) * elem;
+    const uint64_t tag = layout_tag(d, elem, layout);
+    if (buf.bytes < bytes || buf.tag != tag) {
+        TIGRE_TRY(buf.ensure(bytes));
+        TIGRE_CUDA(cudaMemsetAsync(buf.ptr, 0, bytes, st));
+        buf.tag = tag;
+    }
+    return TIGRE_OK;
+}
+
+template <typename TV>
+tigre_status fill_padded(const tigre_geometry_desc& d, const TV* vol, TV* out, int layout,
+                         cudaStream_t st)
+{
+    const int nx = (int)d.n_voxel[0], ny = (int)d.n_voxel[1], nz = (int)d.n_voxel[2];
+    if (layout == 0) {
+        dim3 grid((unsigned)((nx + 255) / 256), (unsigned)ny, (unsigned)nz);
+        pad_xy_kernel<TV><<<grid, 256, 0, st>>>(vol, out, nx, ny, nz);
+        TIGRE_LAUNCHED("pad_xy_kernel");
+    } else {
+        dim3 grid((unsigned)((nx + 31) / 32), (unsigned)((ny + 31) / 32), (unsigned)nz);
+        pad_yx_kernel<TV><<<grid, dim3(32, 8), 0, st>>>(vol, out, nx, ny, nz);
+        TIGRE_LAUNCHED("pad_yx_kernel");
+    }
+    return TIGRE_OK;
+}
+
+tigre_status forward_impl(tigre_geometry* g, const void* vol, tigre_dtype vt, void* proj,
+                          tigre_dtype pt, int64_t a0, int64_t na, cudaStream_t st)
+{
+    TIGRE_TRY(check_geometry(g));
+    TIGRE_TRY(check_range(g, a0, na));
+    if (!vol || !proj) return fail(TIGRE_ERR_INVALID_ARG, "null vol or proj pointer");
+    if (!dtype_ok(vt) || !dtype_ok(pt)) return fail(TIGRE_ERR_INVALID_ARG, "bad dtype");
+    const tigre_geometry_desc& d = g->desc;
+    if (padded_elems(d) >= (size_t)INT32_MAX)
+        return fail(TIGRE_ERR_UNSUPPORTED,
+                    "in-core forward projection needs (nx+4)(ny+4)(nz+4) < 2^31; use out-of-core");
+    if (d.n_det[1] > 65535 * 8)
+        return fail(TIGRE_ERR_UNSUPPORTED, "detector too large for one launch");
+    const FwdConst c = make_fwd_const(d);
+    bool need[2] = {false, false};
+    for (int64_t a = a0; a < a0 + na; ++a) need[g->layout[(size_t)a]] = true;
+
+    return dispatch_dtype(vt, [&](auto vtag) -> tigre_status {
+        using TV = decltype(vtag);
+        DeviceBuffer* bufs[2] = {&g->vol_xy, &g->vol_yx};
+        for (int l = 0; l < 2; ++l) {
+            if (!need[l]) continue;
+            TIGRE_TRY(ensure_padded(*bufs[l], d, sizeof(TV), l, st));
+            TIGRE_TRY(fill_padded<TV>(d, (const TV*)vol, (TV*)bufs[l]->ptr, l, st));
+        }
+        return dispatch_dtype(pt, [&](auto ptag) -> tigre_status {
+            using TP = decltype(ptag);
+            const int64_t step = 65535;
+            for (int64_t s = 0; s < na; s += step) {
+                const int64_t cnt = std::min(step, na - s);
+                dim3 grid((unsigned)((c.nu + 31) / 32), (unsigned)cnt, (unsigned)((c.nv + 7) / 8));
+                fwd_l1_kernel<TV, TP><<<grid, dim3(32, 8), 0, st>>>(
+                    (const TV*)g->vol_xy.ptr, (const TV*)g->vol_yx.ptr,
+                    (TP*)proj + s * (int64_t)c.nu * c.nv, (const FwdAngle*)g->fwd_params.ptr, c,
+                    (int)(a0 + s));
+                TIGRE_LAUNCHED("fwd_l1_kernel");
+            }
+            return TIGRE_OK;
+        });
+    });
+}
+
+}  // namespace tigre
+
+extern "C" tigre_status tigre_forward(tigre_geometry_t geo, const void* vol, tigre_dtype vol_dtype,
+                                      void* proj, tigre_dtype proj_dtype, int64_t angle_begin,
+                                      int64_t angle_count, void* cuda_stream)
+{
+    return tigre::forward_impl(geo, vol, vol_dtype, proj, proj_dtype, angle_begin, angle_count,
+                               (cudaStream_t)cuda_stream);
+}

@@ -1,0 +1,227 @@
+// Geometry handle, parameter upload, workspaces and error reporting.
+//
+// The per-angle parameters are computed on the host in FP64 from the
+// circular cone-beam frame (source S = DSO (cos t, sin t, 0), detector centre
+// D = -(DSD - DSO)(cos t, sin t, 0), e_u = (-sin t, cos t, 0), e_v = z) and
+// rounded once to FP32 for the kernels.
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "common.cuh"
+
+namespace tigre {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+tigre_status fail(tigre_status st, const std::string& msg)
+{
+    set_error(msg);
+    return st;
+}
+
+tigre_status cuda_fail(cudaError_t err, const char* what)
+{
+    set_error(std::string(what) + ": " + cudaGetErrorName(err) + " (" + cudaGetErrorString(err) +
+              ")");
+    return err == cudaErrorMemoryAllocation ? TIGRE_ERR_OOM : TIGRE_ERR_CUDA;
+}
+
+tigre_status DeviceBuffer::ensure(size_t need)
+{
+    if (need <= bytes && ptr) return TIGRE_OK;
+    release();
+    if (need == 0) return TIGRE_OK;
+    cudaError_t e = cudaMalloc(&ptr, need);
+    if (e != cudaSuccess) {
+        ptr = nullptr;
+        bytes = 0;
+        cudaGetLastError();
+        return cuda_fail(e, "cudaMalloc(workspace)");
+    }
+    bytes = need;
+    return TIGRE_OK;
+}
+
+void DeviceBuffer::release()
+{
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+    bytes = 0;
+    tag = 0;
+}
+
+static bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+static tigre_status validate(const tigre_geometry_desc* d, const double* angles, int64_t na)
+{
+    if (!d || !angles) return fail(TIGRE_ERR_INVALID_ARG, "null geometry or angles");
+    if (na <= 0) return fail(TIGRE_ERR_INVALID_ARG, "n_angles must be > 0");
+    if (!finite_pos(d->DSO) || !finite_pos(d->DSD) || !(d->DSD > d->DSO))
+        return fail(TIGRE_ERR_INVALID_ARG, "need 0 < DSO < DSD (finite)");
+    double r2 = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        if (d->n_voxel[a] <= 0 || d->n_voxel[a] > (1 << 20))
+            return fail(TIGRE_ERR_INVALID_ARG, "n_voxel out of range");
+        if (!finite_pos(d->d_voxel[a])) return fail(TIGRE_ERR_INVALID_ARG, "d_voxel must be > 0");
+        if (!std::isfinite(d->off_origin[a]))
+            return fail(TIGRE_ERR_INVALID_ARG, "off_origin must be finite");
+        double half = 0.5 * (double)(d->n_voxel[a] + 1) * d->d_voxel[a] + std::fabs(d->off_origin[a]);
+        if (a < 2) r2 += half * half;
+    }
+    if (!(std::sqrt(r2) < d->DSO))
+        return fail(TIGRE_ERR_INVALID_ARG, "source orbit intersects the volume (DSO too small)");
+    for (int a = 0; a < 2; ++a) {
+        if (d->n_det[a] <= 0 || d->n_det[a] > (1 << 20))
+            return fail(TIGRE_ERR_INVALID_ARG, "n_det out of range");
+        if (!finite_pos(d->d_det[a])) return fail(TIGRE_ERR_INVALID_ARG, "d_det must be > 0");
+        if (!std::isfinite(d->off_det[a])) return fail(TIGRE_ERR_INVALID_ARG, "off_det must be finite");
+    }
+    if (!(std::isfinite(d->accuracy) && d->accuracy >= 1e-3 && d->accuracy <= 4.0))
+        return fail(TIGRE_ERR_INVALID_ARG, "accuracy must be in [1e-3, 4] voxels");
+    for (int64_t i = 0; i < na; ++i)
+        if (!std::isfinite(angles[i])) return fail(TIGRE_ERR_INVALID_ARG, "angles must be finite");
+    return TIGRE_OK;
+}
+
+tigre_status check_geometry(tigre_geometry* g)
+{
+    if (!g) return fail(TIGRE_ERR_INVALID_ARG, "null geometry handle");
+    int dev = -1;
+    TIGRE_CUDA(cudaGetDevice(&dev));
+    if (g->device < 0) g->device = dev;
+    if (dev != g->device)
+        return fail(TIGRE_ERR_INVALID_ARG, "geometry handle used on another device");
+    if (!g->uploaded) TIGRE_TRY(upload_params(g));
+    return TIGRE_OK;
+}
+
+tigre_status check_range(const tigre_geometry* g, int64_t begin, int64_t count)
+{
+    if (begin < 0 || count <= 0 || begin + count > (int64_t)g->angles.size())
+        return fail(TIGRE_ERR_INVALID_ARG, "angle range outside the geometry's angles");
+    return TIGRE_OK;
+}
+
+tigre_status upload_params(tigre_geometry* g)
+{
+    const tigre_geometry_desc& d = g->desc;
+    const int64_t na = (int64_t)g->angles.size();
+    std::vector<FwdAngle> fwd((size_t)na);
+    std::vector<BpAngle> bp((size_t)na);
+    g->layout.assign((size_t)na, 0);
+    const double nu = (double)d.n_det[0], nv = (double)d.n_det[1];
+    const double u0 = -0.5 * (nu - 1.0) * d.d_det[0] + d.off_det[0];
+    const double v0 = -0.5 * (nv - 1.0) * d.d_det[1] + d.off_det[1];
+    for (int64_t a = 0; a < na; ++a) {
+        const double t = g->angles[(size_t)a];
+        const double c = std::cos(t), s = std::sin(t);
+        const double S[3] = {d.DSO * c, d.DSO * s, 0.0};
+        const double D[3] = {-(d.DSD - d.DSO) * c, -(d.DSD - d.DSO) * s, 0.0};
+        const double eu[3] = {-s, c, 0.0};
+        const double ev[3] = {0.0, 0.0, 1.0};
+        double src[3], base[3], dp[3], dq[3];
+        for (int k = 0; k < 3; ++k) {
+            src[k] = (S[k] - d.off_origin[k]) / d.d_voxel[k] + 0.5 * (double)(d.n_voxel[k] - 1);
+            base[k] = (D[k] - S[k] + u0 * eu[k] + v0 * ev[k]) / d.d_voxel[k];
+            dp[k] = d.d_det[0] * eu[k] / d.d_voxel[k];
+            dq[k] = d.d_det[1] * ev[k] / d.d_voxel[k];
+        }
+        // Rays of one detector row spread along e_u: choose the memory layout
+        // whose fastest axis is the one e_u is closest to.
+        const int layout = std::fabs(c) > std::fabs(s) ? 1 : 0;
+        const int perm[3] = {layout ? 1 : 0, layout ? 0 : 1, 2};
+        FwdAngle& f = fwd[(size_t)a];
+        std::memset(&f, 0, sizeof(f));
+        for (int k = 0; k < 3; ++k) {
+            f.src[k] = (float)src[perm[k]];
+            f.base[k] = (float)base[perm[k]];
+            f.dp[k] = (float)dp[perm[k]];
+            f.dq[k] = (float)dq[perm[k]];
+        }
+        f.layout = layout;
+        g->layout[(size_t)a] = layout;
+        bp[(size_t)a] = BpAngle{(float)c, (float)s, (float)S[0], (float)S[1]};
+    }
+    TIGRE_TRY(g->fwd_params.ensure(sizeof(FwdAngle) * (size_t)na));
+    TIGRE_TRY(g->bp_params.ensure(sizeof(BpAngle) * (size_t)na));
+    TIGRE_CUDA(cudaMemcpy(g->fwd_params.ptr, fwd.data(), sizeof(FwdAngle) * (size_t)na,
+                          cudaMemcpyHostToDevice));
+    TIGRE_CUDA(cudaMemcpy(g->bp_params.ptr, bp.data(), sizeof(BpAngle) * (size_t)na,
+                          cudaMemcpyHostToDevice));
+    g->uploaded = true;
+    return TIGRE_OK;
+}
+
+}  // namespace tigre
+
+using namespace tigre;
+
+extern "C" {
+
+const char* tigre_last_error(void) { return g_last_error.c_str(); }
+
+tigre_status tigre_geometry_create(const tigre_geometry_desc* desc, const double* angles,
+                                   int64_t n_angles, tigre_geometry_t* out)
+{
+    if (!out) return fail(TIGRE_ERR_INVALID_ARG, "null output handle pointer");
+    *out = nullptr;
+    TIGRE_TRY(validate(desc, angles, n_angles));
+    tigre_geometry* g = new (std::nothrow) tigre_geometry();
+    if (!g) return fail(TIGRE_ERR_OOM, "host allocation failed");
+    g->desc = *desc;
+    g->angles.assign(angles, angles + n_angles);
+    cudaError_t e = cudaGetDevice(&g->device);
+    if (e != cudaSuccess) {
+        delete g;
+        return cuda_fail(e, "cudaGetDevice");
+    }
+    tigre_status st = upload_params(g);
+    if (st != TIGRE_OK) {
+        tigre_geometry_destroy(g);
+        return st;
+    }
+    *out = g;
+    set_error("");
+    return TIGRE_OK;
+}
+
+tigre_status tigre_geometry_destroy(tigre_geometry_t g)
+{
+    if (!g) return TIGRE_OK;
+    g->fwd_params.release();
+    g->bp_params.release();
+    g->vol_xy.release();
+    g->vol_yx.release();
+    g->proj_pad.release();
+    g->adj_xy.release();
+    g->adj_yx.release();
+    g->scratch_vol.release();
+    g->scratch_red.release();
+    delete g;
+    return TIGRE_OK;
+}
+
+tigre_status tigre_solver_opts_default(tigre_solver_opts* o)
+{
+    if (!o) return fail(TIGRE_ERR_INVALID_ARG, "null opts");
+    std::memset(o, 0, sizeof(*o));
+    o->n_iter = 10;
+    o->lambda = 1.0;
+    o->subset_size = 20;
+    o->tv_steps = 0;
+    o->tv_alpha = 0.002;
+    o->tv_eps = 1e-8;
+    o->bp_weight = TIGRE_BP_MATCHED;
+    o->nonneg = 0;
+    o->storage = TIGRE_F32;
+    o->device_budget_bytes = 0;
+    o->timeout_ms = 0;
+    o->flags = 0;
+    o->cuda_stream = nullptr;
+    return TIGRE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,268 @@
+"""Thin ctypes binding of libtigre103 (the C ABI in include/tigre103.h).
+
+Every function keeps the C name and only marshals arguments: torch tensors
+become device pointers plus a dtype code, streams become cudaStream_t
+handles, and a non-OK status raises TigreError with tigre_last_error().
+All computation happens in the CUDA library; there is no fallback path, and
+importing this module raises if the library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "lib", "libtigre103.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with "
+                      "`python -m paper_1905_03748_gb300.csrc.build` (no CPU fallback exists)")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+TIGRE_OK, TIGRE_ERR_INVALID_ARG, TIGRE_ERR_OOM, TIGRE_ERR_CUDA, TIGRE_ERR_TIMEOUT, \
+    TIGRE_ERR_UNSUPPORTED = range(6)
+TIGRE_F32, TIGRE_BF16, TIGRE_F16 = 0, 1, 2
+TIGRE_BP_MATCHED, TIGRE_BP_FDK, TIGRE_BP_EXACT_ADJOINT = 0, 1, 2
+TIGRE_HOST_RESIDENT = 0x1
+TIGRE_GRAPH = 0x2
+
+EXPORTED = ["tigre_geometry_create", "tigre_geometry_destroy", "tigre_forward", "tigre_backward",
+            "tigre_tv_step", "tigre_solver_opts_default", "tigre_sirt", "tigre_sart",
+            "tigre_cgls", "tigre_last_error"]
+
+_DTYPES = {torch.float32: TIGRE_F32, torch.bfloat16: TIGRE_BF16, torch.float16: TIGRE_F16}
+_BP = {"matched": TIGRE_BP_MATCHED, "fdk": TIGRE_BP_FDK, "adjoint": TIGRE_BP_EXACT_ADJOINT}
+
+
+class tigre_geometry_desc(ctypes.Structure):
+    _fields_ = [("DSO", ctypes.c_double), ("DSD", ctypes.c_double),
+                ("n_voxel", ctypes.c_int64 * 3), ("d_voxel", ctypes.c_double * 3),
+                ("off_origin", ctypes.c_double * 3), ("n_det", ctypes.c_int64 * 2),
+                ("d_det", ctypes.c_double * 2), ("off_det", ctypes.c_double * 2),
+                ("accuracy", ctypes.c_double)]
+
+
+class tigre_solver_opts(ctypes.Structure):
+    _fields_ = [("n_iter", ctypes.c_int), ("lambda_", ctypes.c_double),
+                ("subset_size", ctypes.c_int), ("tv_steps", ctypes.c_int),
+                ("tv_alpha", ctypes.c_double), ("tv_eps", ctypes.c_double),
+                ("bp_weight", ctypes.c_int), ("nonneg", ctypes.c_int), ("storage", ctypes.c_int),
+                ("device_budget_bytes", ctypes.c_int64), ("timeout_ms", ctypes.c_int64),
+                ("flags", ctypes.c_uint32), ("cuda_stream", ctypes.c_void_p)]
+
+
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_ST = ctypes.c_int
+_sigs = {
+    "tigre_geometry_create": [ctypes.POINTER(tigre_geometry_desc), _P, _I64, ctypes.POINTER(_P)],
+    "tigre_geometry_destroy": [_P],
+    "tigre_forward": [_P, _P, ctypes.c_int, _P, ctypes.c_int, _I64, _I64, _P],
+    "tigre_backward": [_P, _P, ctypes.c_int, _P, ctypes.c_int, _I64, _I64, ctypes.c_int, _P],
+    "tigre_tv_step": [_P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, _P],
+    "tigre_solver_opts_default": [ctypes.POINTER(tigre_solver_opts)],
+    "tigre_sirt": [_P, _P, _P, ctypes.POINTER(tigre_solver_opts), _P],
+    "tigre_sart": [_P, _P, _P, ctypes.POINTER(tigre_solver_opts), _P],
+    "tigre_cgls": [_P, _P, _P, ctypes.POINTER(tigre_solver_opts), _P],
+}
+for _name, _args in _sigs.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = _ST
+_lib.tigre_last_error.argtypes = []
+_lib.tigre_last_error.restype = ctypes.c_char_p
+
+
+class TigreError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"tigre status {status}: {msg}")
+        self.status = status
+
+
+def tigre_last_error() -> str:
+    return _lib.tigre_last_error().decode()
+
+
+def _check(status: int):
+    if status != TIGRE_OK:
+        raise TigreError(status, tigre_last_error())
+
+
+def _stream(stream) -> ctypes.c_void_p:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    if isinstance(stream, torch.cuda.Stream):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _dev(t: torch.Tensor, name: str):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if t.dtype not in _DTYPES:
+        raise TypeError(f"{name}: unsupported dtype {t.dtype}")
+    return ctypes.c_void_p(t.data_ptr()), _DTYPES[t.dtype]
+
+
+def make_desc(geo: dict) -> tigre_geometry_desc:
+    d = tigre_geometry_desc()
+    d.DSO, d.DSD = geo["DSO"], geo["DSD"]
+    for i in range(3):
+        d.n_voxel[i] = int(geo["n_voxel"][i])
+        d.d_voxel[i] = float(geo["d_voxel"][i])
+        d.off_origin[i] = float(geo["off_origin"][i])
+    for i in range(2):
+        d.n_det[i] = int(geo["n_det"][i])
+        d.d_det[i] = float(geo["d_det"][i])
+        d.off_det[i] = float(geo["off_det"][i])
+    d.accuracy = float(geo["accuracy"])
+    return d
+
+
+# ------------------------------------------------------------- the C names
+
+def tigre_geometry_create(geo: dict, angles) -> ctypes.c_void_p:
+    ang = np.ascontiguousarray(angles, dtype=np.float64)
+    h = ctypes.c_void_p()
+    desc = make_desc(geo)
+    _check(_lib.tigre_geometry_create(ctypes.byref(desc), ang.ctypes.data_as(_P), len(ang),
+                                      ctypes.byref(h)))
+    return h
+
+
+def tigre_geometry_destroy(handle) -> None:
+    _check(_lib.tigre_geometry_destroy(handle))
+
+
+def tigre_forward(handle, vol: torch.Tensor, proj: torch.Tensor, angle_begin: int,
+                  angle_count: int, stream=None) -> None:
+    vp, vt = _dev(vol, "vol")
+    pp, pt = _dev(proj, "proj")
+    _check(_lib.tigre_forward(handle, vp, vt, pp, pt, int(angle_begin), int(angle_count),
+                              _stream(stream)))
+
+
+def tigre_backward(handle, proj: torch.Tensor, vol: torch.Tensor, angle_begin: int,
+                   angle_count: int, weight="matched", stream=None) -> None:
+    pp, pt = _dev(proj, "proj")
+    vp, vt = _dev(vol, "vol")
+    w = _BP[weight] if isinstance(weight, str) else int(weight)
+    _check(_lib.tigre_backward(handle, pp, pt, vp, vt, int(angle_begin), int(angle_count), w,
+                               _stream(stream)))
+
+
+def tigre_tv_step(vol: torch.Tensor, n_steps: int, alpha: float, eps: float,
+                  stream=None) -> None:
+    vp, vt = _dev(vol, "vol")
+    nz, ny, nx = vol.shape
+    n = (ctypes.c_int64 * 3)(nx, ny, nz)
+    _check(_lib.tigre_tv_step(n, vp, vt, int(n_steps), float(alpha), float(eps),
+                              _stream(stream)))
+
+
+def tigre_solver_opts_default() -> tigre_solver_opts:
+    o = tigre_solver_opts()
+    _check(_lib.tigre_solver_opts_default(ctypes.byref(o)))
+    return o
+
+
+def _solver(fn, handle, proj, vol, opts: tigre_solver_opts, host: bool):
+    hist = np.zeros(max(opts.n_iter, 1), dtype=np.float64)
+    if host:
+        for t, name in ((proj, "proj"), (vol, "vol")):
+            if t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
+                raise TypeError(f"{name} must be a contiguous float32 host tensor")
+        opts.flags |= TIGRE_HOST_RESIDENT
+        pp, vp = ctypes.c_void_p(proj.data_ptr()), ctypes.c_void_p(vol.data_ptr())
+    else:
+        pp, _ = _dev(proj, "proj")
+        vp, _ = _dev(vol, "vol")
+    _check(fn(handle, pp, vp, ctypes.byref(opts), hist.ctypes.data_as(_P)))
+    return hist[:opts.n_iter]
+
+
+def _opts(n_iter, stream, **kw) -> tigre_solver_opts:
+    o = tigre_solver_opts_default()
+    o.n_iter = int(n_iter)
+    o.cuda_stream = _stream(stream).value
+    for k, v in kw.items():
+        if v is None:
+            continue
+        if k == "bp_weight" and isinstance(v, str):
+            v = _BP[v]
+        setattr(o, "lambda_" if k == "lam" else k, v)
+    return o
+
+
+def tigre_sirt(handle, proj, vol, n_iter, lam=1.0, nonneg=False, bp_weight="matched",
+               stream=None, host=False) -> np.ndarray:
+    o = _opts(n_iter, stream, lam=lam, nonneg=int(nonneg), bp_weight=bp_weight)
+    return _solver(_lib.tigre_sirt, handle, proj, vol, o, host)
+
+
+def tigre_sart(handle, proj, vol, n_iter, subset_size=20, lam=1.0, nonneg=False, tv_steps=0,
+               tv_alpha=0.002, tv_eps=1e-8, bp_weight="matched", stream=None,
+               host=False) -> np.ndarray:
+    o = _opts(n_iter, stream, lam=lam, nonneg=int(nonneg), subset_size=int(subset_size),
+              tv_steps=int(tv_steps), tv_alpha=float(tv_alpha), tv_eps=float(tv_eps),
+              bp_weight=bp_weight)
+    return _solver(_lib.tigre_sart, handle, proj, vol, o, host)
+
+
+def tigre_cgls(handle, proj, vol, n_iter, bp_weight="matched", stream=None,
+               host=False) -> np.ndarray:
+    o = _opts(n_iter, stream, bp_weight=bp_weight)
+    return _solver(_lib.tigre_cgls, handle, proj, vol, o, host)
+
+
+# ------------------------------------------------------------ convenience
+
+class Geometry:
+    """Owns a geometry handle; shapes of its volume and projections."""
+
+    def __init__(self, geo: dict, angles):
+        self.geo = dict(geo)
+        self.angles = np.ascontiguousarray(angles, dtype=np.float64)
+        self.handle = tigre_geometry_create(self.geo, self.angles)
+        nx, ny, nz = self.geo["n_voxel"]
+        nu, nv = self.geo["n_det"]
+        self.vol_shape = (nz, ny, nx)
+        self.proj_shape = (len(self.angles), nv, nu)
+
+    def close(self):
+        if self.handle is not None:
+            tigre_geometry_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def forward(self, vol, out=None, angle_begin=0, angle_count=None, dtype=None, stream=None):
+        na = len(self.angles) - angle_begin if angle_count is None else angle_count
+        if out is None:
+            out = torch.empty((na,) + self.proj_shape[1:], device=vol.device,
+                              dtype=dtype or vol.dtype)
+        tigre_forward(self.handle, vol, out, angle_begin, na, stream)
+        return out
+
+    def backward(self, proj, out=None, angle_begin=0, weight="matched", dtype=None, stream=None):
+        na = proj.shape[0]
+        if out is None:
+            out = torch.empty(self.vol_shape, device=proj.device, dtype=dtype or proj.dtype)
+        tigre_backward(self.handle, proj, out, angle_begin, na, weight, stream)
+        return out
