@@ -1,0 +1,329 @@
+#!/usr/bin/env python
+"""Benchmark of the iterative cone-beam CT hot path.
+
+Workload (default): 512^3 float32 volume of 0.5 mm voxels holding 50 seeded
+random ellipsoids, 512^2 detector, 360 angles over 360 degrees, DSO 1000 mm,
+DSD 1536 mm; b = A x_true.  One step = one CGLS iteration: a forward
+projection A p, a matched backprojection A^T r and the FP64 inner products
+and vector updates, all resident on the GPU.
+
+Metric: Gvoxel*angles/s = 2 * 512^3 * 360 per step / step time (each
+operator visits every voxel-angle pair once), plus CGLS s/iter and the
+per-operator rates.  Multi-GPU (torchrun): every rank reconstructs its own
+problem (independent reconstructions, no data-path collective); the value is
+the sum of the work over the max step time across ranks.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Ax/Aᵀy Gvoxel·angles/s and CGLS s/iter at 512³×360"
+UNIT = "Gvoxel*angles/s"
+FLOPS_PER_SAMPLE = 22  # trilinear interpolation: 7 lerps x 3 flops + 1 accumulation
+KERNEL_SOURCES = ["paper_1905_03748_gb300/csrc/forward.cu", "paper_1905_03748_gb300/csrc/ray.cuh"]
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "fwd_kernel_traffic.json")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-iters", type=int, default=20, help="CGLS iterations per e2e call")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-angles", type=int, default=6,
+                    help="angles of the workload in the bounded CPU-oracle sample")
+    return ap.parse_args()
+
+
+def workload():
+    from paper_1905_03748_gb300 import synth
+    geo, ang = synth.workload("cgls_512")
+    return geo, ang
+
+
+def config_dict(geo, ang):
+    nx, ny, nz = geo["n_voxel"]
+    nu, nv = geo["n_det"]
+    return {"workload": f"CGLS at {nx}x{ny}x{nz} float32 vol (0.5 mm), {nu}x{nv} det "
+                        f"({geo['d_det'][0]:.4f} mm), {len(ang)} angles, DSO 1000 / DSD 1536 mm",
+            "step": "one CGLS iteration (Ax + matched A^T y + FP64 dots/updates)",
+            "l2": "inputs larger than L2 (vol 512 MiB, proj 360 MiB > 126 MB L2): no flush",
+            "phantom": "50 seeded random ellipsoids (seed 2), b = A x_true"}
+
+
+def source_hash() -> str:
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        self.out = ""
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in (self.out or "").splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_init(backend):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return 0, 1, None
+    import torch.distributed as dist
+    dist.init_process_group(backend=backend)
+    return dist.get_rank(), ws, dist
+
+
+def cpu_baseline(geo, ang, x_true, n_angles):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload:
+    one forward projection and one matched backprojection over the first
+    n_angles angles (the per-step operators of CGLS)."""
+    import oracle
+    oracle.build()
+    sub = ang[:n_angles]
+    xv = np.asarray(x_true, dtype=np.float64)
+    t0 = time.perf_counter()
+    p = oracle.forward(geo, sub, xv)
+    oracle.backward(geo, sub, p, oracle.BP_MATCHED)
+    dt = time.perf_counter() - t0
+    nvox = int(np.prod(geo["n_voxel"]))
+    return {"value": 2.0 * nvox * n_angles / dt / 1e9, "unit": UNIT, "cores": os.cpu_count(),
+            "kind": "oracle",
+            "sample": f"FP64 oracle Ax + matched A^T y over {n_angles} of {len(ang)} angles of "
+                      f"the 512^3 workload ({dt:.1f} s)"}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle timed on the host cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_1905_03748_gb300 import synth
+    geo, ang = workload()
+    x_true = synth.phantom("ellipsoids50", 512, 0.5, seed=2, dtype=np.float64)
+    import oracle
+    oracle.build()
+    n_sub = 2
+    nvox = int(np.prod(geo["n_voxel"]))
+
+    def step(i):
+        sub = ang[(2 * i) % len(ang):(2 * i) % len(ang) + n_sub]
+        p = oracle.forward(geo, sub, x_true)
+        oracle.backward(geo, sub, p, oracle.BP_MATCHED)
+
+    for i in range(args.warmup):
+        step(i)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        step(args.warmup + i)
+    dt = (time.perf_counter() - t0) / args.steps
+    value = 2.0 * nvox * n_sub / dt / 1e9
+    sample = (f"each step: FP64 oracle Ax + matched A^T y over {n_sub} of {len(ang)} angles "
+              f"of the 512^3 workload")
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config_dict(geo, ang),
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(),
+                            "kind": "oracle", "sample": sample},
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def run_ours(args):
+    import torch
+    from paper_1905_03748_gb300 import synth, tigre
+
+    rank, world, dist = dist_init("nccl")
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    geo, ang = workload()
+    nx, ny, nz = geo["n_voxel"]
+    nvox = nx * ny * nz
+    x_np = synth.phantom("ellipsoids50", 512, 0.5, seed=2 + rank)
+    G = tigre.Geometry(geo, ang)
+    x_true = torch.from_numpy(x_np).to(dev)
+    b = G.forward(x_true)
+    torch.cuda.synchronize()
+    x = torch.zeros(G.vol_shape, device=dev)
+    state = tigre.tigre_cgls_begin(G.handle, b, x, n_iter_hint=args.warmup + args.steps)
+    tigre.tigre_cgls_iterate(state, args.warmup)
+    torch.cuda.synchronize()
+
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        tigre.tigre_profile_enable(True)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        tigre.tigre_cgls_iterate(state, args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+    launches = tigre.tigre_launch_count()
+    fwd_n, fwd_ms = tigre.tigre_profile_read(tigre.PROF_FORWARD)
+    bp_n, bp_ms = tigre.tigre_profile_read(tigre.PROF_BACKPROJECT)
+    tigre.tigre_profile_enable(False)
+    ms = e0.elapsed_time(e1) / args.steps
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    hist = tigre.tigre_cgls_history(state, args.warmup + args.steps)
+    tigre.tigre_cgls_end(state)
+
+    vox_ang = float(nvox) * len(ang)
+    value = world * 2.0 * vox_ang / (ms / 1e3) / 1e9
+    samples = tigre.tigre_forward_samples(G.handle, 0, len(ang))
+    fwd_avg = fwd_ms / max(fwd_n, 1)
+    bp_avg = bp_ms / max(bp_n, 1)
+    peaks = measured_peaks()
+    sm_max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = 152 * 128 * 2 * sm_max_mhz * 1e6 / 1e12  # TFLOP/s, FMA = 2 flops
+    achieved = samples * FLOPS_PER_SAMPLE / (fwd_avg / 1e3) / 1e12
+    traffic = None
+    try:
+        with open(TRAFFIC_FILE) as f:
+            tr = json.load(f)
+        if tr.get("source_hash") == source_hash():
+            traffic = tr.get("dram_bytes_per_launch")
+    except Exception:
+        pass
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config_dict(geo, ang),
+           "cgls_s_per_iter": ms / 1e3,
+           "ax_kernel_gvox_ang_s": vox_ang / (fwd_avg / 1e3) / 1e9,
+           "atb_kernel_gvox_ang_s": vox_ang / (bp_avg / 1e3) / 1e9,
+           "ax_gsamples_s": samples / (fwd_avg / 1e3) / 1e9,
+           "samples_per_ax": samples,
+           "kernel_ms": {"forward": fwd_avg, "backproject_matched": bp_avg},
+           "resid_last": float(hist[-1]) if len(hist) else None,
+           "roofline": {"kernel": "fwd_l1_kernel", "bound": "alu", "achieved": achieved,
+                        "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+                        "traffic": traffic,
+                        "per_unit": f"{FLOPS_PER_SAMPLE} FP32 flops per quadrature sample "
+                                    f"x {samples} samples per launch",
+                        "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock "
+                                       f"{sm_max_mhz:.0f} MHz (derived)"},
+           "gpu_launches": launches, "clocks": clk.summary(),
+           "paper_context": "CGLS 512^3, 15 it in 61 s (4.1 s/iter incl. host copies), "
+                            "1x GTX 1080 Ti (Sec. 4); detector/angles not stated"}
+
+    if not args.no_e2e:
+        n_e2e = args.e2e_iters
+        bh = b.cpu().pin_memory()
+        xh = torch.zeros(G.vol_shape).pin_memory()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        tigre.tigre_cgls(G.handle, bh, xh, n_e2e, host=True)
+        dt = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([dt], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        out["e2e"] = {"value": world * 2.0 * vox_ang * n_e2e / dt / 1e9, "unit": UNIT,
+                      "h2d_bytes_per_step": bh.numel() * 4 + xh.numel() * 4,
+                      "d2h_bytes_per_step": xh.numel() * 4,
+                      "step": f"tigre_cgls call on pinned host buffers: copy b and x0 in, "
+                              f"{n_e2e} CGLS iterations (+ initial Ax, A^T r), copy x out",
+                      "s_per_call": dt}
+    if rank == 0 and world == 1 and not args.no_cpu:
+        out["cpu_baseline"] = cpu_baseline(geo, ang, x_np, args.cpu_angles)
+    G.close()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -174,6 +174,40 @@ TIGRE_API tigre_status tigre_sart(tigre_geometry_t geo, const void* proj, void* 
 TIGRE_API tigre_status tigre_cgls(tigre_geometry_t geo, const void* proj, void* vol,
                         const tigre_solver_opts* opts, double* resid_hist);
 
+/* Stepwise CGLS (the same iteration as tigre_cgls) for callers that
+ * interleave several reconstructions or time single iterations.
+ * begin: device proj (b) and vol (x0, updated in place) must stay valid until
+ *        end; computes r = b - A x0, p = A^T r, gamma = ||p||^2 and allocates
+ *        the workspace (2 projection- and 2 volume-sized FP32 buffers) stream-
+ *        ordered on opts->cuda_stream.  TIGRE_HOST_RESIDENT is not accepted.
+ * iterate: enqueues n_iter iterations on that stream (no host sync).
+ * history: copies the first n residual norms (n <= iterations done) to the
+ *        host, synchronising the stream.
+ * end:   releases the workspace (stream-ordered) and the handle. */
+typedef struct tigre_cgls_state* tigre_cgls_t;
+TIGRE_API tigre_status tigre_cgls_begin(tigre_geometry_t geo, const void* proj, void* vol,
+                                        const tigre_solver_opts* opts, tigre_cgls_t* out);
+TIGRE_API tigre_status tigre_cgls_iterate(tigre_cgls_t state, int n_iter);
+TIGRE_API tigre_status tigre_cgls_history(tigre_cgls_t state, double* resid_hist, int n);
+TIGRE_API tigre_status tigre_cgls_end(tigre_cgls_t state);
+
+/* Total quadrature samples (sum of K over rays) of tigre_forward for the
+ * angle range: the algorithmic work of one forward projection.  Runs a
+ * ray-setup kernel on the current device and synchronises. */
+TIGRE_API tigre_status tigre_forward_samples(tigre_geometry_t geo, int64_t angle_begin,
+                                             int64_t angle_count, int64_t* samples);
+
+/* Profiling: tigre_profile_enable(1) resets the counters and starts timing
+ * the main kernel of each operator call with CUDA events on its stream;
+ * tigre_profile_read(kind, ...) waits for the recorded events and returns the
+ * number of timed calls and their total device time.  kind: 0 forward
+ * projection, 1 voxel-driven backprojection, 2 exact-adjoint scatter, 3 TV
+ * step.  tigre_launch_count() is the number of kernels the library launched
+ * since the last tigre_profile_enable. */
+TIGRE_API tigre_status tigre_profile_enable(int on);
+TIGRE_API tigre_status tigre_profile_read(int kind, int64_t* calls, double* total_ms);
+TIGRE_API int64_t tigre_launch_count(void);
+
 /* Message describing the last failure on the calling thread ("" if none). */
 TIGRE_API const char* tigre_last_error(void);
 

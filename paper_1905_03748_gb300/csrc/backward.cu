@@ -287,6 +287,7 @@ static tigre_status launch_voxel_bp(tigre_geometry* g, const TP* proj, TV* vol, 
     const BpAngle* params = (const BpAngle*)g->bp_params.ptr;
     const TP* pp = (const TP*)g->proj_pad.ptr;
     const dim3 block(32, 8);
+    ProfScope prof(kProfBackproject, st);
     if (sart) {
         if (w == TIGRE_BP_FDK)
             bp_voxel_kernel<TP, TV, kBpNZ, TIGRE_BP_FDK, true><<<grid, block, 0, st>>>(
@@ -335,6 +336,7 @@ static tigre_status launch_adjoint(tigre_geometry* g, const TP* proj, TV* vol, i
     }
     float* axy = need[0] ? (float*)g->adj_xy.ptr : nullptr;
     float* ayx = need[1] ? (float*)g->adj_yx.ptr : nullptr;
+    ProfScope prof(kProfAdjoint, st);
     for (int64_t s = 0; s < na; s += 65535) {
         const int64_t cnt = std::min<int64_t>(65535, na - s);
         dim3 grid((unsigned)((c.nu + 31) / 32), (unsigned)cnt, (unsigned)((c.nv + 7) / 8));

@@ -31,12 +31,32 @@ tigre_status cuda_fail(cudaError_t err, const char* what);
         if (s_ != TIGRE_OK) return s_;             \
     } while (0)
 
-// Check for a launch error right after a kernel launch.
+// Count a kernel launch and check for a launch error right after it.
+void count_launch();
 #define TIGRE_LAUNCHED(name)                                           \
     do {                                                               \
+        ::tigre::count_launch();                                       \
         cudaError_t e_ = cudaGetLastError();                           \
         if (e_ != cudaSuccess) return ::tigre::cuda_fail(e_, name);    \
     } while (0)
+
+// Kernel classes timed by tigre_profile_read.
+enum ProfKind { kProfForward = 0, kProfBackproject = 1, kProfAdjoint = 2, kProfTV = 3, kProfKinds = 4 };
+bool profiling();
+// Records CUDA events around a scope on `st` while profiling is enabled.
+class ProfScope {
+public:
+    ProfScope(int kind, cudaStream_t st);
+    ~ProfScope();
+    ProfScope(const ProfScope&) = delete;
+    ProfScope& operator=(const ProfScope&) = delete;
+
+private:
+    int kind_;
+    cudaStream_t st_;
+    cudaEvent_t a_{}, b_{};
+    bool active_ = false;
+};
 
 inline size_t dtype_size(tigre_dtype t) { return t == TIGRE_F32 ? 4 : 2; }
 inline bool dtype_ok(tigre_dtype t) { return t == TIGRE_F32 || t == TIGRE_BF16 || t == TIGRE_F16; }

@@ -213,6 +213,7 @@ tigre_status forward_impl(tigre_geometry* g, const void* vol, tigre_dtype vt, vo
         }
         return dispatch_dtype(pt, [&](auto ptag) -> tigre_status {
             using TP = decltype(ptag);
+            ProfScope prof(kProfForward, st);
             const int64_t step = 65535;
             for (int64_t s = 0; s < na; s += step) {
                 const int64_t cnt = std::min(step, na - s);
@@ -228,7 +229,53 @@ tigre_status forward_impl(tigre_geometry* g, const void* vol, tigre_dtype vt, vo
     });
 }
 
+// Sum of K over the rays of a launch-sized block of angles (ray setup only).
+__global__ void __launch_bounds__(256) sample_count_kernel(const FwdAngle* __restrict__ params,
+                                                           FwdConst c, int a_first,
+                                                           unsigned long long* total)
+{
+    const int p = blockIdx.x * 32 + threadIdx.x;
+    const int q = blockIdx.z * blockDim.y + threadIdx.y;
+    const int a = blockIdx.y;
+    int K = 0;
+    if (p < c.nu && q < c.nv) {
+        Ray R;
+        setup_ray(params + a_first + a, c, p, q, R);
+        K = R.ok ? R.K : 0;
+    }
+    for (int o = 16; o > 0; o >>= 1) K += __shfl_down_sync(0xffffffffu, K, o);
+    if ((threadIdx.x & 31) == 0 && K) atomicAdd(total, (unsigned long long)K);
+}
+
 }  // namespace tigre
+
+extern "C" tigre_status tigre_forward_samples(tigre_geometry_t g, int64_t angle_begin,
+                                              int64_t angle_count, int64_t* samples)
+{
+    using namespace tigre;
+    TIGRE_TRY(check_geometry(g));
+    TIGRE_TRY(check_range(g, angle_begin, angle_count));
+    if (!samples) return fail(TIGRE_ERR_INVALID_ARG, "null output");
+    const FwdConst c = make_fwd_const(g->desc);
+    unsigned long long* d = nullptr;
+    TIGRE_CUDA(cudaMalloc(&d, sizeof(unsigned long long)));
+    tigre_status st = TIGRE_OK;
+    cudaError_t e = cudaMemset(d, 0, sizeof(unsigned long long));
+    for (int64_t s = 0; e == cudaSuccess && s < angle_count; s += 65535) {
+        const int64_t cnt = std::min<int64_t>(65535, angle_count - s);
+        dim3 grid((unsigned)((c.nu + 31) / 32), (unsigned)cnt, (unsigned)((c.nv + 7) / 8));
+        sample_count_kernel<<<grid, dim3(32, 8)>>>((const FwdAngle*)g->fwd_params.ptr, c,
+                                                   (int)(angle_begin + s), d);
+        count_launch();
+        e = cudaGetLastError();
+    }
+    unsigned long long h = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&h, d, sizeof(h), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) st = cuda_fail(e, "tigre_forward_samples");
+    cudaFree(d);
+    *samples = (int64_t)h;
+    return st;
+}
 
 extern "C" tigre_status tigre_forward(tigre_geometry_t geo, const void* vol, tigre_dtype vol_dtype,
                                       void* proj, tigre_dtype proj_dtype, int64_t angle_begin,

@@ -12,8 +12,10 @@
 // With TIGRE_HOST_RESIDENT the projections and the volume are host pointers:
 // they are staged to the device once, solved in-core, and the result copied
 // back (the whole problem must fit the device memory).
+#include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <new>
 
 #include "vecops.cuh"
 
@@ -179,49 +181,136 @@ tigre_status run_sart(const Problem& P, int64_t subset, double* h_hist)
     return finish_history(hist, h_hist, o->n_iter, P.st);
 }
 
-tigre_status run_cgls(const Problem& P, double* h_hist)
+}  // namespace
+
+}  // namespace tigre
+
+// CGLS state: x_{k+1} = x_k + alpha p_k, r_{k+1} = r_k - alpha q_k,
+// alpha = gamma_k / ||A p_k||^2, s = A^T r_{k+1}, p_{k+1} = s + (gamma_{k+1}/gamma_k) p_k,
+// gamma = ||s||^2; gamma alternates between two device slots.
+struct tigre_cgls_state {
+    tigre_geometry* g = nullptr;
+    tigre_bp_weight bw = TIGRE_BP_MATCHED;
+    cudaStream_t st = nullptr;
+    int64_t nvox = 0, m = 0, na = 0;
+    const float* b = nullptr;
+    float* x = nullptr;
+    float *r = nullptr, *q = nullptr, *p = nullptr, *s = nullptr;
+    double* sc = nullptr;    // Scalars area
+    double* hist = nullptr;  // residual norms, capacity hist_cap
+    int hist_cap = 0;
+    int done = 0;
+    int cur = 0;
+};
+
+namespace tigre {
+namespace {
+
+void cgls_release(tigre_cgls_state* S)
 {
-    const tigre_solver_opts* o = P.o;
-    const tigre_bp_weight bw = o->bp_weight;
-    Scratch s(P.st);
-    float *r, *q, *p, *sv;
-    double *sc_base, *hist;
-    TIGRE_TRY(s.alloc(&r, (size_t)(P.npix * P.na)));
-    TIGRE_TRY(s.alloc(&q, (size_t)(P.npix * P.na)));
-    TIGRE_TRY(s.alloc(&p, (size_t)P.nvox));
-    TIGRE_TRY(s.alloc(&sv, (size_t)P.nvox));
-    TIGRE_TRY(s.alloc(&sc_base, Scalars::count(4)));
-    TIGRE_TRY(s.alloc(&hist, (size_t)std::max(o->n_iter, 1)));
-    Scalars sc{sc_base};
+    for (void* ptr : {(void*)S->r, (void*)S->q, (void*)S->p, (void*)S->s, (void*)S->sc,
+                      (void*)S->hist})
+        if (ptr) cudaFreeAsync(ptr, S->st);
+    delete S;
+}
+
+template <typename T>
+tigre_status dalloc(T** out, size_t count, cudaStream_t st)
+{
+    void* ptr = nullptr;
+    cudaError_t e = cudaMallocAsync(&ptr, sizeof(T) * (count ? count : 1), st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return cuda_fail(e, "cudaMallocAsync(cgls workspace)");
+    }
+    *out = (T*)ptr;
+    return TIGRE_OK;
+}
+
+tigre_status cgls_init(tigre_cgls_state* S, int hist_cap)
+{
+    TIGRE_TRY(dalloc(&S->r, (size_t)S->m, S->st));
+    TIGRE_TRY(dalloc(&S->q, (size_t)S->m, S->st));
+    TIGRE_TRY(dalloc(&S->p, (size_t)S->nvox, S->st));
+    TIGRE_TRY(dalloc(&S->s, (size_t)S->nvox, S->st));
+    TIGRE_TRY(dalloc(&S->sc, Scalars::count(4), S->st));
+    S->hist_cap = std::max(hist_cap, 16);
+    TIGRE_TRY(dalloc(&S->hist, (size_t)S->hist_cap, S->st));
+    Scalars sc{S->sc};
+    // r = b - A x0; p = A^T r; gamma = ||p||^2
+    TIGRE_TRY(forward_impl(S->g, S->x, TIGRE_F32, S->q, TIGRE_F32, 0, S->na, S->st));
+    TIGRE_TRY(weighted_residual(S->b, S->q, nullptr, S->r, S->m, sc.partials(), sc.slot(3), S->st));
+    TIGRE_TRY(backward_impl(S->g, S->r, TIGRE_F32, S->p, TIGRE_F32, 0, S->na, S->bw, 0, S->st));
+    TIGRE_TRY(dot_f64(S->p, S->p, S->nvox, sc.partials(), sc.slot(0), S->st));
+    S->cur = 0;
+    return TIGRE_OK;
+}
+
+tigre_status cgls_step(tigre_cgls_state* S)
+{
+    if (S->done == S->hist_cap) {  // grow the history, stream-ordered
+        double* nh = nullptr;
+        TIGRE_TRY(dalloc(&nh, (size_t)S->hist_cap * 2, S->st));
+        TIGRE_CUDA(cudaMemcpyAsync(nh, S->hist, sizeof(double) * (size_t)S->hist_cap,
+                                   cudaMemcpyDeviceToDevice, S->st));
+        cudaFreeAsync(S->hist, S->st);
+        S->hist = nh;
+        S->hist_cap *= 2;
+    }
+    Scalars sc{S->sc};
     double* gam[2] = {sc.slot(0), sc.slot(1)};
     double* qq = sc.slot(2);
     double* rr = sc.slot(3);
-    const int64_t m = P.npix * P.na;
+    const int c = S->cur;
+    TIGRE_TRY(forward_impl(S->g, S->p, TIGRE_F32, S->q, TIGRE_F32, 0, S->na, S->st));
+    TIGRE_TRY(dot_f64(S->q, S->q, S->m, sc.partials(), qq, S->st));
+    // alpha = gamma / ||q||^2: x += alpha p, r -= alpha q
+    TIGRE_TRY(axpy_ratio(S->x, S->p, S->nvox, gam[c], qq, 1.0f, S->st));
+    TIGRE_TRY(axpy_ratio_norm(S->r, S->q, S->m, gam[c], qq, -1.0f, sc.partials(), rr, S->st));
+    TIGRE_TRY(copy_dscalar(S->hist + S->done, rr + 1, S->st));
+    TIGRE_TRY(backward_impl(S->g, S->r, TIGRE_F32, S->s, TIGRE_F32, 0, S->na, S->bw, 0, S->st));
+    TIGRE_TRY(dot_f64(S->s, S->s, S->nvox, sc.partials(), gam[1 - c], S->st));
+    // p = s + (gamma_new / gamma) p
+    TIGRE_TRY(xpay_ratio(S->p, S->s, S->nvox, gam[1 - c], gam[c], S->st));
+    S->cur = 1 - c;
+    S->done += 1;
+    return TIGRE_OK;
+}
 
-    // r = b - A x0; p = A^T r; gamma = ||p||^2
-    TIGRE_TRY(forward_impl(P.g, P.x, TIGRE_F32, q, TIGRE_F32, 0, P.na, P.st));
-    TIGRE_TRY(weighted_residual(P.b, q, nullptr, r, m, sc.partials(), rr, P.st));
-    TIGRE_TRY(backward_impl(P.g, r, TIGRE_F32, p, TIGRE_F32, 0, P.na, bw, 0, P.st));
-    TIGRE_TRY(dot_f64(p, p, P.nvox, sc.partials(), gam[0], P.st));
-    int cur = 0;
-    for (int it = 0; it < o->n_iter; ++it) {
-        TIGRE_TRY(forward_impl(P.g, p, TIGRE_F32, q, TIGRE_F32, 0, P.na, P.st));
-        TIGRE_TRY(dot_f64(q, q, m, sc.partials(), qq, P.st));
-        // alpha = gamma / ||q||^2: x += alpha p, r -= alpha q
-        TIGRE_TRY(axpy_ratio(P.x, p, P.nvox, gam[cur], qq, 1.0f, P.st));
-        TIGRE_TRY(axpy_ratio_norm(r, q, m, gam[cur], qq, -1.0f, sc.partials(), rr, P.st));
-        TIGRE_TRY(copy_dscalar(hist + it, rr + 1, P.st));
-        TIGRE_TRY(backward_impl(P.g, r, TIGRE_F32, sv, TIGRE_F32, 0, P.na, bw, 0, P.st));
-        TIGRE_TRY(dot_f64(sv, sv, P.nvox, sc.partials(), gam[1 - cur], P.st));
-        // p = s + (gamma_new / gamma) p
-        TIGRE_TRY(xpay_ratio(p, sv, P.nvox, gam[1 - cur], gam[cur], P.st));
-        cur = 1 - cur;
+tigre_status cgls_begin_device(tigre_geometry* g, const float* b, float* x,
+                               const tigre_solver_opts* o, tigre_cgls_state** out)
+{
+    tigre_cgls_state* S = new (std::nothrow) tigre_cgls_state();
+    if (!S) return fail(TIGRE_ERR_OOM, "host allocation failed");
+    S->g = g;
+    S->bw = o->bp_weight;
+    S->st = (cudaStream_t)o->cuda_stream;
+    S->nvox = n_vox(g);
+    S->na = (int64_t)g->angles.size();
+    S->m = n_pix(g) * S->na;
+    S->b = b;
+    S->x = x;
+    tigre_status st = cgls_init(S, o->n_iter);
+    if (st != TIGRE_OK) {
+        cgls_release(S);
+        return st;
     }
-    return finish_history(hist, h_hist, o->n_iter, P.st);
+    *out = S;
+    return TIGRE_OK;
+}
+
+tigre_status run_cgls(const Problem& P, double* h_hist)
+{
+    tigre_cgls_state* S = nullptr;
+    TIGRE_TRY(cgls_begin_device(P.g, P.b, P.x, P.o, &S));
+    tigre_status st = TIGRE_OK;
+    for (int it = 0; it < P.o->n_iter && st == TIGRE_OK; ++it) st = cgls_step(S);
+    if (st == TIGRE_OK) st = finish_history(S->hist, h_hist, P.o->n_iter, P.st);
+    cgls_release(S);
+    return st;
 }
 
 }  // namespace
-
 }  // namespace tigre
 
 using namespace tigre;
@@ -249,6 +338,38 @@ tigre_status tigre_cgls(tigre_geometry_t geo, const void* proj, void* vol,
 {
     return with_device_problem(geo, proj, vol, opts,
                                [&](const Problem& P) { return run_cgls(P, resid_hist); });
+}
+
+tigre_status tigre_cgls_begin(tigre_geometry_t geo, const void* proj, void* vol,
+                              const tigre_solver_opts* opts, tigre_cgls_t* out)
+{
+    if (!out) return fail(TIGRE_ERR_INVALID_ARG, "null output handle pointer");
+    *out = nullptr;
+    TIGRE_TRY(check_geometry(geo));
+    TIGRE_TRY(check_opts(geo, opts, proj, vol));
+    if (opts->flags & TIGRE_HOST_RESIDENT)
+        return fail(TIGRE_ERR_UNSUPPORTED, "stepwise CGLS takes device buffers");
+    return cgls_begin_device(geo, (const float*)proj, (float*)vol, opts, out);
+}
+
+tigre_status tigre_cgls_iterate(tigre_cgls_t S, int n_iter)
+{
+    if (!S || n_iter < 0) return fail(TIGRE_ERR_INVALID_ARG, "null state or n_iter < 0");
+    for (int it = 0; it < n_iter; ++it) TIGRE_TRY(cgls_step(S));
+    return TIGRE_OK;
+}
+
+tigre_status tigre_cgls_history(tigre_cgls_t S, double* resid_hist, int n)
+{
+    if (!S || n < 0 || n > S->done || (n > 0 && !resid_hist))
+        return fail(TIGRE_ERR_INVALID_ARG, "history: need 0 <= n <= iterations done");
+    return finish_history(S->hist, resid_hist, n, S->st);
+}
+
+tigre_status tigre_cgls_end(tigre_cgls_t S)
+{
+    if (S) cgls_release(S);
+    return TIGRE_OK;
 }
 
 }  // extern "C"

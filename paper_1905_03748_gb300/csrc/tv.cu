@@ -103,6 +103,7 @@ tigre_status tv_impl(const int64_t n[3], void* vol, tigre_dtype t, int n_steps, 
     double* norm = d_red + kRedBlocks;
     return dispatch_dtype(t, [&](auto tag) -> tigre_status {
         using T = decltype(tag);
+        ProfScope prof(kProfTV, st);
         for (int s = 0; s < n_steps; ++s) {
             tv_grad_kernel<T><<<kRedBlocks, kRedThreads, 0, st>>>(
                 (const T*)vol, (float*)scratch_g, (int)n[0], (int)n[1], (int)n[2], (float)eps,

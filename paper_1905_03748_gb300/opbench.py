@@ -1,0 +1,68 @@
+"""Operator microbenchmark: time one operator of the library on an N^3 volume
+with an N^2 detector (cube workload geometry) and a chosen number of angles.
+
+    python -m paper_1905_03748_gb300.opbench --op forward --n 512 --angles 360
+    python -m paper_1905_03748_gb300.opbench --op backward --weight matched --n 512 --angles 16 --repeat 1
+
+Prints one JSON line: device ms per call (CUDA events on the launching
+stream, after one warm-up call) and Gvoxel*angles/s.  Also the small-case
+target of the committed ncu profiles.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+
+import numpy as np
+import torch
+
+from . import synth, tigre
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--op", choices=["forward", "backward", "adjoint", "tv"], default="forward")
+    ap.add_argument("--weight", choices=["matched", "fdk"], default="matched")
+    ap.add_argument("--n", type=int, default=512)
+    ap.add_argument("--angles", type=int, default=360)
+    ap.add_argument("--dtype", choices=["f32", "bf16", "f16"], default="f32")
+    ap.add_argument("--repeat", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=1)
+    a = ap.parse_args()
+    dt = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}[a.dtype]
+    geo = synth.cube_geometry(a.n, a.n)
+    ang = synth.angles(a.angles)
+    G = tigre.Geometry(geo, ang)
+    vol = torch.from_numpy(synth.phantom("ellipsoids50", a.n, 256.0 / a.n)).cuda().to(dt)
+    proj = torch.empty(G.proj_shape, device="cuda", dtype=dt)
+    out = torch.empty(G.vol_shape, device="cuda", dtype=dt)
+    if a.op in ("backward", "adjoint"):
+        G.forward(vol, out=proj)
+    if a.op == "forward":
+        fn = lambda: G.forward(vol, out=proj)  # noqa: E731
+    elif a.op == "backward":
+        fn = lambda: G.backward(proj, out=out, weight=a.weight)  # noqa: E731
+    elif a.op == "adjoint":
+        fn = lambda: G.backward(proj, out=out, weight="adjoint")  # noqa: E731
+    else:
+        fn = lambda: tigre.tigre_tv_step(vol, 1, 0.002, 1e-8)  # noqa: E731
+    for _ in range(a.warmup):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(a.repeat):
+        fn()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / max(a.repeat, 1)
+    va = float(a.n) ** 3 * a.angles
+    print(json.dumps({"op": a.op, "weight": a.weight, "n": a.n, "angles": a.angles,
+                      "dtype": a.dtype, "ms": ms, "gvox_ang_s": va / ms / 1e6,
+                      "checksum": float(out.float().sum() if a.op != "forward" else
+                                        proj.float().sum())}))
+    G.close()
+
+
+if __name__ == "__main__":
+    main()

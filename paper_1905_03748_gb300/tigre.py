@@ -32,7 +32,9 @@ TIGRE_GRAPH = 0x2
 
 EXPORTED = ["tigre_geometry_create", "tigre_geometry_destroy", "tigre_forward", "tigre_backward",
             "tigre_tv_step", "tigre_solver_opts_default", "tigre_sirt", "tigre_sart",
-            "tigre_cgls", "tigre_last_error"]
+            "tigre_cgls", "tigre_cgls_begin", "tigre_cgls_iterate", "tigre_cgls_history",
+            "tigre_cgls_end", "tigre_forward_samples", "tigre_profile_enable",
+            "tigre_profile_read", "tigre_launch_count", "tigre_last_error"]
 
 _DTYPES = {torch.float32: TIGRE_F32, torch.bfloat16: TIGRE_BF16, torch.float16: TIGRE_F16}
 _BP = {"matched": TIGRE_BP_MATCHED, "fdk": TIGRE_BP_FDK, "adjoint": TIGRE_BP_EXACT_ADJOINT}
@@ -68,6 +70,13 @@ _sigs = {
     "tigre_sirt": [_P, _P, _P, ctypes.POINTER(tigre_solver_opts), _P],
     "tigre_sart": [_P, _P, _P, ctypes.POINTER(tigre_solver_opts), _P],
     "tigre_cgls": [_P, _P, _P, ctypes.POINTER(tigre_solver_opts), _P],
+    "tigre_cgls_begin": [_P, _P, _P, ctypes.POINTER(tigre_solver_opts), ctypes.POINTER(_P)],
+    "tigre_cgls_iterate": [_P, ctypes.c_int],
+    "tigre_cgls_history": [_P, _P, ctypes.c_int],
+    "tigre_cgls_end": [_P],
+    "tigre_forward_samples": [_P, _I64, _I64, ctypes.POINTER(_I64)],
+    "tigre_profile_enable": [ctypes.c_int],
+    "tigre_profile_read": [ctypes.c_int, ctypes.POINTER(_I64), ctypes.POINTER(ctypes.c_double)],
 }
 for _name, _args in _sigs.items():
     _f = getattr(_lib, _name)
@@ -75,6 +84,10 @@ for _name, _args in _sigs.items():
     _f.restype = _ST
 _lib.tigre_last_error.argtypes = []
 _lib.tigre_last_error.restype = ctypes.c_char_p
+_lib.tigre_launch_count.argtypes = []
+_lib.tigre_launch_count.restype = ctypes.c_int64
+
+PROF_FORWARD, PROF_BACKPROJECT, PROF_ADJOINT, PROF_TV = 0, 1, 2, 3
 
 
 class TigreError(RuntimeError):
@@ -219,6 +232,50 @@ def tigre_cgls(handle, proj, vol, n_iter, bp_weight="matched", stream=None,
                host=False) -> np.ndarray:
     o = _opts(n_iter, stream, bp_weight=bp_weight)
     return _solver(_lib.tigre_cgls, handle, proj, vol, o, host)
+
+
+def tigre_cgls_begin(handle, proj, vol, n_iter_hint=16, bp_weight="matched", stream=None):
+    o = _opts(n_iter_hint, stream, bp_weight=bp_weight)
+    pp, _ = _dev(proj, "proj")
+    vp, _ = _dev(vol, "vol")
+    s = ctypes.c_void_p()
+    _check(_lib.tigre_cgls_begin(handle, pp, vp, ctypes.byref(o), ctypes.byref(s)))
+    return s
+
+
+def tigre_cgls_iterate(state, n_iter: int) -> None:
+    _check(_lib.tigre_cgls_iterate(state, int(n_iter)))
+
+
+def tigre_cgls_history(state, n: int) -> np.ndarray:
+    h = np.zeros(max(n, 1), dtype=np.float64)
+    _check(_lib.tigre_cgls_history(state, h.ctypes.data_as(_P), int(n)))
+    return h[:n]
+
+
+def tigre_cgls_end(state) -> None:
+    _check(_lib.tigre_cgls_end(state))
+
+
+def tigre_forward_samples(handle, angle_begin: int, angle_count: int) -> int:
+    n = _I64()
+    _check(_lib.tigre_forward_samples(handle, int(angle_begin), int(angle_count), ctypes.byref(n)))
+    return int(n.value)
+
+
+def tigre_profile_enable(on: bool = True) -> None:
+    _check(_lib.tigre_profile_enable(int(bool(on))))
+
+
+def tigre_profile_read(kind: int):
+    """(number of timed calls, total device ms) for a kernel class."""
+    n, ms = _I64(), ctypes.c_double()
+    _check(_lib.tigre_profile_read(int(kind), ctypes.byref(n), ctypes.byref(ms)))
+    return int(n.value), float(ms.value)
+
+
+def tigre_launch_count() -> int:
+    return int(_lib.tigre_launch_count())
 
 
 # ------------------------------------------------------------ convenience
