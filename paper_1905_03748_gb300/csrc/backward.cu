@@ -10,8 +10,14 @@
 //   (u, v) = ((X.e_u) mag, X_z mag) -> bilinear tap of the projection,
 //   FDK:     w = (DSO/(DSO - s))^2
 //   matched: w = (dx dy dz)/(du dv) * |X - S| * DSD^2/(DSO - s)^3.
-// The projections are first copied into a buffer with a two-pixel zero
-// border, so clamped coordinates read zeros and the loop has no branches.
+//
+// GB300 layout: the projections are first rewritten as horizontal pairs,
+// element (r, c) = (y[r][c-2], y[r][c-1]), with zero rows and columns around
+// the detector.  A bilinear tap is then two aligned 8-byte loads (one per
+// row) instead of four scalar loads.  The zero border is two columns wide in
+// u (u is clamped once per column and angle) and, in v, as many rows as the
+// volume's shadow can reach beyond the detector for this geometry (bounded on
+// the host), so the per-voxel loop has neither clamps nor branches.
 // Grid order: x-tiles fastest, z-chunks slowest, so resident blocks share one
 // band of detector rows per angle in L2.
 //
@@ -20,13 +26,18 @@
 // (FP32 atomics into padded accumulators in the same two layouts as the
 // forward projector, so a warp's atomics hit adjacent addresses).
 #include <algorithm>
+#include <cmath>
 
 #include "ray.cuh"
 
 namespace tigre {
 
+constexpr int kBpNZ = 16;  // voxels per thread along z
+
 struct BpConst {
     int nx, ny, nz, nu, nv;
+    int PU, PV;        // padded pair-buffer row length and rows per angle
+    int pv_lo;         // zero rows above the detector
     float x0, y0, z0;  // world position (mm) of voxel (0, 0, 0)
     float dx, dy, dz;
     float DSO, DSD;
@@ -35,24 +46,31 @@ struct BpConst {
     float wscale;          // (dx dy dz)/(du dv) * DSD^2
 };
 
-template <typename T>
-__device__ __forceinline__ float ldp(const T* p)
+template <typename T> struct PairOf;
+template <> struct PairOf<float> { using type = float2; };
+template <> struct PairOf<__nv_bfloat16> { using type = __nv_bfloat162; };
+template <> struct PairOf<__half> { using type = __half2; };
+
+__device__ __forceinline__ float2 ldpair(const float2* p) { return __ldg(p); }
+__device__ __forceinline__ float2 ldpair(const __nv_bfloat162* p)
 {
-    return to_f32<T>(__ldg(p));
+    return __bfloat1622float2(__ldg(p));
 }
+__device__ __forceinline__ float2 ldpair(const __half2* p) { return __half22float2(__ldg(p)); }
 
 // SART == true: also accumulate the backprojection of the all-ones
 // projections (the normaliser V^-1 = A_w^T 1, from the same weights and
 // interpolation) and finish with vol += lambda * num / den (den > 1e-12),
 // clamped at zero when nonneg.
 template <typename TP, typename TV, int NZ, int MODE, bool SART = false>
-__global__ void __launch_bounds__(256) bp_voxel_kernel(const TP* __restrict__ pp,
+__global__ void __launch_bounds__(256) bp_voxel_kernel(const typename PairOf<TP>::type* __restrict__ pp,
                                                        TV* __restrict__ vol,
                                                        const BpAngle* __restrict__ params,
                                                        BpConst c, int a_first, int na,
                                                        int accumulate, float lambda = 0.0f,
                                                        int nonneg = 0)
 {
+    using Pair = typename PairOf<TP>::type;
     const int x = blockIdx.x * 32 + threadIdx.x;
     const int y = blockIdx.y * 8 + threadIdx.y;
     const int zb = blockIdx.z * NZ;
@@ -60,9 +78,10 @@ __global__ void __launch_bounds__(256) bp_voxel_kernel(const TP* __restrict__ pp
     const float X = fmaf((float)x, c.dx, c.x0);
     const float Y = fmaf((float)y, c.dy, c.y0);
     const float Zb = fmaf((float)zb, c.dz, c.z0);
-    const int PU = c.nu + 2 * kPad;
-    const int64_t PA = (int64_t)PU * (c.nv + 2 * kPad);
-    const float pu_hi = (float)c.nu + 0.5f, pv_hi = (float)c.nv + 0.5f;
+    const int PU = c.PU;
+    const int64_t PA = (int64_t)PU * c.PV;
+    const float pu_hi = (float)c.nu + 0.5f;
+    const float pv_off = c.pv_off + (float)c.pv_lo;
 
     float acc[NZ];
     float nrm[SART ? NZ : 1];
@@ -82,11 +101,12 @@ __global__ void __launch_bounds__(256) bp_voxel_kernel(const TP* __restrict__ pp
         int ip;
         float fu;
         split_floor(pu, ip, fu);
-        const TP* col = pp + (int64_t)a * PA + ip;
-        const float pv0 = fmaf(Zb * mag, c.inv_dv, c.pv_off);
+        const Pair* col = pp + (int64_t)a * PA + ip;
+        // Padded row coordinate of voxel k: within [2, PV - 2) by the
+        // host-side bound on the volume's shadow.
+        const float pv0 = fmaf(Zb * mag, c.inv_dv, pv_off);
         const float dpv = c.dz * mag * c.inv_dv;
-        // Bilinear weight of the all-ones image (zero outside the detector).
-        float tu = 0.0f;
+        float tu = 0.0f;  // bilinear weight of the all-ones image along u
         if (SART)
             tu = ((unsigned)(ip - kPad) < (unsigned)c.nu ? 1.0f - fu : 0.0f) +
                  ((unsigned)(ip - kPad + 1) < (unsigned)c.nu ? fu : 0.0f);
@@ -101,16 +121,13 @@ __global__ void __launch_bounds__(256) bp_voxel_kernel(const TP* __restrict__ pp
         }
 #pragma unroll
         for (int k = 0; k < NZ; ++k) {
-            const float pv =
-                fminf(fmaxf(fmaf((float)k, dpv, pv0), -1.5f), pv_hi) + (float)kPad;
             int iq;
             float fv;
-            split_floor(pv, iq, fv);
-            const TP* r0 = col + iq * PU;
-            const float a00 = ldp(r0), a01 = ldp(r0 + 1);
-            const float a10 = ldp(r0 + PU), a11 = ldp(r0 + PU + 1);
-            const float top = fmaf(fu, a01 - a00, a00);
-            const float bot = fmaf(fu, a11 - a10, a10);
+            split_floor(fmaf((float)k, dpv, pv0), iq, fv);
+            const Pair* r0 = col + iq * PU;
+            const float2 t0 = ldpair(r0), t1 = ldpair(r0 + PU);
+            const float top = fmaf(fu, t0.y - t0.x, t0.x);
+            const float bot = fmaf(fu, t1.y - t1.x, t1.x);
             const float val = fmaf(fv, bot - top, top);
             float wk = w;
             if (MODE != TIGRE_BP_FDK) {
@@ -120,8 +137,9 @@ __global__ void __launch_bounds__(256) bp_voxel_kernel(const TP* __restrict__ pp
             }
             acc[k] = fmaf(wk, val, acc[k]);
             if (SART) {
-                const float tv = ((unsigned)(iq - kPad) < (unsigned)c.nv ? 1.0f - fv : 0.0f) +
-                                 ((unsigned)(iq - kPad + 1) < (unsigned)c.nv ? fv : 0.0f);
+                const int qq = iq - c.pv_lo;
+                const float tv = ((unsigned)qq < (unsigned)c.nv ? 1.0f - fv : 0.0f) +
+                                 ((unsigned)(qq + 1) < (unsigned)c.nv ? fv : 0.0f);
                 nrm[k] = fmaf(wk, tu * tv, nrm[k]);
             }
         }
@@ -145,16 +163,30 @@ __global__ void __launch_bounds__(256) bp_voxel_kernel(const TP* __restrict__ pp
     }
 }
 
-// Copy projections into the zero-bordered buffer: out[a][q+P][p+P] = in[a][q][p].
 template <typename TP>
-__global__ void pad_proj_kernel(const TP* __restrict__ in, TP* __restrict__ out, int nu, int nv)
+__device__ __forceinline__ TP pix_or_zero(const TP* row, int p, int nu)
 {
-    const int q = blockIdx.y, a = blockIdx.z;
-    const int PU = nu + 2 * kPad, PV = nv + 2 * kPad;
-    const TP* src = in + ((int64_t)a * nv + q) * nu;
-    TP* dst = out + ((int64_t)a * PV + q + kPad) * PU + kPad;
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < nu; p += gridDim.x * blockDim.x)
-        dst[p] = src[p];
+    return (unsigned)p < (unsigned)nu ? row[p] : from_f32<TP>(0.0f);
+}
+
+// Write the whole pair buffer of one angle range (zeros included):
+// out[a][r][c] = (y[a][r - pv_lo][c - 2], y[a][r - pv_lo][c - 1]).
+template <typename TP>
+__global__ void pair_proj_kernel(const TP* __restrict__ in, typename PairOf<TP>::type* __restrict__ out,
+                                 int nu, int nv, int PU, int PV, int pv_lo)
+{
+    using Pair = typename PairOf<TP>::type;
+    const int r = blockIdx.y, a = blockIdx.z;
+    const int q = r - pv_lo;
+    Pair* dst = out + ((int64_t)a * PV + r) * PU;
+    const TP* row = in + ((int64_t)a * nv + q) * nu;
+    const bool inrow = (unsigned)q < (unsigned)nv;
+    for (int col = blockIdx.x * blockDim.x + threadIdx.x; col < PU; col += gridDim.x * blockDim.x) {
+        Pair v;
+        v.x = inrow ? pix_or_zero(row, col - 2, nu) : from_f32<TP>(0.0f);
+        v.y = inrow ? pix_or_zero(row, col - 1, nu) : from_f32<TP>(0.0f);
+        dst[col] = v;
+    }
 }
 
 // Exact adjoint: scatter every sample of each ray.
@@ -230,6 +262,9 @@ __global__ void adj_finish_kernel(const float* __restrict__ acc_xy,
     }
 }
 
+// Bound, over every voxel a launch can touch (z-chunks rounded up to NZ) and
+// every angle, of the detector row coordinate a voxel projects to; the pair
+// buffer gets enough zero rows that all of them land inside it.
 static BpConst make_bp_const(const tigre_geometry_desc& d)
 {
     BpConst c;
@@ -238,9 +273,12 @@ static BpConst make_bp_const(const tigre_geometry_desc& d)
     c.nz = (int)d.n_voxel[2];
     c.nu = (int)d.n_det[0];
     c.nv = (int)d.n_det[1];
-    c.x0 = (float)(-0.5 * (double)(d.n_voxel[0] - 1) * d.d_voxel[0] + d.off_origin[0]);
-    c.y0 = (float)(-0.5 * (double)(d.n_voxel[1] - 1) * d.d_voxel[1] + d.off_origin[1]);
-    c.z0 = (float)(-0.5 * (double)(d.n_voxel[2] - 1) * d.d_voxel[2] + d.off_origin[2]);
+    const double x0 = -0.5 * (double)(d.n_voxel[0] - 1) * d.d_voxel[0] + d.off_origin[0];
+    const double y0 = -0.5 * (double)(d.n_voxel[1] - 1) * d.d_voxel[1] + d.off_origin[1];
+    const double z0 = -0.5 * (double)(d.n_voxel[2] - 1) * d.d_voxel[2] + d.off_origin[2];
+    c.x0 = (float)x0;
+    c.y0 = (float)y0;
+    c.z0 = (float)z0;
     c.dx = (float)d.d_voxel[0];
     c.dy = (float)d.d_voxel[1];
     c.dz = (float)d.d_voxel[2];
@@ -252,10 +290,25 @@ static BpConst make_bp_const(const tigre_geometry_desc& d)
     c.pv_off = (float)(0.5 * (double)(d.n_det[1] - 1) - d.off_det[1] / d.d_det[1]);
     c.wscale = (float)(d.d_voxel[0] * d.d_voxel[1] * d.d_voxel[2] / (d.d_det[0] * d.d_det[1]) *
                        d.DSD * d.DSD);
+    const double x1 = x0 + (double)(d.n_voxel[0] - 1) * d.d_voxel[0];
+    const double y1 = y0 + (double)(d.n_voxel[1] - 1) * d.d_voxel[1];
+    const int64_t nzc = (d.n_voxel[2] + kBpNZ - 1) / kBpNZ * kBpNZ;
+    const double z1 = z0 + (double)(nzc - 1) * d.d_voxel[2];
+    const double R = std::sqrt(std::max(x0 * x0, x1 * x1) + std::max(y0 * y0, y1 * y1));
+    const double mags[2] = {d.DSD / (d.DSO + R), d.DSD / (d.DSO - R)};
+    double vmin = 1e300, vmax = -1e300;
+    for (double Z : {z0, z1})
+        for (double m : mags) {
+            const double pv = Z * m / d.d_det[1] + (double)c.pv_off;
+            vmin = std::min(vmin, pv);
+            vmax = std::max(vmax, pv);
+        }
+    c.pv_lo = (int)std::max(2.0, std::ceil(-vmin) + 2.0);
+    const int pv_hi = (int)std::max(2.0, std::ceil(vmax - (double)(c.nv - 1)) + 2.0);
+    c.PV = c.nv + c.pv_lo + pv_hi;
+    c.PU = c.nu + 2 * kPad;
     return c;
 }
-
-constexpr int kBpNZ = 16;
 
 template <typename TP, typename TV>
 static tigre_status launch_voxel_bp(tigre_geometry* g, const TP* proj, TV* vol, int64_t a0,
@@ -263,29 +316,25 @@ static tigre_status launch_voxel_bp(tigre_geometry* g, const TP* proj, TV* vol, 
                                     cudaStream_t st, bool sart = false, float lambda = 0.0f,
                                     int nonneg = 0)
 {
+    using Pair = typename PairOf<TP>::type;
     const tigre_geometry_desc& d = g->desc;
     const BpConst c = make_bp_const(d);
-    const size_t pelems = (size_t)na * (size_t)(c.nu + 2 * kPad) * (size_t)(c.nv + 2 * kPad);
-    const uint64_t tag = 0x9000000000000000ull ^ ((uint64_t)sizeof(TP) << 56) ^
-                         ((uint64_t)na << 40) ^ ((uint64_t)c.nu << 20) ^ (uint64_t)c.nv;
-    if (g->proj_pad.bytes < pelems * sizeof(TP) || g->proj_pad.tag != tag) {
-        TIGRE_TRY(g->proj_pad.ensure(pelems * sizeof(TP)));
-        TIGRE_CUDA(cudaMemsetAsync(g->proj_pad.ptr, 0, pelems * sizeof(TP), st));
-        g->proj_pad.tag = tag;
-    }
+    const size_t pelems = (size_t)na * (size_t)c.PU * (size_t)c.PV;
+    TIGRE_TRY(g->proj_pad.ensure(pelems * sizeof(Pair)));
+    g->proj_pad.tag = 0;
+    Pair* pp = (Pair*)g->proj_pad.ptr;
     for (int64_t s = 0; s < na; s += 65535) {
         const int64_t cnt = std::min<int64_t>(65535, na - s);
-        dim3 grid((unsigned)((c.nu + 255) / 256), (unsigned)c.nv, (unsigned)cnt);
-        pad_proj_kernel<TP><<<grid, 256, 0, st>>>(
-            proj + s * (int64_t)c.nu * c.nv,
-            (TP*)g->proj_pad.ptr + s * (int64_t)(c.nu + 2 * kPad) * (c.nv + 2 * kPad), c.nu, c.nv);
-        TIGRE_LAUNCHED("pad_proj_kernel");
+        dim3 grid((unsigned)((c.PU + 255) / 256), (unsigned)c.PV, (unsigned)cnt);
+        pair_proj_kernel<TP><<<grid, 256, 0, st>>>(proj + s * (int64_t)c.nu * c.nv,
+                                                   pp + s * (int64_t)c.PU * c.PV, c.nu, c.nv,
+                                                   c.PU, c.PV, c.pv_lo);
+        TIGRE_LAUNCHED("pair_proj_kernel");
     }
     dim3 grid((unsigned)((c.nx + 31) / 32), (unsigned)((c.ny + 7) / 8),
               (unsigned)((c.nz + kBpNZ - 1) / kBpNZ));
     if (grid.y > 65535 || grid.z > 65535) return fail(TIGRE_ERR_UNSUPPORTED, "volume too large");
     const BpAngle* params = (const BpAngle*)g->bp_params.ptr;
-    const TP* pp = (const TP*)g->proj_pad.ptr;
     const dim3 block(32, 8);
     ProfScope prof(kProfBackproject, st);
     if (sart) {

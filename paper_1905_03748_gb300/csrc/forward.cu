@@ -57,6 +57,40 @@ __device__ __forceinline__ float ld(const T* p)
     return to_f32<T>(__ldg(p));
 }
 
+// Trilinear sample k of ray R from the padded volume.
+template <typename TV>
+__device__ __forceinline__ float tri_sample(const TV* __restrict__ vol, const Ray& R, float kf,
+                                            int PF, int PFM)
+{
+    int i_f, i_m, i_s;
+    float af, am, as;
+    split_floor(fmaf(kf, R.d[0], R.x0[0]), i_f, af);
+    split_floor(fmaf(kf, R.d[1], R.x0[1]), i_m, am);
+    split_floor(fmaf(kf, R.d[2], R.x0[2]), i_s, as);
+    const TV* b = vol + (i_s * PFM + i_m * PF + i_f);
+    const float v000 = ld(b), v100 = ld(b + 1);
+    const float v010 = ld(b + PF), v110 = ld(b + PF + 1);
+    const float v001 = ld(b + PFM), v101 = ld(b + PFM + 1);
+    const float v011 = ld(b + PFM + PF), v111 = ld(b + PFM + PF + 1);
+    const float c00 = fmaf(af, v100 - v000, v000);
+    const float c10 = fmaf(af, v110 - v010, v010);
+    const float c01 = fmaf(af, v101 - v001, v001);
+    const float c11 = fmaf(af, v111 - v011, v011);
+    const float c0 = fmaf(am, c10 - c00, c00);
+    const float c1 = fmaf(am, c11 - c01, c01);
+    return fmaf(as, c1 - c0, c0);
+}
+
+// One warp = 32 adjacent pixels of a detector row.  Their rays are nearly
+// parallel, but each starts its samples on its own entry face of the box, so
+// the k-th samples of neighbouring lanes sit at different depths and a
+// warp-wide gather would touch many rows.  The warp therefore marches in
+// depth order along the layout's middle axis (the main direction of the
+// rays): slab j holds main-axis coordinates [Y0 + j D, Y0 + (j+1) D) with D the
+// smallest per-sample advance in the warp, so each lane has at most one sample
+// per slab and all lanes gather at about the same depth.  Every lane still
+// adds its samples in the order k = 0..K-1, so the sums are identical to a
+// per-lane loop.
 template <typename TV, typename TP>
 __global__ void __launch_bounds__(256) fwd_l1_kernel(const TV* __restrict__ vxy,
                                                      const TV* __restrict__ vyx,
@@ -64,44 +98,62 @@ __global__ void __launch_bounds__(256) fwd_l1_kernel(const TV* __restrict__ vxy,
                                                      const FwdAngle* __restrict__ params,
                                                      FwdConst c, int a_first)
 {
+    const unsigned full = 0xffffffffu;
     const int p = blockIdx.x * 32 + threadIdx.x;
     const int q = blockIdx.z * blockDim.y + threadIdx.y;
     const int a = blockIdx.y;
-    if (p >= c.nu || q >= c.nv) return;
+    const bool inside = p < c.nu && q < c.nv;
 
     Ray R;
-    setup_ray(params + a_first + a, c, p, q, R);
-    float out = 0.0f;
-    if (!R.ok) {
-        out = __int_as_float(0x7fc00000);  // NaN: the ray failed the bounds proof
-    } else if (R.K > 0) {
-        const TV* __restrict__ vol = R.layout ? vyx : vxy;
-        const int PF = R.nf + 2 * kPad;
-        const int PFM = PF * (R.nm + 2 * kPad);
-        float acc = 0.0f;
+    R.K = 0;
+    R.ok = true;
+    if (inside) setup_ray(params + a_first + a, c, p, q, R);
+    const bool active = inside && R.ok && R.K > 0;
+    const unsigned act = __ballot_sync(full, active);
+    const int layout = params[a_first + a].layout;  // uniform per block
+    const TV* __restrict__ vol = layout ? vyx : vxy;
+    const int PF = (layout ? c.ny : c.nx) + 2 * kPad;
+    const int PFM = PF * ((layout ? c.nx : c.ny) + 2 * kPad);
+
+    float acc = 0.0f;
+    if (act) {
+        const unsigned pos = __ballot_sync(full, active && R.d[1] > 0.0f);
+        const unsigned neg = __ballot_sync(full, active && R.d[1] < 0.0f);
+        int k = 0;
         float kf = 0.0f;
-#pragma unroll 2
-        for (int k = 0; k < R.K; ++k, kf += 1.0f) {
-            int i_f, i_m, i_s;
-            float af, am, as;
-            split_floor(fmaf(kf, R.d[0], R.x0[0]), i_f, af);
-            split_floor(fmaf(kf, R.d[1], R.x0[1]), i_m, am);
-            split_floor(fmaf(kf, R.d[2], R.x0[2]), i_s, as);
-            const TV* b = vol + (i_s * PFM + i_m * PF + i_f);
-            const float v000 = ld(b), v100 = ld(b + 1);
-            const float v010 = ld(b + PF), v110 = ld(b + PF + 1);
-            const float v001 = ld(b + PFM), v101 = ld(b + PFM + 1);
-            const float v011 = ld(b + PFM + PF), v111 = ld(b + PFM + PF + 1);
-            const float c00 = fmaf(af, v100 - v000, v000);
-            const float c10 = fmaf(af, v110 - v010, v010);
-            const float c01 = fmaf(af, v101 - v001, v001);
-            const float c11 = fmaf(af, v111 - v011, v011);
-            const float c0 = fmaf(am, c10 - c00, c00);
-            const float c1 = fmaf(am, c11 - c01, c01);
-            acc += fmaf(as, c1 - c0, c0);
+        if (pos == act || neg == act) {
+            const float sgn = pos == act ? 1.0f : -1.0f;
+            const float y0 = sgn * R.x0[1], dy = sgn * R.d[1];
+            const float y1 = fmaf((float)(R.K - 1), dy, y0);
+            float D = active ? dy : 3.0e38f, Y0 = active ? y0 : 3.0e38f;
+            float Y1 = active ? y1 : -3.0e38f;
+            int kmax = active ? R.K : 0;
+            for (int o = 16; o > 0; o >>= 1) {
+                D = fminf(D, __shfl_xor_sync(full, D, o));
+                Y0 = fminf(Y0, __shfl_xor_sync(full, Y0, o));
+                Y1 = fmaxf(Y1, __shfl_xor_sync(full, Y1, o));
+                kmax = max(kmax, __shfl_xor_sync(full, kmax, o));
+            }
+            // A warp whose rays disagree wildly (a near-grazing ray makes D
+            // tiny) skips the march; the tail loop below does the work.
+            const float ns = (Y1 - Y0) / D;
+            const int nslab = ns < (float)(2 * kmax + 64) ? (int)ns + 1 : 0;
+            for (int j = 1; j <= nslab; ++j) {
+                const float bound = fmaf((float)j, D, Y0);
+                if (k < R.K && fmaf(kf, dy, y0) < bound) {
+                    acc += tri_sample(vol, R, kf, PF, PFM);
+                    ++k;
+                    kf += 1.0f;
+                }
+            }
         }
-        out = acc * R.h;
+        // Samples not consumed above (mixed directions, or rounding at a slab
+        // edge) finish in order here.
+        for (; active && k < R.K; ++k, kf += 1.0f) acc += tri_sample(vol, R, kf, PF, PFM);
     }
+    if (!inside) return;
+    const float out = !R.ok ? __int_as_float(0x7fc00000)  // NaN: ray failed the bounds proof
+                            : acc * R.h;
     proj[((int64_t)a * c.nv + q) * c.nu + p] = from_f32<TP>(out);
 }
 
