@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--e2e-iters", type=int, default=20, help="CGLS iterations per e2e call")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--cpu-angles", type=int, default=6,
+    ap.add_argument("--cpu-angles", type=int, default=48,
                     help="angles of the workload in the bounded CPU-oracle sample")
     return ap.parse_args()
 

@@ -11,13 +11,11 @@
 //   FDK:     w = (DSO/(DSO - s))^2
 //   matched: w = (dx dy dz)/(du dv) * |X - S| * DSD^2/(DSO - s)^3.
 //
-// GB300 layout: the projections are first rewritten as horizontal pairs,
-// element (r, c) = (y[r][c-2], y[r][c-1]), with zero rows and columns around
-// the detector.  A bilinear tap is then two aligned 8-byte loads (one per
-// row) instead of four scalar loads.  The zero border is two columns wide in
-// u (u is clamped once per column and angle) and, in v, as many rows as the
-// volume's shadow can reach beyond the detector for this geometry (bounded on
-// the host), so the per-voxel loop has neither clamps nor branches.
+// GB300 layout: the projections are first copied into a buffer with zero
+// columns (two) and rows around the detector: in v, as many rows as the
+// volume's shadow can reach beyond the detector for this geometry (bounded
+// on the host), so the per-voxel loop has neither clamps nor branches; u is
+// clamped once per column and angle.
 // Grid order: x-tiles fastest, z-chunks slowest, so resident blocks share one
 // band of detector rows per angle in L2.
 //
@@ -36,7 +34,7 @@ constexpr int kBpNZ = 16;  // voxels per thread along z
 
 struct BpConst {
     int nx, ny, nz, nu, nv;
-    int PU, PV;        // padded pair-buffer row length and rows per angle
+    int PU, PV;        // padded buffer row length and rows per angle
     int pv_lo;         // zero rows above the detector
     float x0, y0, z0;  // world position (mm) of voxel (0, 0, 0)
     float dx, dy, dz;
@@ -46,31 +44,24 @@ struct BpConst {
     float wscale;          // (dx dy dz)/(du dv) * DSD^2
 };
 
-template <typename T> struct PairOf;
-template <> struct PairOf<float> { using type = float2; };
-template <> struct PairOf<__nv_bfloat16> { using type = __nv_bfloat162; };
-template <> struct PairOf<__half> { using type = __half2; };
-
-__device__ __forceinline__ float2 ldpair(const float2* p) { return __ldg(p); }
-__device__ __forceinline__ float2 ldpair(const __nv_bfloat162* p)
+template <typename T>
+__device__ __forceinline__ float ldp(const T* p)
 {
-    return __bfloat1622float2(__ldg(p));
+    return to_f32<T>(__ldg(p));
 }
-__device__ __forceinline__ float2 ldpair(const __half2* p) { return __half22float2(__ldg(p)); }
 
 // SART == true: also accumulate the backprojection of the all-ones
 // projections (the normaliser V^-1 = A_w^T 1, from the same weights and
 // interpolation) and finish with vol += lambda * num / den (den > 1e-12),
 // clamped at zero when nonneg.
 template <typename TP, typename TV, int NZ, int MODE, bool SART = false>
-__global__ void __launch_bounds__(256) bp_voxel_kernel(const typename PairOf<TP>::type* __restrict__ pp,
+__global__ void __launch_bounds__(256) bp_voxel_kernel(const TP* __restrict__ pp,
                                                        TV* __restrict__ vol,
                                                        const BpAngle* __restrict__ params,
                                                        BpConst c, int a_first, int na,
                                                        int accumulate, float lambda = 0.0f,
                                                        int nonneg = 0)
 {
-    using Pair = typename PairOf<TP>::type;
     const int x = blockIdx.x * 32 + threadIdx.x;
     const int y = blockIdx.y * 8 + threadIdx.y;
     const int zb = blockIdx.z * NZ;
@@ -101,7 +92,7 @@ __global__ void __launch_bounds__(256) bp_voxel_kernel(const typename PairOf<TP>
         int ip;
         float fu;
         split_floor(pu, ip, fu);
-        const Pair* col = pp + (int64_t)a * PA + ip;
+        const TP* col = pp + (int64_t)a * PA + ip;
         // Padded row coordinate of voxel k: within [2, PV - 2) by the
         // host-side bound on the volume's shadow.
         const float pv0 = fmaf(Zb * mag, c.inv_dv, pv_off);
@@ -124,10 +115,11 @@ __global__ void __launch_bounds__(256) bp_voxel_kernel(const typename PairOf<TP>
             int iq;
             float fv;
             split_floor(fmaf((float)k, dpv, pv0), iq, fv);
-            const Pair* r0 = col + iq * PU;
-            const float2 t0 = ldpair(r0), t1 = ldpair(r0 + PU);
-            const float top = fmaf(fu, t0.y - t0.x, t0.x);
-            const float bot = fmaf(fu, t1.y - t1.x, t1.x);
+            const TP* r0 = col + iq * PU;
+            const float a00 = ldp(r0), a01 = ldp(r0 + 1);
+            const float a10 = ldp(r0 + PU), a11 = ldp(r0 + PU + 1);
+            const float top = fmaf(fu, a01 - a00, a00);
+            const float bot = fmaf(fu, a11 - a10, a10);
             const float val = fmaf(fv, bot - top, top);
             float wk = w;
             if (MODE != TIGRE_BP_FDK) {
@@ -169,24 +161,19 @@ __device__ __forceinline__ TP pix_or_zero(const TP* row, int p, int nu)
     return (unsigned)p < (unsigned)nu ? row[p] : from_f32<TP>(0.0f);
 }
 
-// Write the whole pair buffer of one angle range (zeros included):
-// out[a][r][c] = (y[a][r - pv_lo][c - 2], y[a][r - pv_lo][c - 1]).
+// Write the whole zero-bordered buffer of one angle range:
+// out[a][r][c] = y[a][r - pv_lo][c - 2] (zero outside the detector).
 template <typename TP>
-__global__ void pair_proj_kernel(const TP* __restrict__ in, typename PairOf<TP>::type* __restrict__ out,
-                                 int nu, int nv, int PU, int PV, int pv_lo)
+__global__ void pad_proj_kernel(const TP* __restrict__ in, TP* __restrict__ out, int nu, int nv,
+                                int PU, int PV, int pv_lo)
 {
-    using Pair = typename PairOf<TP>::type;
     const int r = blockIdx.y, a = blockIdx.z;
     const int q = r - pv_lo;
-    Pair* dst = out + ((int64_t)a * PV + r) * PU;
+    TP* dst = out + ((int64_t)a * PV + r) * PU;
     const TP* row = in + ((int64_t)a * nv + q) * nu;
     const bool inrow = (unsigned)q < (unsigned)nv;
-    for (int col = blockIdx.x * blockDim.x + threadIdx.x; col < PU; col += gridDim.x * blockDim.x) {
-        Pair v;
-        v.x = inrow ? pix_or_zero(row, col - 2, nu) : from_f32<TP>(0.0f);
-        v.y = inrow ? pix_or_zero(row, col - 1, nu) : from_f32<TP>(0.0f);
-        dst[col] = v;
-    }
+    for (int col = blockIdx.x * blockDim.x + threadIdx.x; col < PU; col += gridDim.x * blockDim.x)
+        dst[col] = inrow ? pix_or_zero(row, col - kPad, nu) : from_f32<TP>(0.0f);
 }
 
 // Exact adjoint: scatter every sample of each ray.
@@ -263,7 +250,7 @@ __global__ void adj_finish_kernel(const float* __restrict__ acc_xy,
 }
 
 // Bound, over every voxel a launch can touch (z-chunks rounded up to NZ) and
-// every angle, of the detector row coordinate a voxel projects to; the pair
+// every angle, of the detector row coordinate a voxel projects to; the padded
 // buffer gets enough zero rows that all of them land inside it.
 static BpConst make_bp_const(const tigre_geometry_desc& d)
 {
@@ -316,20 +303,19 @@ static tigre_status launch_voxel_bp(tigre_geometry* g, const TP* proj, TV* vol, 
                                     cudaStream_t st, bool sart = false, float lambda = 0.0f,
                                     int nonneg = 0)
 {
-    using Pair = typename PairOf<TP>::type;
     const tigre_geometry_desc& d = g->desc;
     const BpConst c = make_bp_const(d);
     const size_t pelems = (size_t)na * (size_t)c.PU * (size_t)c.PV;
-    TIGRE_TRY(g->proj_pad.ensure(pelems * sizeof(Pair)));
+    TIGRE_TRY(g->proj_pad.ensure(pelems * sizeof(TP)));
     g->proj_pad.tag = 0;
-    Pair* pp = (Pair*)g->proj_pad.ptr;
+    TP* pp = (TP*)g->proj_pad.ptr;
     for (int64_t s = 0; s < na; s += 65535) {
         const int64_t cnt = std::min<int64_t>(65535, na - s);
         dim3 grid((unsigned)((c.PU + 255) / 256), (unsigned)c.PV, (unsigned)cnt);
-        pair_proj_kernel<TP><<<grid, 256, 0, st>>>(proj + s * (int64_t)c.nu * c.nv,
+        pad_proj_kernel<TP><<<grid, 256, 0, st>>>(proj + s * (int64_t)c.nu * c.nv,
                                                    pp + s * (int64_t)c.PU * c.PV, c.nu, c.nv,
                                                    c.PU, c.PV, c.pv_lo);
-        TIGRE_LAUNCHED("pair_proj_kernel");
+        TIGRE_LAUNCHED("pad_proj_kernel");
     }
     dim3 grid((unsigned)((c.nx + 31) / 32), (unsigned)((c.ny + 7) / 8),
               (unsigned)((c.nz + kBpNZ - 1) / kBpNZ));
