@@ -191,6 +191,18 @@ TIGRE_API tigre_status tigre_cgls_iterate(tigre_cgls_t state, int n_iter);
 TIGRE_API tigre_status tigre_cgls_history(tigre_cgls_t state, double* resid_hist, int n);
 TIGRE_API tigre_status tigre_cgls_end(tigre_cgls_t state);
 
+/* Forward-projector kernel choice for this handle: 0 = automatic (the
+ * shared-memory slab kernel when a conservative bound says every block's
+ * slab fits its staging box, else the L1 gather kernel), 1 = L1 gather
+ * kernel, 2 = shared-memory slab kernel.  Both compute the same sums in the
+ * same order. */
+TIGRE_API tigre_status tigre_geometry_set_forward_path(tigre_geometry_t geo, int path);
+
+/* Error bits raised by kernels of this handle (1 = a bounded wait timed out,
+ * 2 = a slab did not fit its staging box, 4 = rays of one block ran opposite
+ * ways; the affected outputs are NaN).  Synchronous; clear != 0 resets. */
+TIGRE_API tigre_status tigre_geometry_error_flags(tigre_geometry_t geo, int* flags, int clear);
+
 /* Total quadrature samples (sum of K over rays) of tigre_forward for the
  * angle range: the algorithmic work of one forward projection.  Runs a
  * ray-setup kernel on the current device and synchronises. */

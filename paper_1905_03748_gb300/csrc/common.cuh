@@ -133,6 +133,8 @@ struct tigre_geometry {
     tigre::DeviceBuffer scratch_vol;  // FP32 volume-sized scratch
     tigre::DeviceBuffer scratch_red;  // reduction partials / device scalars
     std::vector<int> layout;          // forward-projector layout per angle (host copy)
+    int fwd_path = 0;                 // 0 auto, 1 L1 gather kernel, 2 TMA slab kernel
+    tigre::DeviceBuffer err_flag;     // int: error bits set by kernels (bounds, timeouts)
 };
 
 namespace tigre {
@@ -141,6 +143,11 @@ constexpr int kPad = 2;  // zero voxels around the volume in the padded layouts
 
 tigre_status upload_params(tigre_geometry* g);
 size_t padded_elems(const tigre_geometry_desc& d);
+// Shared-memory slab forward projector (forward_tma.cu).
+bool tma_forward_fits(const tigre_geometry_desc& d, size_t elem);
+template <typename TV, typename TP>
+tigre_status launch_forward_tma(tigre_geometry* g, const TV* vol, TP* proj, int64_t a0, int64_t na,
+                                const bool need[2], int* d_err, cudaStream_t st);
 tigre_status ensure_padded(DeviceBuffer& buf, const tigre_geometry_desc& d, size_t elem, int layout,
                            cudaStream_t st);
 tigre_status check_geometry(tigre_geometry* g);

@@ -254,6 +254,22 @@ tigre_status forward_impl(tigre_geometry* g, const void* vol, tigre_dtype vt, vo
     const FwdConst c = make_fwd_const(d);
     bool need[2] = {false, false};
     for (int64_t a = a0; a < a0 + na; ++a) need[g->layout[(size_t)a]] = true;
+    const bool use_tma =
+        g->fwd_path == 2 || (g->fwd_path == 0 && tma_forward_fits(d, dtype_size(vt)));
+    if (use_tma) {
+        if (!g->err_flag.ptr) {
+            TIGRE_TRY(g->err_flag.ensure(sizeof(int)));
+            TIGRE_CUDA(cudaMemsetAsync(g->err_flag.ptr, 0, sizeof(int), st));
+        }
+        return dispatch_dtype(vt, [&](auto vtag) -> tigre_status {
+            using TV = decltype(vtag);
+            return dispatch_dtype(pt, [&](auto ptag) -> tigre_status {
+                using TP = decltype(ptag);
+                return launch_forward_tma<TV, TP>(g, (const TV*)vol, (TP*)proj, a0, na, need,
+                                                  (int*)g->err_flag.ptr, st);
+            });
+        });
+    }
 
     return dispatch_dtype(vt, [&](auto vtag) -> tigre_status {
         using TV = decltype(vtag);
@@ -300,6 +316,23 @@ __global__ void __launch_bounds__(256) sample_count_kernel(const FwdAngle* __res
 }
 
 }  // namespace tigre
+
+extern "C" tigre_status tigre_geometry_set_forward_path(tigre_geometry_t g, int path)
+{
+    if (!g || path < 0 || path > 2) return tigre::fail(TIGRE_ERR_INVALID_ARG, "path must be 0, 1 or 2");
+    g->fwd_path = path;
+    return TIGRE_OK;
+}
+
+extern "C" tigre_status tigre_geometry_error_flags(tigre_geometry_t g, int* flags, int clear)
+{
+    if (!g || !flags) return tigre::fail(TIGRE_ERR_INVALID_ARG, "null argument");
+    *flags = 0;
+    if (!g->err_flag.ptr) return TIGRE_OK;
+    TIGRE_CUDA(cudaMemcpy(flags, g->err_flag.ptr, sizeof(int), cudaMemcpyDeviceToHost));
+    if (clear) TIGRE_CUDA(cudaMemset(g->err_flag.ptr, 0, sizeof(int)));
+    return TIGRE_OK;
+}
 
 extern "C" tigre_status tigre_forward_samples(tigre_geometry_t g, int64_t angle_begin,
                                               int64_t angle_count, int64_t* samples)

@@ -33,7 +33,8 @@ TIGRE_GRAPH = 0x2
 EXPORTED = ["tigre_geometry_create", "tigre_geometry_destroy", "tigre_forward", "tigre_backward",
             "tigre_tv_step", "tigre_solver_opts_default", "tigre_sirt", "tigre_sart",
             "tigre_cgls", "tigre_cgls_begin", "tigre_cgls_iterate", "tigre_cgls_history",
-            "tigre_cgls_end", "tigre_forward_samples", "tigre_profile_enable",
+            "tigre_cgls_end", "tigre_forward_samples", "tigre_geometry_set_forward_path",
+            "tigre_geometry_error_flags", "tigre_profile_enable",
             "tigre_profile_read", "tigre_launch_count", "tigre_last_error"]
 
 _DTYPES = {torch.float32: TIGRE_F32, torch.bfloat16: TIGRE_BF16, torch.float16: TIGRE_F16}
@@ -75,6 +76,8 @@ _sigs = {
     "tigre_cgls_history": [_P, _P, ctypes.c_int],
     "tigre_cgls_end": [_P],
     "tigre_forward_samples": [_P, _I64, _I64, ctypes.POINTER(_I64)],
+    "tigre_geometry_set_forward_path": [_P, ctypes.c_int],
+    "tigre_geometry_error_flags": [_P, ctypes.POINTER(ctypes.c_int), ctypes.c_int],
     "tigre_profile_enable": [ctypes.c_int],
     "tigre_profile_read": [ctypes.c_int, ctypes.POINTER(_I64), ctypes.POINTER(ctypes.c_double)],
 }
@@ -261,6 +264,19 @@ def tigre_forward_samples(handle, angle_begin: int, angle_count: int) -> int:
     n = _I64()
     _check(_lib.tigre_forward_samples(handle, int(angle_begin), int(angle_count), ctypes.byref(n)))
     return int(n.value)
+
+
+FWD_AUTO, FWD_L1, FWD_TMA = 0, 1, 2
+
+
+def tigre_geometry_set_forward_path(handle, path: int) -> None:
+    _check(_lib.tigre_geometry_set_forward_path(handle, int(path)))
+
+
+def tigre_geometry_error_flags(handle, clear: bool = True) -> int:
+    f = ctypes.c_int()
+    _check(_lib.tigre_geometry_error_flags(handle, ctypes.byref(f), int(bool(clear))))
+    return int(f.value)
 
 
 def tigre_profile_enable(on: bool = True) -> None:

@@ -219,3 +219,54 @@ def test_cgls_host_resident_equals_device(tigre):
         hh = tigre.tigre_cgls(G.handle, torch.from_numpy(b).pin_memory(), xh, 4, host=True)
     np.testing.assert_array_equal(hh, hd)
     assert torch.equal(xh, xd.cpu())
+
+
+# ----------------------------------------------- forward kernel paths
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
+def test_forward_paths_are_bitwise_identical(tigre, case, dtype):
+    """The shared-memory slab kernel and the L1 gather kernel add the same
+    samples in the same order: identical bits, no error flags."""
+    geo, ang, vol = case
+    with tigre.Geometry(geo, ang) as G:
+        v = torch.from_numpy(vol).cuda().to(dtype)
+        tigre.tigre_geometry_set_forward_path(G.handle, tigre.FWD_L1)
+        a = G.forward(v, dtype=torch.float32)
+        tigre.tigre_geometry_set_forward_path(G.handle, tigre.FWD_TMA)
+        b = G.forward(v, dtype=torch.float32)
+        assert tigre.tigre_geometry_error_flags(G.handle) == 0
+    assert torch.isfinite(b).all()
+    assert torch.equal(a, b)
+
+
+def test_forward_large_pixels_fall_back_and_match_oracle(tigre):
+    """Pixels much larger than voxels: a block's slab cannot be staged in one
+    box, so the automatic choice is the L1 kernel; forcing the slab kernel
+    reports it (error bit 2, NaN) instead of reading outside its tile."""
+    geo = synth.geometry(48, 0.5, (20, 12), 4.0, dso=200.0, dsd=300.0)
+    ang = synth.angles(7)
+    vol = synth.random_volume((48, 48, 48), seed=6)
+    with tigre.Geometry(geo, ang) as G:
+        v = torch.from_numpy(vol).cuda()
+        p = G.forward(v).cpu().numpy()
+        assert tigre.tigre_geometry_error_flags(G.handle) == 0
+        tigre.tigre_geometry_set_forward_path(G.handle, tigre.FWD_TMA)
+        bad = G.forward(v)
+        assert tigre.tigre_geometry_error_flags(G.handle) & 2
+        assert torch.isnan(bad).any()
+    assert rel(p, oracle.forward(geo, ang, vol)) < TOL
+
+
+@pytest.mark.parametrize("dtype", [torch.bfloat16, torch.float16])
+def test_reduced_precision_storage_forward_and_backward(tigre, dtype):
+    """BF16/FP16 storage with FP32 accumulation: on the storage-rounded
+    inputs the result matches the oracle to FP32 accuracy (output in F32)."""
+    geo, ang, vol = small_case()
+    with tigre.Geometry(geo, ang) as G:
+        v = torch.from_numpy(vol).cuda().to(dtype)
+        p = G.forward(v, dtype=torch.float32)
+        y = p.to(dtype)
+        b = G.backward(y, weight="matched", dtype=torch.float32)
+    vr = v.float().cpu().numpy()
+    assert rel(p.cpu().numpy(), oracle.forward(geo, ang, vr)) < TOL
+    assert rel(b.cpu().numpy(), oracle.backward(geo, ang, y.float().cpu().numpy())) < TOL
