@@ -417,7 +417,11 @@ bool tma_forward_fits(const tigre_geometry_desc& d, size_t elem)
     const double vmax = 0.5 * (double)d.n_det[1] * d.d_det[1] + std::fabs(d.off_det[1]);
     const double slope = vmax / (d.DSD * std::cos(45.0 * kDeg + phi));
     const double lat_s = 8.0 * d.d_det[1] * Lmax / d.DSD / d.d_voxel[2];
-    const double need_s = lat_s + kTmaTS * (dmM / d.d_voxel[2]) * slope + 2.0 + 1.0;
+    // A row's rays cross a plane m = const at depths that differ by up to the
+    // f-extent, and z = v depth / DSD moves with depth: rows far from the
+    // mid-plane need that much more height.
+    const double couple = (vmax / d.DSD) * need_f * dfm / d.d_voxel[2];
+    const double need_s = lat_s + couple + kTmaTS * (dmM / d.d_voxel[2]) * slope + 2.0 + 1.0;
     return need_f <= (double)kTmaFB && need_s <= (double)kTmaSB;
 }
 
