@@ -132,6 +132,24 @@ TIGRE_API tigre_status tigre_backward(tigre_geometry_t geo, const void* proj, ti
 TIGRE_API tigre_status tigre_tv_step(const int64_t n_voxel[3], void* vol, tigre_dtype dtype, int n_steps,
                            double alpha, double eps, void* cuda_stream);
 
+/* tigre_tv_step without any device allocation (the paper has no counterpart:
+ * this is a service for callers that cannot allocate device memory while they
+ * run, such as a real-time loop that reserved all GPU memory at start-up
+ * because cudaMalloc/cudaFree can synchronise the device and take unbounded
+ * time, or a process whose memory another allocator already holds).  Same
+ * arguments and results as tigre_tv_step; the gradient and the FP64 reduction
+ * live in one fixed scratch array compiled into the library (16 MiB + 5 KiB,
+ * held on every GPU that loads the library until the process exits).
+ * Volumes of more than 4,194,304 voxels are rejected with
+ * TIGRE_ERR_INVALID_ARG.  The first call on a device looks up the scratch
+ * address (cudaGetSymbolAddress) with that device current, so make it before
+ * any stream capture.  All calls share the scratch: calls that overlap on the
+ * GPU (other streams or host threads) race and must be serialised by the
+ * caller.  No state carries over between calls. */
+TIGRE_API tigre_status tigre_tv_step_noalloc(const int64_t n_voxel[3], void* vol, tigre_dtype dtype,
+                                             int n_steps, double alpha, double eps,
+                                             void* cuda_stream);
+
 /* Solver flags. */
 #define TIGRE_HOST_RESIDENT 0x1u /* proj / vol are host pointers (out-of-core mode) */
 #define TIGRE_GRAPH 0x2u         /* capture each iteration in a CUDA graph */

@@ -31,7 +31,8 @@ TIGRE_HOST_RESIDENT = 0x1
 TIGRE_GRAPH = 0x2
 
 EXPORTED = ["tigre_geometry_create", "tigre_geometry_destroy", "tigre_forward", "tigre_backward",
-            "tigre_tv_step", "tigre_solver_opts_default", "tigre_sirt", "tigre_sart",
+            "tigre_tv_step", "tigre_tv_step_noalloc", "tigre_solver_opts_default", "tigre_sirt",
+            "tigre_sart",
             "tigre_cgls", "tigre_cgls_begin", "tigre_cgls_iterate", "tigre_cgls_history",
             "tigre_cgls_end", "tigre_forward_samples", "tigre_geometry_set_forward_path",
             "tigre_geometry_error_flags", "tigre_profile_enable",
@@ -67,6 +68,8 @@ _sigs = {
     "tigre_forward": [_P, _P, ctypes.c_int, _P, ctypes.c_int, _I64, _I64, _P],
     "tigre_backward": [_P, _P, ctypes.c_int, _P, ctypes.c_int, _I64, _I64, ctypes.c_int, _P],
     "tigre_tv_step": [_P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double, _P],
+    "tigre_tv_step_noalloc": [_P, _P, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                              ctypes.c_double, _P],
     "tigre_solver_opts_default": [ctypes.POINTER(tigre_solver_opts)],
     "tigre_sirt": [_P, _P, _P, ctypes.POINTER(tigre_solver_opts), _P],
     "tigre_sart": [_P, _P, _P, ctypes.POINTER(tigre_solver_opts), _P],
@@ -180,6 +183,18 @@ def tigre_tv_step(vol: torch.Tensor, n_steps: int, alpha: float, eps: float,
     n = (ctypes.c_int64 * 3)(nx, ny, nz)
     _check(_lib.tigre_tv_step(n, vp, vt, int(n_steps), float(alpha), float(eps),
                               _stream(stream)))
+
+
+def tigre_tv_step_noalloc(vol: torch.Tensor, n_steps: int, alpha: float, eps: float,
+                          stream=None) -> None:
+    """tigre_tv_step without device allocation, for callers that must not
+    allocate while they run (volumes up to 4,194,304 voxels; calls that
+    overlap on the GPU share one scratch area and must not run concurrently)."""
+    vp, vt = _dev(vol, "vol")
+    nz, ny, nx = vol.shape
+    n = (ctypes.c_int64 * 3)(nx, ny, nz)
+    _check(_lib.tigre_tv_step_noalloc(n, vp, vt, int(n_steps), float(alpha), float(eps),
+                                      _stream(stream)))
 
 
 def tigre_solver_opts_default() -> tigre_solver_opts:
