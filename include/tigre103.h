@@ -209,11 +209,13 @@ TIGRE_API tigre_status tigre_cgls_iterate(tigre_cgls_t state, int n_iter);
 TIGRE_API tigre_status tigre_cgls_history(tigre_cgls_t state, double* resid_hist, int n);
 TIGRE_API tigre_status tigre_cgls_end(tigre_cgls_t state);
 
-/* Forward-projector kernel choice for this handle: 0 = automatic (the
- * shared-memory slab kernel when a conservative bound says every block's
- * slab fits its staging box, else the L1 gather kernel), 1 = L1 gather
- * kernel, 2 = shared-memory slab kernel.  Both compute the same sums in the
- * same order. */
+/* Forward-projector kernel choice for this handle: 0 = automatic (the quad
+ * gather kernel), 1 = scalar L1 gather kernel, 2 = shared-memory slab kernel
+ * (TMA-staged; only for geometries whose ray bundles fit its staging box,
+ * otherwise it reports error bit 2 and NaN), 3 = quad gather kernel (two
+ * 16-byte loads per sample from a layout holding the four taps of a cell's
+ * plane; four times the volume in workspace).  All compute the same sums in
+ * the same order and give identical results. */
 TIGRE_API tigre_status tigre_geometry_set_forward_path(tigre_geometry_t geo, int path);
 
 /* Error bits raised by kernels of this handle (1 = a bounded wait timed out,

@@ -127,13 +127,15 @@ struct tigre_geometry {
     tigre::DeviceBuffer bp_params;    // BpAngle[n_angles]
     tigre::DeviceBuffer vol_xy;       // padded volume, x fastest
     tigre::DeviceBuffer vol_yx;       // padded volume, y fastest
+    tigre::DeviceBuffer vol_qxy;      // quad volumes of the two padded layouts
+    tigre::DeviceBuffer vol_qyx;
     tigre::DeviceBuffer proj_pad;     // zero-bordered projections for the backprojector
     tigre::DeviceBuffer adj_xy;       // FP32 padded accumulators of the exact adjoint
     tigre::DeviceBuffer adj_yx;
     tigre::DeviceBuffer scratch_vol;  // FP32 volume-sized scratch
     tigre::DeviceBuffer scratch_red;  // reduction partials / device scalars
     std::vector<int> layout;          // forward-projector layout per angle (host copy)
-    int fwd_path = 0;                 // 0 auto, 1 L1 gather kernel, 2 TMA slab kernel
+    int fwd_path = 0;                 // 0 auto, 1 L1 scalar, 2 TMA slab, 3 L1 quad
     tigre::DeviceBuffer err_flag;     // int: error bits set by kernels (bounds, timeouts)
 };
 

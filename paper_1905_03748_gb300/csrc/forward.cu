@@ -157,6 +157,152 @@ __global__ void __launch_bounds__(256) fwd_l1_kernel(const TV* __restrict__ vxy,
     proj[((int64_t)a * c.nv + q) * c.nu + p] = from_f32<TP>(out);
 }
 
+// ----------------------------------------------------------- quad layout
+// Element (s, m, f) of a quad volume holds the four taps of the cell's lower
+// s-plane: (P[s][m][f], P[s][m][f+1], P[s][m+1][f], P[s][m+1][f+1]) of the
+// zero-padded layout P.  A trilinear sample is then two aligned loads (planes
+// s and s+1) instead of eight scalar ones.  F32 quads are float4 (16 B);
+// BF16/F16 quads are four 16-bit values in a uint2 (8 B).
+template <typename T> struct QuadOf;
+template <> struct QuadOf<float> { using type = float4; };
+template <> struct QuadOf<__nv_bfloat16> { using type = uint2; };
+template <> struct QuadOf<__half> { using type = uint2; };
+
+__device__ __forceinline__ float4 pack_quad(float a, float b, float c, float d)
+{
+    return make_float4(a, b, c, d);
+}
+__device__ __forceinline__ uint32_t bits16(__nv_bfloat16 v) { return __bfloat16_as_ushort(v); }
+__device__ __forceinline__ uint32_t bits16(__half v) { return __half_as_ushort(v); }
+template <typename T>
+__device__ __forceinline__ uint2 pack_quad16(T a, T b, T c, T d)
+{
+    return make_uint2(bits16(a) | (bits16(b) << 16), bits16(c) | (bits16(d) << 16));
+}
+
+__device__ __forceinline__ float4 load_quad(const float4* p, float*) { return __ldg(p); }
+__device__ __forceinline__ float4 load_quad(const uint2* p, __nv_bfloat16*)
+{
+    const uint2 q = __ldg(p);
+    return make_float4(__uint_as_float(q.x << 16), __uint_as_float(q.x & 0xffff0000u),
+                       __uint_as_float(q.y << 16), __uint_as_float(q.y & 0xffff0000u));
+}
+__device__ __forceinline__ float4 load_quad(const uint2* p, __half*)
+{
+    const uint2 q = __ldg(p);
+    return make_float4(__half2float(__ushort_as_half((unsigned short)(q.x & 0xffffu))),
+                       __half2float(__ushort_as_half((unsigned short)(q.x >> 16))),
+                       __half2float(__ushort_as_half((unsigned short)(q.y & 0xffffu))),
+                       __half2float(__ushort_as_half((unsigned short)(q.y >> 16))));
+}
+
+// Build the quad volume of a padded layout; one block per (s, m) row.
+template <typename T>
+__global__ void quad_kernel(const T* __restrict__ pad, typename QuadOf<T>::type* __restrict__ out,
+                            int PF, int PM, int64_t rows)
+{
+    const int64_t r = blockIdx.x;
+    if (r >= rows) return;
+    const int m = (int)(r % PM);
+    const T* row = pad + r * PF;
+    const bool has_m1 = m + 1 < PM;
+    for (int f = threadIdx.x; f < PF; f += blockDim.x) {
+        const bool has_f1 = f + 1 < PF;
+        const T z = from_f32<T>(0.0f);
+        const T a = row[f];
+        const T b = has_f1 ? row[f + 1] : z;
+        const T c = has_m1 ? row[PF + f] : z;
+        const T d = (has_m1 && has_f1) ? row[PF + f + 1] : z;
+        if constexpr (sizeof(T) == 4)
+            out[r * PF + f] = pack_quad(a, b, c, d);
+        else
+            out[r * PF + f] = pack_quad16(a, b, c, d);
+    }
+}
+
+template <typename TV>
+__device__ __forceinline__ float tri_sample_quad(const typename QuadOf<TV>::type* __restrict__ qv,
+                                                 const Ray& R, float kf, int PF, int PFM)
+{
+    int i_f, i_m, i_s;
+    float af, am, as;
+    split_floor(fmaf(kf, R.d[0], R.x0[0]), i_f, af);
+    split_floor(fmaf(kf, R.d[1], R.x0[1]), i_m, am);
+    split_floor(fmaf(kf, R.d[2], R.x0[2]), i_s, as);
+    const typename QuadOf<TV>::type* b = qv + (i_s * PFM + i_m * PF + i_f);
+    const float4 lo = load_quad(b, (TV*)nullptr);        // plane s: v000 v100 v010 v110
+    const float4 hi = load_quad(b + PFM, (TV*)nullptr);  // plane s+1: v001 v101 v011 v111
+    const float c00 = fmaf(af, lo.y - lo.x, lo.x);
+    const float c10 = fmaf(af, lo.w - lo.z, lo.z);
+    const float c01 = fmaf(af, hi.y - hi.x, hi.x);
+    const float c11 = fmaf(af, hi.w - hi.z, hi.z);
+    const float c0 = fmaf(am, c10 - c00, c00);
+    const float c1 = fmaf(am, c11 - c01, c01);
+    return fmaf(as, c1 - c0, c0);
+}
+
+// The L1 kernel's depth-ordered march, gathering from quad volumes.
+template <typename TV, typename TP>
+__global__ void __launch_bounds__(256) fwd_quad_kernel(
+    const typename QuadOf<TV>::type* __restrict__ qxy,
+    const typename QuadOf<TV>::type* __restrict__ qyx, TP* __restrict__ proj,
+    const FwdAngle* __restrict__ params, FwdConst c, int a_first)
+{
+    using Q = typename QuadOf<TV>::type;
+    const unsigned full = 0xffffffffu;
+    const int p = blockIdx.x * 32 + threadIdx.x;
+    const int q = blockIdx.z * blockDim.y + threadIdx.y;
+    const int a = blockIdx.y;
+    const bool inside = p < c.nu && q < c.nv;
+
+    Ray R;
+    R.K = 0;
+    R.ok = true;
+    if (inside) setup_ray(params + a_first + a, c, p, q, R);
+    const bool active = inside && R.ok && R.K > 0;
+    const unsigned act = __ballot_sync(full, active);
+    const int layout = params[a_first + a].layout;  // uniform per block
+    const Q* __restrict__ vol = layout ? qyx : qxy;
+    const int PF = (layout ? c.ny : c.nx) + 2 * kPad;
+    const int PFM = PF * ((layout ? c.nx : c.ny) + 2 * kPad);
+
+    float acc = 0.0f;
+    if (act) {
+        const unsigned pos = __ballot_sync(full, active && R.d[1] > 0.0f);
+        const unsigned neg = __ballot_sync(full, active && R.d[1] < 0.0f);
+        int k = 0;
+        float kf = 0.0f;
+        if (pos == act || neg == act) {
+            const float sgn = pos == act ? 1.0f : -1.0f;
+            const float y0 = sgn * R.x0[1], dy = sgn * R.d[1];
+            const float y1 = fmaf((float)(R.K - 1), dy, y0);
+            float D = active ? dy : 3.0e38f, Y0 = active ? y0 : 3.0e38f;
+            float Y1 = active ? y1 : -3.0e38f;
+            int kmax = active ? R.K : 0;
+            for (int o = 16; o > 0; o >>= 1) {
+                D = fminf(D, __shfl_xor_sync(full, D, o));
+                Y0 = fminf(Y0, __shfl_xor_sync(full, Y0, o));
+                Y1 = fmaxf(Y1, __shfl_xor_sync(full, Y1, o));
+                kmax = max(kmax, __shfl_xor_sync(full, kmax, o));
+            }
+            const float ns = (Y1 - Y0) / D;
+            const int nslab = ns < (float)(2 * kmax + 64) ? (int)ns + 1 : 0;
+            for (int j = 1; j <= nslab; ++j) {
+                const float bound = fmaf((float)j, D, Y0);
+                if (k < R.K && fmaf(kf, dy, y0) < bound) {
+                    acc += tri_sample_quad<TV>(vol, R, kf, PF, PFM);
+                    ++k;
+                    kf += 1.0f;
+                }
+            }
+        }
+        for (; active && k < R.K; ++k, kf += 1.0f) acc += tri_sample_quad<TV>(vol, R, kf, PF, PFM);
+    }
+    if (!inside) return;
+    const float out = !R.ok ? __int_as_float(0x7fc00000) : acc * R.h;
+    proj[((int64_t)a * c.nv + q) * c.nu + p] = from_f32<TP>(out);
+}
+
 // out (padded, x fastest): out[z+P][y+P][x+P] = vol[z][y][x].
 template <typename T>
 __global__ void pad_xy_kernel(const T* __restrict__ vol, T* __restrict__ out, int nx, int ny,
@@ -254,8 +400,8 @@ tigre_status forward_impl(tigre_geometry* g, const void* vol, tigre_dtype vt, vo
     const FwdConst c = make_fwd_const(d);
     bool need[2] = {false, false};
     for (int64_t a = a0; a < a0 + na; ++a) need[g->layout[(size_t)a]] = true;
-    const bool use_tma =
-        g->fwd_path == 2 || (g->fwd_path == 0 && tma_forward_fits(d, dtype_size(vt)));
+    const bool use_tma = g->fwd_path == 2;
+    const bool use_quad = g->fwd_path == 0 || g->fwd_path == 3;
     if (use_tma) {
         if (!g->err_flag.ptr) {
             TIGRE_TRY(g->err_flag.ensure(sizeof(int)));
@@ -273,15 +419,39 @@ tigre_status forward_impl(tigre_geometry* g, const void* vol, tigre_dtype vt, vo
 
     return dispatch_dtype(vt, [&](auto vtag) -> tigre_status {
         using TV = decltype(vtag);
+        using Q = typename QuadOf<TV>::type;
         DeviceBuffer* bufs[2] = {&g->vol_xy, &g->vol_yx};
+        DeviceBuffer* qbufs[2] = {&g->vol_qxy, &g->vol_qyx};
         for (int l = 0; l < 2; ++l) {
             if (!need[l]) continue;
             TIGRE_TRY(ensure_padded(*bufs[l], d, sizeof(TV), l, st));
             TIGRE_TRY(fill_padded<TV>(d, (const TV*)vol, (TV*)bufs[l]->ptr, l, st));
+            if (use_quad) {
+                const int PF = (int)(l ? d.n_voxel[1] : d.n_voxel[0]) + 2 * kPad;
+                const int PM = (int)(l ? d.n_voxel[0] : d.n_voxel[1]) + 2 * kPad;
+                const int64_t rows = (int64_t)PM * (d.n_voxel[2] + 2 * kPad);
+                TIGRE_TRY(qbufs[l]->ensure(padded_elems(d) * sizeof(Q)));
+                quad_kernel<TV><<<(unsigned)rows, 128, 0, st>>>((const TV*)bufs[l]->ptr,
+                                                                (Q*)qbufs[l]->ptr, PF, PM, rows);
+                TIGRE_LAUNCHED("quad_kernel");
+            }
         }
         return dispatch_dtype(pt, [&](auto ptag) -> tigre_status {
             using TP = decltype(ptag);
             ProfScope prof(kProfForward, st);
+            if (use_quad) {
+                for (int64_t s = 0; s < na; s += 65535) {
+                    const int64_t cnt = std::min<int64_t>(65535, na - s);
+                    dim3 grid((unsigned)((c.nu + 31) / 32), (unsigned)cnt,
+                              (unsigned)((c.nv + 7) / 8));
+                    fwd_quad_kernel<TV, TP><<<grid, dim3(32, 8), 0, st>>>(
+                        (const Q*)g->vol_qxy.ptr, (const Q*)g->vol_qyx.ptr,
+                        (TP*)proj + s * (int64_t)c.nu * c.nv, (const FwdAngle*)g->fwd_params.ptr,
+                        c, (int)(a0 + s));
+                    TIGRE_LAUNCHED("fwd_quad_kernel");
+                }
+                return TIGRE_OK;
+            }
             const int64_t step = 65535;
             for (int64_t s = 0; s < na; s += step) {
                 const int64_t cnt = std::min(step, na - s);
@@ -319,7 +489,7 @@ __global__ void __launch_bounds__(256) sample_count_kernel(const FwdAngle* __res
 
 extern "C" tigre_status tigre_geometry_set_forward_path(tigre_geometry_t g, int path)
 {
-    if (!g || path < 0 || path > 2) return tigre::fail(TIGRE_ERR_INVALID_ARG, "path must be 0, 1 or 2");
+    if (!g || path < 0 || path > 3) return tigre::fail(TIGRE_ERR_INVALID_ARG, "path must be 0..3");
     g->fwd_path = path;
     return TIGRE_OK;
 }

@@ -195,6 +195,8 @@ tigre_status tigre_geometry_destroy(tigre_geometry_t g)
     g->bp_params.release();
     g->vol_xy.release();
     g->vol_yx.release();
+    g->vol_qxy.release();
+    g->vol_qyx.release();
     g->proj_pad.release();
     g->adj_xy.release();
     g->adj_yx.release();

@@ -28,14 +28,14 @@ def main():
     ap.add_argument("--dtype", choices=["f32", "bf16", "f16"], default="f32")
     ap.add_argument("--repeat", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=1)
-    ap.add_argument("--path", choices=["auto", "l1", "tma"], default="auto",
+    ap.add_argument("--path", choices=["auto", "l1", "tma", "quad"], default="auto",
                     help="forward-projector kernel")
     a = ap.parse_args()
     dt = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}[a.dtype]
     geo = synth.cube_geometry(a.n, a.n)
     ang = synth.angles(a.angles)
     G = tigre.Geometry(geo, ang)
-    tigre.tigre_geometry_set_forward_path(G.handle, {"auto": 0, "l1": 1, "tma": 2}[a.path])
+    tigre.tigre_geometry_set_forward_path(G.handle, {"auto": 0, "l1": 1, "tma": 2, "quad": 3}[a.path])
     vol = torch.from_numpy(synth.phantom("ellipsoids50", a.n, 256.0 / a.n)).cuda().to(dt)
     proj = torch.empty(G.proj_shape, device="cuda", dtype=dt)
     out = torch.empty(G.vol_shape, device="cuda", dtype=dt)

@@ -281,7 +281,7 @@ def tigre_forward_samples(handle, angle_begin: int, angle_count: int) -> int:
     return int(n.value)
 
 
-FWD_AUTO, FWD_L1, FWD_TMA = 0, 1, 2
+FWD_AUTO, FWD_L1, FWD_TMA, FWD_QUAD = 0, 1, 2, 3
 
 
 def tigre_geometry_set_forward_path(handle, path: int) -> None:
