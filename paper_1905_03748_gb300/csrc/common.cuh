@@ -125,6 +125,7 @@ struct tigre_geometry {
     bool uploaded = false;
     tigre::DeviceBuffer fwd_params;   // FwdAngle[n_angles]
     tigre::DeviceBuffer bp_params;    // BpAngle[n_angles]
+    tigre::DeviceBuffer angle_order;  // int[n_angles]: angle indices grouped by layout
     tigre::DeviceBuffer vol_xy;       // padded volume, x fastest
     tigre::DeviceBuffer vol_yx;       // padded volume, y fastest
     tigre::DeviceBuffer vol_qxy;      // quad volumes of the two padded layouts

@@ -96,12 +96,13 @@ __global__ void __launch_bounds__(256) fwd_l1_kernel(const TV* __restrict__ vxy,
                                                      const TV* __restrict__ vyx,
                                                      TP* __restrict__ proj,
                                                      const FwdAngle* __restrict__ params,
-                                                     FwdConst c, int a_first)
+                                                     FwdConst c, int a_first,
+                                                     const int* __restrict__ order)
 {
     const unsigned full = 0xffffffffu;
     const int p = blockIdx.x * 32 + threadIdx.x;
     const int q = blockIdx.z * blockDim.y + threadIdx.y;
-    const int a = blockIdx.y;
+    const int a = order ? order[blockIdx.y] : (int)blockIdx.y;
     const bool inside = p < c.nu && q < c.nv;
 
     Ray R;
@@ -246,13 +247,13 @@ template <typename TV, typename TP>
 __global__ void __launch_bounds__(256) fwd_quad_kernel(
     const typename QuadOf<TV>::type* __restrict__ qxy,
     const typename QuadOf<TV>::type* __restrict__ qyx, TP* __restrict__ proj,
-    const FwdAngle* __restrict__ params, FwdConst c, int a_first)
+    const FwdAngle* __restrict__ params, FwdConst c, int a_first, const int* __restrict__ order)
 {
     using Q = typename QuadOf<TV>::type;
     const unsigned full = 0xffffffffu;
     const int p = blockIdx.x * 32 + threadIdx.x;
     const int q = blockIdx.z * blockDim.y + threadIdx.y;
-    const int a = blockIdx.y;
+    const int a = order ? order[blockIdx.y] : (int)blockIdx.y;
     const bool inside = p < c.nu && q < c.nv;
 
     Ray R;
@@ -402,6 +403,12 @@ tigre_status forward_impl(tigre_geometry* g, const void* vol, tigre_dtype vt, vo
     for (int64_t a = a0; a < a0 + na; ++a) need[g->layout[(size_t)a]] = true;
     const bool use_tma = g->fwd_path == 2;
     const bool use_quad = g->fwd_path == 0 || g->fwd_path == 3;
+    // Full-range launches visit the angles grouped by memory layout, so the
+    // blocks resident at one time read one layout's z-slab (half the L2
+    // working set of an interleaved order).
+    const int* order = (a0 == 0 && na == (int64_t)g->angles.size() && na <= 65535)
+                           ? (const int*)g->angle_order.ptr
+                           : nullptr;
     if (use_tma) {
         if (!g->err_flag.ptr) {
             TIGRE_TRY(g->err_flag.ensure(sizeof(int)));
@@ -447,7 +454,7 @@ tigre_status forward_impl(tigre_geometry* g, const void* vol, tigre_dtype vt, vo
                     fwd_quad_kernel<TV, TP><<<grid, dim3(32, 8), 0, st>>>(
                         (const Q*)g->vol_qxy.ptr, (const Q*)g->vol_qyx.ptr,
                         (TP*)proj + s * (int64_t)c.nu * c.nv, (const FwdAngle*)g->fwd_params.ptr,
-                        c, (int)(a0 + s));
+                        c, (int)(a0 + s), order);
                     TIGRE_LAUNCHED("fwd_quad_kernel");
                 }
                 return TIGRE_OK;
@@ -459,7 +466,7 @@ tigre_status forward_impl(tigre_geometry* g, const void* vol, tigre_dtype vt, vo
                 fwd_l1_kernel<TV, TP><<<grid, dim3(32, 8), 0, st>>>(
                     (const TV*)g->vol_xy.ptr, (const TV*)g->vol_yx.ptr,
                     (TP*)proj + s * (int64_t)c.nu * c.nv, (const FwdAngle*)g->fwd_params.ptr, c,
-                    (int)(a0 + s));
+                    (int)(a0 + s), order);
                 TIGRE_LAUNCHED("fwd_l1_kernel");
             }
             return TIGRE_OK;

@@ -145,6 +145,15 @@ tigre_status upload_params(tigre_geometry* g)
         g->layout[(size_t)a] = layout;
         bp[(size_t)a] = BpAngle{(float)c, (float)s, (float)S[0], (float)S[1]};
     }
+    // Angle indices grouped by layout (stable), for full-range projections.
+    std::vector<int> order;
+    order.reserve((size_t)na);
+    for (int l = 0; l < 2; ++l)
+        for (int64_t a = 0; a < na; ++a)
+            if (g->layout[(size_t)a] == l) order.push_back((int)a);
+    TIGRE_TRY(g->angle_order.ensure(sizeof(int) * (size_t)na));
+    TIGRE_CUDA(cudaMemcpy(g->angle_order.ptr, order.data(), sizeof(int) * (size_t)na,
+                          cudaMemcpyHostToDevice));
     TIGRE_TRY(g->fwd_params.ensure(sizeof(FwdAngle) * (size_t)na));
     TIGRE_TRY(g->bp_params.ensure(sizeof(BpAngle) * (size_t)na));
     TIGRE_CUDA(cudaMemcpy(g->fwd_params.ptr, fwd.data(), sizeof(FwdAngle) * (size_t)na,
@@ -193,6 +202,7 @@ tigre_status tigre_geometry_destroy(tigre_geometry_t g)
     if (!g) return TIGRE_OK;
     g->fwd_params.release();
     g->bp_params.release();
+    g->angle_order.release();
     g->vol_xy.release();
     g->vol_yx.release();
     g->vol_qxy.release();
