@@ -278,7 +278,7 @@ def run_ours(args):
            "samples_per_ax": samples,
            "kernel_ms": {"forward": fwd_avg, "backproject_matched": bp_avg},
            "resid_last": float(hist[-1]) if len(hist) else None,
-           "roofline": {"kernel": "fwd_l1_kernel", "bound": "alu", "achieved": achieved,
+           "roofline": {"kernel": "fwd_quad_kernel", "bound": "alu", "achieved": achieved,
                         "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
                         "traffic": traffic,
                         "per_unit": f"{FLOPS_PER_SAMPLE} FP32 flops per quadrature sample "

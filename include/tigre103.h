@@ -150,6 +150,28 @@ TIGRE_API tigre_status tigre_tv_step_noalloc(const int64_t n_voxel[3], void* vol
                                              int n_steps, double alpha, double eps,
                                              void* cuda_stream);
 
+/* Out-of-core forward projection (paper Alg. 1 on one GPU): vol_host is a
+ * HOST pointer (F32, (nz, ny, nx)), streamed to the device in axial slabs of
+ * slab_planes planes (0 = sized from free device memory) on a copy stream,
+ * overlapped with the projection of the previous slab; partial projections
+ * accumulate into proj (DEVICE, F32, (angle_count, nv, nu), overwritten).
+ * Pageable host memory is page-locked for the call.  Synchronous. */
+TIGRE_API tigre_status tigre_forward_ooc(tigre_geometry_t geo, const float* vol_host, float* proj,
+                                         int64_t angle_begin, int64_t angle_count,
+                                         int64_t slab_planes, void* cuda_stream);
+
+/* Out-of-core voxel-driven backprojection (paper Alg. 2 on one GPU): each
+ * axial slab of vol_host (HOST, F32, overwritten) is backprojected from all
+ * angles on the device and copied out while the next slab is computed.
+ * proj (F32) is a device pointer, or with proj_on_host != 0 a host pointer
+ * streamed in chunks of angle_chunk angles through two device buffers.
+ * weight: MATCHED or FDK.  Synchronous. */
+TIGRE_API tigre_status tigre_backward_ooc(tigre_geometry_t geo, const float* proj,
+                                          int proj_on_host, float* vol_host, int64_t angle_begin,
+                                          int64_t angle_count, tigre_bp_weight weight,
+                                          int64_t slab_planes, int64_t angle_chunk,
+                                          void* cuda_stream);
+
 /* Solver flags. */
 #define TIGRE_HOST_RESIDENT 0x1u /* proj / vol are host pointers (out-of-core mode) */
 #define TIGRE_GRAPH 0x2u         /* capture each iteration in a CUDA graph */

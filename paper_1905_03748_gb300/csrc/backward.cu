@@ -36,6 +36,8 @@ struct BpConst {
     int nx, ny, nz, nu, nv;
     int PU, PV;        // padded buffer row length and rows per angle
     int pv_lo;         // zero rows above the detector
+    int z_first, z_end;  // voxel planes computed by this launch
+    int z_out0;          // plane of the output buffer's first plane
     float x0, y0, z0;  // world position (mm) of voxel (0, 0, 0)
     float dx, dy, dz;
     float DSO, DSD;
@@ -64,7 +66,7 @@ __global__ void __launch_bounds__(256) bp_voxel_kernel(const TP* __restrict__ pp
 {
     const int x = blockIdx.x * 32 + threadIdx.x;
     const int y = blockIdx.y * 8 + threadIdx.y;
-    const int zb = blockIdx.z * NZ;
+    const int zb = c.z_first + blockIdx.z * NZ;
     if (x >= c.nx || y >= c.ny) return;
     const float X = fmaf((float)x, c.dx, c.x0);
     const float Y = fmaf((float)y, c.dy, c.y0);
@@ -139,8 +141,8 @@ __global__ void __launch_bounds__(256) bp_voxel_kernel(const TP* __restrict__ pp
 #pragma unroll
     for (int k = 0; k < NZ; ++k) {
         const int z = zb + k;
-        if (z < c.nz) {
-            TV* o = vol + ((int64_t)z * c.ny + y) * c.nx + x;
+        if (z < c.z_end) {
+            TV* o = vol + ((int64_t)(z - c.z_out0) * c.ny + y) * c.nx + x;
             if (SART) {
                 const float den = nrm[k];
                 float v = to_f32<TV>(*o);
@@ -279,7 +281,9 @@ static BpConst make_bp_const(const tigre_geometry_desc& d)
                        d.DSD * d.DSD);
     const double x1 = x0 + (double)(d.n_voxel[0] - 1) * d.d_voxel[0];
     const double y1 = y0 + (double)(d.n_voxel[1] - 1) * d.d_voxel[1];
-    const int64_t nzc = (d.n_voxel[2] + kBpNZ - 1) / kBpNZ * kBpNZ;
+    // Launches may start at any plane (z-slabs), so the last chunk of NZ
+    // planes can reach up to nz + NZ - 2: bound that far.
+    const int64_t nzc = d.n_voxel[2] + kBpNZ;
     const double z1 = z0 + (double)(nzc - 1) * d.d_voxel[2];
     const double R = std::sqrt(std::max(x0 * x0, x1 * x1) + std::max(y0 * y0, y1 * y1));
     const double mags[2] = {d.DSD / (d.DSO + R), d.DSD / (d.DSO - R)};
@@ -294,17 +298,29 @@ static BpConst make_bp_const(const tigre_geometry_desc& d)
     const int pv_hi = (int)std::max(2.0, std::ceil(vmax - (double)(c.nv - 1)) + 2.0);
     c.PV = c.nv + c.pv_lo + pv_hi;
     c.PU = c.nu + 2 * kPad;
+    c.z_first = 0;
+    c.z_end = c.nz;
+    c.z_out0 = 0;
     return c;
 }
 
+// Voxel planes [z_first, z_end) into an output buffer whose first plane is
+// z_out0 (in-core: 0, nz, 0; out-of-core slabs: the slab's planes).
 template <typename TP, typename TV>
-static tigre_status launch_voxel_bp(tigre_geometry* g, const TP* proj, TV* vol, int64_t a0,
-                                    int64_t na, tigre_bp_weight w, int accumulate,
-                                    cudaStream_t st, bool sart = false, float lambda = 0.0f,
-                                    int nonneg = 0)
+tigre_status launch_voxel_bp(tigre_geometry* g, const TP* proj, TV* vol, int64_t a0, int64_t na,
+                             tigre_bp_weight w, int accumulate, cudaStream_t st, bool sart = false,
+                             float lambda = 0.0f, int nonneg = 0, int z_first = 0, int z_end = -1,
+                             int z_out0 = 0)
 {
     const tigre_geometry_desc& d = g->desc;
-    const BpConst c = make_bp_const(d);
+    BpConst c = make_bp_const(d);
+    if (z_end >= 0) {
+        if (z_first < 0 || z_end > c.nz || z_first >= z_end || z_out0 > z_first)
+            return fail(TIGRE_ERR_INVALID_ARG, "bad z range");
+        c.z_first = z_first;
+        c.z_end = z_end;
+        c.z_out0 = z_out0;
+    }
     const size_t pelems = (size_t)na * (size_t)c.PU * (size_t)c.PV;
     TIGRE_TRY(g->proj_pad.ensure(pelems * sizeof(TP)));
     g->proj_pad.tag = 0;
@@ -318,7 +334,7 @@ static tigre_status launch_voxel_bp(tigre_geometry* g, const TP* proj, TV* vol, 
         TIGRE_LAUNCHED("pad_proj_kernel");
     }
     dim3 grid((unsigned)((c.nx + 31) / 32), (unsigned)((c.ny + 7) / 8),
-              (unsigned)((c.nz + kBpNZ - 1) / kBpNZ));
+              (unsigned)((c.z_end - c.z_first + kBpNZ - 1) / kBpNZ));
     if (grid.y > 65535 || grid.z > 65535) return fail(TIGRE_ERR_UNSUPPORTED, "volume too large");
     const BpAngle* params = (const BpAngle*)g->bp_params.ptr;
     const dim3 block(32, 8);
@@ -339,6 +355,18 @@ static tigre_status launch_voxel_bp(tigre_geometry* g, const TP* proj, TV* vol, 
     }
     TIGRE_LAUNCHED("bp_voxel_kernel");
     return TIGRE_OK;
+}
+
+tigre_status backward_slab_impl(tigre_geometry* g, const float* proj, float* vol_slab, int64_t a0,
+                                int64_t na, tigre_bp_weight w, int accumulate, int z_first,
+                                int z_end, cudaStream_t st)
+{
+    TIGRE_TRY(check_geometry(g));
+    TIGRE_TRY(check_range(g, a0, na));
+    if (w == TIGRE_BP_EXACT_ADJOINT)
+        return fail(TIGRE_ERR_UNSUPPORTED, "out-of-core backprojection is voxel-driven");
+    return launch_voxel_bp<float, float>(g, proj, vol_slab, a0, na, w, accumulate, st, false, 0.0f,
+                                         0, z_first, z_end, z_first);
 }
 
 tigre_status sart_update_impl(tigre_geometry* g, const float* r, float* x, int64_t a0, int64_t na,

@@ -146,6 +146,15 @@ constexpr int kPad = 2;  // zero voxels around the volume in the padded layouts
 
 tigre_status upload_params(tigre_geometry* g);
 size_t padded_elems(const tigre_geometry_desc& d);
+// Out-of-core building blocks: the zero-padded layout of a (sub-)volume
+// described by d, and the voxel-driven backprojection of planes
+// [z_first, z_end) into a slab buffer whose first plane is z_first.
+tigre_status fill_padded_f32(const tigre_geometry_desc& d, const float* vol, float* out, int layout,
+                             cudaStream_t st);
+tigre_status backward_slab_impl(tigre_geometry* g, const float* proj, float* vol_slab, int64_t a0,
+                                int64_t na, tigre_bp_weight w, int accumulate, int z_first,
+                                int z_end, cudaStream_t st);
+
 // Shared-memory slab forward projector (forward_tma.cu).
 bool tma_forward_fits(const tigre_geometry_desc& d, size_t elem);
 template <typename TV, typename TP>

@@ -385,6 +385,12 @@ tigre_status fill_padded(const tigre_geometry_desc& d, const TV* vol, TV* out, i
     return TIGRE_OK;
 }
 
+tigre_status fill_padded_f32(const tigre_geometry_desc& d, const float* vol, float* out, int layout,
+                             cudaStream_t st)
+{
+    return fill_padded<float>(d, vol, out, layout, st);
+}
+
 tigre_status forward_impl(tigre_geometry* g, const void* vol, tigre_dtype vt, void* proj,
                           tigre_dtype pt, int64_t a0, int64_t na, cudaStream_t st)
 {

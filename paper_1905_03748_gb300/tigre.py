@@ -34,7 +34,8 @@ EXPORTED = ["tigre_geometry_create", "tigre_geometry_destroy", "tigre_forward", 
             "tigre_tv_step", "tigre_tv_step_noalloc", "tigre_solver_opts_default", "tigre_sirt",
             "tigre_sart",
             "tigre_cgls", "tigre_cgls_begin", "tigre_cgls_iterate", "tigre_cgls_history",
-            "tigre_cgls_end", "tigre_forward_samples", "tigre_geometry_set_forward_path",
+            "tigre_cgls_end", "tigre_forward_samples", "tigre_forward_ooc", "tigre_backward_ooc",
+            "tigre_geometry_set_forward_path",
             "tigre_geometry_error_flags", "tigre_profile_enable",
             "tigre_profile_read", "tigre_launch_count", "tigre_last_error"]
 
@@ -79,6 +80,8 @@ _sigs = {
     "tigre_cgls_history": [_P, _P, ctypes.c_int],
     "tigre_cgls_end": [_P],
     "tigre_forward_samples": [_P, _I64, _I64, ctypes.POINTER(_I64)],
+    "tigre_forward_ooc": [_P, _P, _P, _I64, _I64, _I64, _P],
+    "tigre_backward_ooc": [_P, _P, ctypes.c_int, _P, _I64, _I64, ctypes.c_int, _I64, _I64, _P],
     "tigre_geometry_set_forward_path": [_P, ctypes.c_int],
     "tigre_geometry_error_flags": [_P, ctypes.POINTER(ctypes.c_int), ctypes.c_int],
     "tigre_profile_enable": [ctypes.c_int],
@@ -279,6 +282,34 @@ def tigre_forward_samples(handle, angle_begin: int, angle_count: int) -> int:
     n = _I64()
     _check(_lib.tigre_forward_samples(handle, int(angle_begin), int(angle_count), ctypes.byref(n)))
     return int(n.value)
+
+
+def _host_f32(t: torch.Tensor, name: str):
+    if t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous float32 host tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def tigre_forward_ooc(handle, vol_host: torch.Tensor, proj: torch.Tensor, angle_begin: int,
+                      angle_count: int, slab_planes: int = 0, stream=None) -> None:
+    """Out-of-core A x: host volume streamed in z-slabs, device projections."""
+    pp, pt = _dev(proj, "proj")
+    if pt != TIGRE_F32:
+        raise TypeError("proj must be float32")
+    _check(_lib.tigre_forward_ooc(handle, _host_f32(vol_host, "vol_host"), pp, int(angle_begin),
+                                  int(angle_count), int(slab_planes), _stream(stream)))
+
+
+def tigre_backward_ooc(handle, proj: torch.Tensor, vol_host: torch.Tensor, angle_begin: int,
+                       angle_count: int, weight="matched", slab_planes: int = 0,
+                       angle_chunk: int = 0, stream=None) -> None:
+    """Out-of-core A^T y into a host volume; proj on device or host."""
+    on_host = not proj.is_cuda
+    pp = _host_f32(proj, "proj") if on_host else _dev(proj, "proj")[0]
+    w = _BP[weight] if isinstance(weight, str) else int(weight)
+    _check(_lib.tigre_backward_ooc(handle, pp, int(on_host), _host_f32(vol_host, "vol_host"),
+                                   int(angle_begin), int(angle_count), w, int(slab_planes),
+                                   int(angle_chunk), _stream(stream)))
 
 
 FWD_AUTO, FWD_L1, FWD_TMA, FWD_QUAD = 0, 1, 2, 3
