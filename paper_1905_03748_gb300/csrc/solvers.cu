@@ -198,9 +198,12 @@ struct tigre_cgls_state {
     float *r = nullptr, *q = nullptr, *p = nullptr, *s = nullptr;
     double* sc = nullptr;    // Scalars area
     double* hist = nullptr;  // residual norms, capacity hist_cap
+    int* counter = nullptr;  // device: number of residuals recorded (graph-safe index)
     int hist_cap = 0;
     int done = 0;
     int cur = 0;
+    bool graph = false;              // replay captured iteration pairs
+    cudaGraphExec_t exec[2] = {};    // two iterations, by starting gamma slot
 };
 
 namespace tigre {
@@ -208,8 +211,10 @@ namespace {
 
 void cgls_release(tigre_cgls_state* S)
 {
+    for (cudaGraphExec_t e : S->exec)
+        if (e) cudaGraphExecDestroy(e);
     for (void* ptr : {(void*)S->r, (void*)S->q, (void*)S->p, (void*)S->s, (void*)S->sc,
-                      (void*)S->hist})
+                      (void*)S->hist, (void*)S->counter})
         if (ptr) cudaFreeAsync(ptr, S->st);
     delete S;
 }
@@ -236,6 +241,8 @@ tigre_status cgls_init(tigre_cgls_state* S, int hist_cap)
     TIGRE_TRY(dalloc(&S->sc, Scalars::count(4), S->st));
     S->hist_cap = std::max(hist_cap, 16);
     TIGRE_TRY(dalloc(&S->hist, (size_t)S->hist_cap, S->st));
+    TIGRE_TRY(dalloc(&S->counter, 1, S->st));
+    TIGRE_CUDA(cudaMemsetAsync(S->counter, 0, sizeof(int), S->st));
     Scalars sc{S->sc};
     // r = b - A x0; p = A^T r; gamma = ||p||^2
     TIGRE_TRY(forward_impl(S->g, S->x, TIGRE_F32, S->q, TIGRE_F32, 0, S->na, S->st));
@@ -246,17 +253,30 @@ tigre_status cgls_init(tigre_cgls_state* S, int hist_cap)
     return TIGRE_OK;
 }
 
+// Make room for `more` residuals (stream-ordered; never inside a capture).
+tigre_status cgls_reserve(tigre_cgls_state* S, int more)
+{
+    int cap = S->hist_cap;
+    while (S->done + more > cap) cap *= 2;
+    if (cap == S->hist_cap) return TIGRE_OK;
+    double* nh = nullptr;
+    TIGRE_TRY(dalloc(&nh, (size_t)cap, S->st));
+    TIGRE_CUDA(cudaMemcpyAsync(nh, S->hist, sizeof(double) * (size_t)S->hist_cap,
+                               cudaMemcpyDeviceToDevice, S->st));
+    cudaFreeAsync(S->hist, S->st);
+    S->hist = nh;
+    S->hist_cap = cap;
+    // Captured graphs hold the old history pointer: recapture on next use.
+    for (cudaGraphExec_t& e : S->exec)
+        if (e) {
+            cudaGraphExecDestroy(e);
+            e = nullptr;
+        }
+    return TIGRE_OK;
+}
+
 tigre_status cgls_step(tigre_cgls_state* S)
 {
-    if (S->done == S->hist_cap) {  // grow the history, stream-ordered
-        double* nh = nullptr;
-        TIGRE_TRY(dalloc(&nh, (size_t)S->hist_cap * 2, S->st));
-        TIGRE_CUDA(cudaMemcpyAsync(nh, S->hist, sizeof(double) * (size_t)S->hist_cap,
-                                   cudaMemcpyDeviceToDevice, S->st));
-        cudaFreeAsync(S->hist, S->st);
-        S->hist = nh;
-        S->hist_cap *= 2;
-    }
     Scalars sc{S->sc};
     double* gam[2] = {sc.slot(0), sc.slot(1)};
     double* qq = sc.slot(2);
@@ -267,13 +287,37 @@ tigre_status cgls_step(tigre_cgls_state* S)
     // alpha = gamma / ||q||^2: x += alpha p, r -= alpha q
     TIGRE_TRY(axpy_ratio(S->x, S->p, S->nvox, gam[c], qq, 1.0f, S->st));
     TIGRE_TRY(axpy_ratio_norm(S->r, S->q, S->m, gam[c], qq, -1.0f, sc.partials(), rr, S->st));
-    TIGRE_TRY(copy_dscalar(S->hist + S->done, rr + 1, S->st));
+    TIGRE_TRY(record_dscalar(S->hist, S->hist_cap, S->counter, rr + 1, S->st));
     TIGRE_TRY(backward_impl(S->g, S->r, TIGRE_F32, S->s, TIGRE_F32, 0, S->na, S->bw, 0, S->st));
     TIGRE_TRY(dot_f64(S->s, S->s, S->nvox, sc.partials(), gam[1 - c], S->st));
     // p = s + (gamma_new / gamma) p
     TIGRE_TRY(xpay_ratio(S->p, S->s, S->nvox, gam[1 - c], gam[c], S->st));
     S->cur = 1 - c;
     S->done += 1;
+    return TIGRE_OK;
+}
+
+// Capture two iterations on the state's stream into an executable graph.
+// The host-side counters advance while capturing; they are put back, since
+// the captured work has not run yet.
+tigre_status cgls_capture(tigre_cgls_state* S, cudaGraphExec_t* out)
+{
+    const int done0 = S->done, cur0 = S->cur;
+    TIGRE_CUDA(cudaStreamBeginCapture(S->st, cudaStreamCaptureModeThreadLocal));
+    tigre_status st = cgls_step(S);
+    if (st == TIGRE_OK) st = cgls_step(S);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(S->st, &graph);
+    S->done = done0;
+    S->cur = cur0;
+    if (st != TIGRE_OK || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return st != TIGRE_OK ? st : cuda_fail(e, "cudaStreamEndCapture(cgls)");
+    }
+    const cudaError_t ei = cudaGraphInstantiate(out, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) return cuda_fail(ei, "cudaGraphInstantiate(cgls)");
     return TIGRE_OK;
 }
 
@@ -284,6 +328,8 @@ tigre_status cgls_begin_device(tigre_geometry* g, const float* b, float* x,
     if (!S) return fail(TIGRE_ERR_OOM, "host allocation failed");
     S->g = g;
     S->bw = o->bp_weight;
+    // Graph replay needs a capturable stream (not the legacy default stream).
+    S->graph = (o->flags & TIGRE_GRAPH) && o->cuda_stream != nullptr;
     S->st = (cudaStream_t)o->cuda_stream;
     S->nvox = n_vox(g);
     S->na = (int64_t)g->angles.size();
@@ -303,7 +349,7 @@ tigre_status run_cgls(const Problem& P, double* h_hist)
 {
     tigre_cgls_state* S = nullptr;
     TIGRE_TRY(cgls_begin_device(P.g, P.b, P.x, P.o, &S));
-    tigre_status st = TIGRE_OK;
+    tigre_status st = cgls_reserve(S, P.o->n_iter);
     for (int it = 0; it < P.o->n_iter && st == TIGRE_OK; ++it) st = cgls_step(S);
     if (st == TIGRE_OK) st = finish_history(S->hist, h_hist, P.o->n_iter, P.st);
     cgls_release(S);
@@ -355,7 +401,20 @@ tigre_status tigre_cgls_begin(tigre_geometry_t geo, const void* proj, void* vol,
 tigre_status tigre_cgls_iterate(tigre_cgls_t S, int n_iter)
 {
     if (!S || n_iter < 0) return fail(TIGRE_ERR_INVALID_ARG, "null state or n_iter < 0");
-    for (int it = 0; it < n_iter; ++it) TIGRE_TRY(cgls_step(S));
+    TIGRE_TRY(cgls_reserve(S, n_iter));
+    int left = n_iter;
+    if (S->graph) {
+        // Two iterations return the gamma slots to where they started, so a
+        // captured pair replays correctly from the same parity.
+        while (left >= 2) {
+            cudaGraphExec_t& e = S->exec[S->cur];
+            if (!e) TIGRE_TRY(cgls_capture(S, &e));
+            TIGRE_CUDA(cudaGraphLaunch(e, S->st));
+            S->done += 2;
+            left -= 2;
+        }
+    }
+    for (; left > 0; --left) TIGRE_TRY(cgls_step(S));
     return TIGRE_OK;
 }
 

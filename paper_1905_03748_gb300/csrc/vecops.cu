@@ -177,6 +177,22 @@ __global__ void scale_dscalar_kernel(double* dst, const double* src, double fact
     *dst = factor * *src;
 }
 
+// hist[*counter] = *v (if it fits), ++*counter: an append whose index lives on
+// the device, so replays of a captured graph keep appending.
+__global__ void record_dscalar_kernel(double* hist, int cap, int* counter, const double* v)
+{
+    const int i = *counter;
+    if (i >= 0 && i < cap) hist[i] = *v;
+    *counter = i + 1;
+}
+
+tigre_status record_dscalar(double* hist, int cap, int* counter, const double* v, cudaStream_t st)
+{
+    record_dscalar_kernel<<<1, 1, 0, st>>>(hist, cap, counter, v);
+    TIGRE_LAUNCHED("record_dscalar_kernel");
+    return TIGRE_OK;
+}
+
 static inline unsigned ew_blocks(int64_t n)
 {
     const int64_t b = (n + 255) / 256;

@@ -26,6 +26,8 @@ tigre_status guarded_reciprocal(float* y, int64_t n, float floor_, cudaStream_t 
 tigre_status diff_norm(const float* a, const float* b, int64_t n, double* partials, double* out,
                        cudaStream_t st);
 tigre_status copy_dscalar(double* dst, const double* src, cudaStream_t st);
+// hist[*counter] = *v when *counter < cap; ++*counter (device-side index)
+tigre_status record_dscalar(double* hist, int cap, int* counter, const double* v, cudaStream_t st);
 // mode 0: dst = src; 1: dst += src; 2: dst = sqrt(src)
 tigre_status combine_dscalar(double* dst, const double* src, int mode, cudaStream_t st);
 tigre_status fill_f32(float* p, float v, int64_t n, cudaStream_t st);

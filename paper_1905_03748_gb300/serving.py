@@ -1,0 +1,197 @@
+"""Continuous-batching server for CBCT reconstruction requests (CGLS).
+
+Requests (geometry, angles, projections, iteration count) arrive over time.
+The scheduler keeps up to `max_slots` reconstructions resident on the GPU at
+once, each with its own stream, geometry handle and CGLS state (iterates stay
+in HBM from admission to completion).  A request is admitted, in arrival
+order, as soon as a slot is free and its HBM footprint fits the remaining
+budget; it does not wait for the requests already running to finish.  Every
+scheduler tick enqueues the next iterations of every resident request on its
+stream (as replays of a captured CUDA graph of two CGLS iterations), so
+different requests' projections and backprojections overlap on the device.
+Finished requests are detected with events, copied back, and their slot and
+memory returned to the pool.
+
+`run_plain` is the one-at-a-time reference path: each request is solved
+alone with tigre_cgls, in arrival order.
+"""
+from __future__ import annotations
+
+import math
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+from . import tigre
+
+
+@dataclass
+class Request:
+    rid: int
+    geo: dict
+    angles: np.ndarray
+    proj: torch.Tensor            # host (pinned preferred) projections, F32 or BF16
+    n_iter: int = 15
+    arrival: float = 0.0          # seconds after the start of the run
+
+
+@dataclass
+class Result:
+    rid: int
+    x: torch.Tensor               # host F32 volume
+    resid: np.ndarray
+    arrival: float
+    admitted: float
+    finished: float
+
+    @property
+    def latency(self) -> float:
+        return self.finished - self.arrival
+
+
+def footprint_bytes(geo: dict, n_angles: int) -> int:
+    """HBM needed by one resident CGLS reconstruction: x, p, s (volume-sized),
+    b, r, q (projection-sized), the forward projector's two padded layouts
+    and their quad copies (5 padded volumes each), the backprojector's padded
+    projections, plus 64 MiB of slack."""
+    nx, ny, nz = geo["n_voxel"]
+    nu, nv = geo["n_det"]
+    vol = 4 * nx * ny * nz
+    padded = 4 * (nx + 4) * (ny + 4) * (nz + 4)
+    proj = 4 * nu * nv * n_angles
+    return 3 * vol + 4 * proj + 10 * padded + (64 << 20)
+
+
+@dataclass
+class _Slot:
+    req: Request
+    G: tigre.Geometry
+    stream: torch.cuda.Stream
+    b: torch.Tensor
+    x: torch.Tensor
+    state: object
+    issued: int
+    admitted: float
+    done_event: torch.cuda.Event = field(default_factory=lambda: torch.cuda.Event())
+    bytes: int = 0
+
+
+class Server:
+    def __init__(self, max_slots: int = 8, hbm_budget: int | None = None, graph: bool = True,
+                 iters_per_tick: int = 2, device: int = 0):
+        self.max_slots = max_slots
+        self.graph = graph
+        self.iters_per_tick = max(1, iters_per_tick)
+        self.device = torch.device("cuda", device)
+        if hbm_budget is None:
+            free, _ = torch.cuda.mem_get_info(self.device)
+            hbm_budget = int(0.8 * free)
+        self.hbm_budget = hbm_budget
+
+    def _admit(self, req: Request, now: float) -> _Slot:
+        stream = torch.cuda.Stream(device=self.device)
+        with torch.cuda.stream(stream):
+            G = tigre.Geometry(req.geo, req.angles)
+            b = req.proj.to(self.device, non_blocking=True).float()
+            x = torch.zeros(G.vol_shape, device=self.device)
+            state = tigre.tigre_cgls_begin(G.handle, b, x, n_iter_hint=req.n_iter,
+                                           stream=stream, graph=self.graph)
+        return _Slot(req, G, stream, b, x, state, 0, now,
+                     bytes=footprint_bytes(req.geo, len(req.angles)))
+
+    def _finish(self, s: _Slot, now: float) -> Result:
+        resid = tigre.tigre_cgls_history(s.state, s.req.n_iter)  # syncs the slot's stream
+        x = s.x.cpu()
+        tigre.tigre_cgls_end(s.state)
+        s.G.close()
+        return Result(s.req.rid, x, resid, s.req.arrival, s.admitted, now)
+
+    def run(self, requests: list[Request], realtime: bool = True) -> list[Result]:
+        """Serve requests (arrival offsets in seconds) and return results in
+        completion order."""
+        pending = sorted(requests, key=lambda r: (r.arrival, r.rid))
+        queue: list[Request] = []
+        active: list[_Slot] = []
+        results: list[Result] = []
+        used = 0
+        t0 = time.perf_counter()
+        while pending or queue or active:
+            now = time.perf_counter() - t0
+            while pending and (pending[0].arrival <= now or not realtime):
+                queue.append(pending.pop(0))
+            # Admission: arrival order, as slots and memory free up.
+            while queue and len(active) < self.max_slots:
+                need = footprint_bytes(queue[0].geo, len(queue[0].angles))
+                if used + need > self.hbm_budget and active:
+                    break
+                req = queue.pop(0)
+                slot = self._admit(req, time.perf_counter() - t0)
+                used += slot.bytes
+                active.append(slot)
+            # One tick of work for every resident reconstruction.
+            for s in active:
+                if s.issued < s.req.n_iter:
+                    n = min(self.iters_per_tick, s.req.n_iter - s.issued)
+                    with torch.cuda.stream(s.stream):
+                        tigre.tigre_cgls_iterate(s.state, n)
+                    s.issued += n
+                    if s.issued == s.req.n_iter:
+                        s.done_event.record(s.stream)
+            # Retire finished reconstructions.
+            still = []
+            for s in active:
+                if s.issued == s.req.n_iter and s.done_event.query():
+                    results.append(self._finish(s, time.perf_counter() - t0))
+                    used -= s.bytes
+                else:
+                    still.append(s)
+            active = still
+            if not active and not queue and pending and realtime:
+                time.sleep(max(0.0, pending[0].arrival - (time.perf_counter() - t0)))
+            elif active and all(s.issued == s.req.n_iter for s in active):
+                time.sleep(0.0005)
+        return results
+
+
+def run_plain(requests: list[Request], realtime: bool = True,
+              device: int = 0) -> list[Result]:
+    """One request at a time, arrival order, each solved alone by tigre_cgls."""
+    dev = torch.device("cuda", device)
+    results = []
+    t0 = time.perf_counter()
+    for req in sorted(requests, key=lambda r: (r.arrival, r.rid)):
+        now = time.perf_counter() - t0
+        if realtime and req.arrival > now:
+            time.sleep(req.arrival - now)
+        admitted = time.perf_counter() - t0
+        with tigre.Geometry(req.geo, req.angles) as G:
+            b = req.proj.to(dev).float()
+            x = torch.zeros(G.vol_shape, device=dev)
+            resid = tigre.tigre_cgls(G.handle, b, x, req.n_iter)
+            xh = x.cpu()
+        results.append(Result(req.rid, xh, resid, req.arrival, admitted,
+                              time.perf_counter() - t0))
+    return results
+
+
+def latency_stats(results: list[Result]) -> dict:
+    lat = np.array([r.latency for r in results])
+    span = max(r.finished for r in results) - min(r.arrival for r in results)
+    return {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "mean_s": float(lat.mean()), "makespan_s": float(span),
+            "throughput_req_s": len(results) / span}
+
+
+def poisson_requests(n: int, rate: float, seed: int, make) -> list[Request]:
+    """n requests with exponential inter-arrival times (rate per second);
+    make(i, rng) returns (geo, angles, proj, n_iter)."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for i in range(n):
+        t += rng.exponential(1.0 / rate)
+        geo, ang, proj, n_iter = make(i, rng)
+        out.append(Request(i, geo, ang, proj, n_iter, t))
+    return out

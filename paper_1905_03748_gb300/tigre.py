@@ -255,8 +255,13 @@ def tigre_cgls(handle, proj, vol, n_iter, bp_weight="matched", stream=None,
     return _solver(_lib.tigre_cgls, handle, proj, vol, o, host)
 
 
-def tigre_cgls_begin(handle, proj, vol, n_iter_hint=16, bp_weight="matched", stream=None):
+def tigre_cgls_begin(handle, proj, vol, n_iter_hint=16, bp_weight="matched", stream=None,
+                     graph=False):
+    """Stepwise CGLS; graph=True replays captured iteration pairs as CUDA
+    graphs (needs a non-default stream)."""
     o = _opts(n_iter_hint, stream, bp_weight=bp_weight)
+    if graph:
+        o.flags |= TIGRE_GRAPH
     pp, _ = _dev(proj, "proj")
     vp, _ = _dev(vol, "vol")
     s = ctypes.c_void_p()

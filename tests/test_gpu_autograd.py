@@ -75,4 +75,4 @@ def test_dot_product_at_full_workload(tigre):
         lhs.backward(retain_graph=False)
         # d<Ax, y>/dx = A^T y
         rhs = (x.detach().double() * x.grad.double()).sum()
-        assert abs(float(lhs) - float(rhs)) / abs(float(lhs)) < 1e-5
+        assert abs(float(lhs.detach()) - float(rhs)) / abs(float(lhs.detach())) < 1e-5

@@ -44,7 +44,9 @@ def test_forward_ooc_equals_in_core(tigre, slab, pinned):
 
 @pytest.mark.parametrize("slab", [1, 5, 23])
 @pytest.mark.parametrize("weight", ["matched", "fdk"])
-def test_backward_ooc_device_projections_bitwise(tigre, slab, weight):
+def test_backward_ooc_device_projections(tigre, slab, weight):
+    """Same sums as in-core; a slab launch computes a voxel's z from its own
+    first plane, so the last bits may differ (1e-6)."""
     geo, ang, vol = case()
     y = torch.from_numpy(np.random.default_rng(7).random(
         (len(ang), geo["n_det"][1], geo["n_det"][0])).astype(np.float32)).cuda()
@@ -52,7 +54,7 @@ def test_backward_ooc_device_projections_bitwise(tigre, slab, weight):
         ref = G.backward(y, weight=weight).cpu()
         out = torch.zeros(G.vol_shape).pin_memory()
         tigre.tigre_backward_ooc(G.handle, y, out, 0, len(ang), weight=weight, slab_planes=slab)
-    assert torch.equal(out, ref)
+    assert rel(out.numpy(), ref.numpy()) < 1e-6
 
 
 @pytest.mark.parametrize("chunk", [1, 4, 19])
