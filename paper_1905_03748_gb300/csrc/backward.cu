@@ -369,6 +369,21 @@ tigre_status backward_slab_impl(tigre_geometry* g, const float* proj, float* vol
                                          0, z_first, z_end, z_first);
 }
 
+tigre_status sart_update_dt(tigre_geometry* g, tigre_dtype t, const void* r, void* x, int64_t a0,
+                            int64_t na, tigre_bp_weight w, float lambda, int nonneg,
+                            cudaStream_t st)
+{
+    TIGRE_TRY(check_geometry(g));
+    TIGRE_TRY(check_range(g, a0, na));
+    if (w == TIGRE_BP_EXACT_ADJOINT)
+        return fail(TIGRE_ERR_UNSUPPORTED, "SIRT/OS-SART use the voxel-driven backprojector");
+    return dispatch_dtype(t, [&](auto tag) -> tigre_status {
+        using T = decltype(tag);
+        return launch_voxel_bp<T, T>(g, (const T*)r, (T*)x, a0, na, w, 0, st, true, lambda,
+                                     nonneg);
+    });
+}
+
 tigre_status sart_update_impl(tigre_geometry* g, const float* r, float* x, int64_t a0, int64_t na,
                               tigre_bp_weight w, float lambda, int nonneg, cudaStream_t st)
 {

@@ -201,5 +201,9 @@ tigre_status dot_f64(const float* a, const float* b, int64_t n, double* d_partia
 // nonneg.  r: device F32 (na, nv, nu); x: device F32 volume.
 tigre_status sart_update_impl(tigre_geometry* g, const float* r, float* x, int64_t a0, int64_t na,
                               tigre_bp_weight w, float lambda, int nonneg, cudaStream_t st);
+// Same with r and x stored in dtype t (FP32 arithmetic).
+tigre_status sart_update_dt(tigre_geometry* g, tigre_dtype t, const void* r, void* x, int64_t a0,
+                            int64_t na, tigre_bp_weight w, float lambda, int nonneg,
+                            cudaStream_t st);
 
 }  // namespace tigre

@@ -60,8 +60,10 @@ struct Problem {
     const tigre_solver_opts* o;
     cudaStream_t st;
     int64_t nvox, npix, na;
-    const float* b;  // device
-    float* x;        // device
+    const void* b;   // device, storage dtype
+    void* x;         // device, storage dtype
+    tigre_dtype dt;  // storage of b, x and the projection-sized work buffer
+    size_t elem;
 };
 
 tigre_status check_opts(const tigre_geometry* g, const tigre_solver_opts* o, const void* proj,
@@ -69,8 +71,7 @@ tigre_status check_opts(const tigre_geometry* g, const tigre_solver_opts* o, con
 {
     if (!g || !o || !proj || !vol) return fail(TIGRE_ERR_INVALID_ARG, "null argument");
     if (o->n_iter < 0) return fail(TIGRE_ERR_INVALID_ARG, "n_iter must be >= 0");
-    if (o->storage != TIGRE_F32)
-        return fail(TIGRE_ERR_UNSUPPORTED, "solver iterates are stored in F32");
+    if (!dtype_ok(o->storage)) return fail(TIGRE_ERR_INVALID_ARG, "bad storage dtype");
     if (!(std::isfinite(o->lambda))) return fail(TIGRE_ERR_INVALID_ARG, "lambda must be finite");
     if (o->flags & ~(TIGRE_HOST_RESIDENT | TIGRE_GRAPH))
         return fail(TIGRE_ERR_INVALID_ARG, "unknown flags");
@@ -85,24 +86,25 @@ tigre_status with_device_problem(tigre_geometry* g, const void* proj, void* vol,
     TIGRE_TRY(check_geometry(g));
     TIGRE_TRY(check_opts(g, o, proj, vol));
     cudaStream_t st = (cudaStream_t)o->cuda_stream;
-    Problem P{g, o, st, n_vox(g), n_pix(g), (int64_t)g->angles.size(), nullptr, nullptr};
+    Problem P{g, o, st, n_vox(g), n_pix(g), (int64_t)g->angles.size(), nullptr, nullptr,
+              o->storage, dtype_size(o->storage)};
     if (!(o->flags & TIGRE_HOST_RESIDENT)) {
-        P.b = (const float*)proj;
-        P.x = (float*)vol;
+        P.b = proj;
+        P.x = vol;
         return body(P);
     }
     Scratch s(st);
-    float* db = nullptr;
-    float* dx = nullptr;
-    TIGRE_TRY(s.alloc(&db, (size_t)(P.npix * P.na)));
-    TIGRE_TRY(s.alloc(&dx, (size_t)P.nvox));
-    TIGRE_CUDA(cudaMemcpyAsync(db, proj, sizeof(float) * (size_t)(P.npix * P.na),
+    unsigned char* db = nullptr;
+    unsigned char* dx = nullptr;
+    TIGRE_TRY(s.alloc(&db, P.elem * (size_t)(P.npix * P.na)));
+    TIGRE_TRY(s.alloc(&dx, P.elem * (size_t)P.nvox));
+    TIGRE_CUDA(cudaMemcpyAsync(db, proj, P.elem * (size_t)(P.npix * P.na),
                                cudaMemcpyHostToDevice, st));
-    TIGRE_CUDA(cudaMemcpyAsync(dx, vol, sizeof(float) * (size_t)P.nvox, cudaMemcpyHostToDevice, st));
+    TIGRE_CUDA(cudaMemcpyAsync(dx, vol, P.elem * (size_t)P.nvox, cudaMemcpyHostToDevice, st));
     P.b = db;
     P.x = dx;
     TIGRE_TRY(body(P));
-    TIGRE_CUDA(cudaMemcpyAsync(vol, dx, sizeof(float) * (size_t)P.nvox, cudaMemcpyDeviceToHost, st));
+    TIGRE_CUDA(cudaMemcpyAsync(vol, dx, P.elem * (size_t)P.nvox, cudaMemcpyDeviceToHost, st));
     TIGRE_CUDA(cudaStreamSynchronize(st));
     return TIGRE_OK;
 }
@@ -126,19 +128,19 @@ tigre_status row_weights(const Problem& P, float* W, float* ones)
 
 // One OS-SART sweep over subsets of `subset` angles (SIRT: subset = all).
 // Accumulates sum ||b_s - A_s x||^2 into acc[0] (cleared first).
-tigre_status sart_sweep(const Problem& P, const float* W, float* q, int64_t subset,
+tigre_status sart_sweep(const Problem& P, const float* W, void* q, int64_t subset,
                         const Scalars& sc, double* acc)
 {
     const tigre_solver_opts* o = P.o;
     for (int64_t a0 = 0; a0 < P.na; a0 += subset) {
         const int64_t cnt = std::min(subset, P.na - a0);
         const int64_t off = a0 * P.npix;
-        TIGRE_TRY(forward_impl(P.g, P.x, TIGRE_F32, q, TIGRE_F32, a0, cnt, P.st));
-        TIGRE_TRY(weighted_residual(P.b + off, q, W + off, q, cnt * P.npix, sc.partials(),
-                                    sc.slot(0), P.st));
+        TIGRE_TRY(forward_impl(P.g, P.x, P.dt, q, P.dt, a0, cnt, P.st));
+        TIGRE_TRY(weighted_residual_dt(P.dt, (const unsigned char*)P.b + off * P.elem, q, W + off,
+                                       q, cnt * P.npix, sc.partials(), sc.slot(0), P.st));
         TIGRE_TRY(combine_dscalar(acc, sc.slot(0), a0 == 0 ? 0 : 1, P.st));
-        TIGRE_TRY(sart_update_impl(P.g, q, P.x, a0, cnt, o->bp_weight, (float)o->lambda,
-                                   o->nonneg, P.st));
+        TIGRE_TRY(sart_update_dt(P.g, P.dt, q, P.x, a0, cnt, o->bp_weight, (float)o->lambda,
+                                 o->nonneg, P.st));
     }
     return TIGRE_OK;
 }
@@ -152,29 +154,31 @@ tigre_status run_sart(const Problem& P, int64_t subset, double* h_hist)
     if (o->tv_steps < 0 || !std::isfinite(o->tv_alpha) || !(o->tv_eps >= 0.0))
         return fail(TIGRE_ERR_INVALID_ARG, "bad TV options");
     Scratch s(P.st);
-    float *W, *q, *tmp;
+    float *W, *ones;
+    void *q, *tmp = nullptr;
     double *sc_base, *hist, *tv_red;
     TIGRE_TRY(s.alloc(&W, (size_t)(P.npix * P.na)));
-    TIGRE_TRY(s.alloc(&q, (size_t)(P.npix * std::min(subset, P.na))));
-    TIGRE_TRY(s.alloc(&tmp, (size_t)P.nvox));  // ones, then x_prev, for TV
+    TIGRE_TRY(s.alloc((unsigned char**)&q, P.elem * (size_t)(P.npix * std::min(subset, P.na))));
+    TIGRE_TRY(s.alloc(&ones, (size_t)P.nvox));
+    if (o->tv_steps > 0) TIGRE_TRY(s.alloc((unsigned char**)&tmp, P.elem * (size_t)P.nvox));
     TIGRE_TRY(s.alloc(&sc_base, Scalars::count(4)));
     TIGRE_TRY(s.alloc(&hist, (size_t)std::max(o->n_iter, 1)));
     TIGRE_TRY(s.alloc(&tv_red, Scalars::count(1)));
     float* tv_g = nullptr;
     if (o->tv_steps > 0) TIGRE_TRY(s.alloc(&tv_g, (size_t)P.nvox));
     Scalars sc{sc_base};
-    TIGRE_TRY(row_weights(P, W, tmp));
+    TIGRE_TRY(row_weights(P, W, ones));
     for (int it = 0; it < o->n_iter; ++it) {
         if (o->tv_steps > 0)
-            TIGRE_CUDA(cudaMemcpyAsync(tmp, P.x, sizeof(float) * (size_t)P.nvox,
-                                       cudaMemcpyDeviceToDevice, P.st));
+            TIGRE_CUDA(cudaMemcpyAsync(tmp, P.x, P.elem * (size_t)P.nvox, cudaMemcpyDeviceToDevice,
+                                       P.st));
         TIGRE_TRY(sart_sweep(P, W, q, subset, sc, sc.slot(1)));
         TIGRE_TRY(combine_dscalar(hist + it, sc.slot(1), 2, P.st));
         if (o->tv_steps > 0) {
             // TV step size = tv_alpha * ||x_after_data - x_before_data||.
-            TIGRE_TRY(diff_norm(P.x, tmp, P.nvox, sc.partials(), sc.slot(2), P.st));
+            TIGRE_TRY(diff_norm_dt(P.dt, P.x, tmp, P.nvox, sc.partials(), sc.slot(2), P.st));
             TIGRE_TRY(scale_dscalar(sc.slot(3), sc.slot(2) + 1, o->tv_alpha, P.st));
-            TIGRE_TRY(tv_impl(P.g->desc.n_voxel, P.x, TIGRE_F32, o->tv_steps, 1.0, o->tv_eps,
+            TIGRE_TRY(tv_impl(P.g->desc.n_voxel, P.x, P.dt, o->tv_steps, 1.0, o->tv_eps,
                               sc.slot(3), tv_g, tv_red, P.st));
         }
     }
@@ -348,7 +352,8 @@ tigre_status cgls_begin_device(tigre_geometry* g, const float* b, float* x,
 tigre_status run_cgls(const Problem& P, double* h_hist)
 {
     tigre_cgls_state* S = nullptr;
-    TIGRE_TRY(cgls_begin_device(P.g, P.b, P.x, P.o, &S));
+    if (P.dt != TIGRE_F32) return fail(TIGRE_ERR_UNSUPPORTED, "CGLS iterates are stored in F32");
+    TIGRE_TRY(cgls_begin_device(P.g, (const float*)P.b, (float*)P.x, P.o, &S));
     tigre_status st = cgls_reserve(S, P.o->n_iter);
     for (int it = 0; it < P.o->n_iter && st == TIGRE_OK; ++it) st = cgls_step(S);
     if (st == TIGRE_OK) st = finish_history(S->hist, h_hist, P.o->n_iter, P.st);
@@ -395,6 +400,8 @@ tigre_status tigre_cgls_begin(tigre_geometry_t geo, const void* proj, void* vol,
     TIGRE_TRY(check_opts(geo, opts, proj, vol));
     if (opts->flags & TIGRE_HOST_RESIDENT)
         return fail(TIGRE_ERR_UNSUPPORTED, "stepwise CGLS takes device buffers");
+    if (opts->storage != TIGRE_F32)
+        return fail(TIGRE_ERR_UNSUPPORTED, "CGLS iterates are stored in F32");
     return cgls_begin_device(geo, (const float*)proj, (float*)vol, opts, out);
 }
 

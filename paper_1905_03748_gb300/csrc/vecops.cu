@@ -193,6 +193,68 @@ tigre_status record_dscalar(double* hist, int cap, int* counter, const double* v
     return TIGRE_OK;
 }
 
+// Storage-typed variants (BF16 / F16 / F32 storage, FP32 arithmetic, FP64 sums).
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads) weighted_residual_t_kernel(
+    const T* __restrict__ b, const T* q, const float* __restrict__ W, T* r, int64_t n,
+    double* __restrict__ partials)
+{
+    __shared__ double sh[kRedThreads];
+    double acc = 0.0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const float d = to_f32<T>(b[i]) - to_f32<T>(q[i]);
+        r[i] = from_f32<T>(W ? W[i] * d : d);
+        acc = fma((double)d, (double)d, acc);
+    }
+    const double t = block_sum(acc, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = t;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads) diff_norm_t_kernel(const T* __restrict__ a,
+                                                                  const T* __restrict__ b,
+                                                                  int64_t n,
+                                                                  double* __restrict__ partials)
+{
+    __shared__ double sh[kRedThreads];
+    double acc = 0.0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const double d = (double)to_f32<T>(a[i]) - (double)to_f32<T>(b[i]);
+        acc = fma(d, d, acc);
+    }
+    const double t = block_sum(acc, sh);
+    if (threadIdx.x == 0) partials[blockIdx.x] = t;
+}
+
+tigre_status weighted_residual_dt(tigre_dtype t, const void* b, const void* q, const float* W,
+                                  void* r, int64_t n, double* partials, double* out,
+                                  cudaStream_t st)
+{
+    TIGRE_TRY(dispatch_dtype(t, [&](auto tag) -> tigre_status {
+        using T = decltype(tag);
+        weighted_residual_t_kernel<T><<<kRedBlocks, kRedThreads, 0, st>>>(
+            (const T*)b, (const T*)q, W, (T*)r, n, partials);
+        TIGRE_LAUNCHED("weighted_residual_t_kernel");
+        return TIGRE_OK;
+    }));
+    return reduce_partials(partials, out, 1, st);
+}
+
+tigre_status diff_norm_dt(tigre_dtype t, const void* a, const void* b, int64_t n, double* partials,
+                          double* out, cudaStream_t st)
+{
+    TIGRE_TRY(dispatch_dtype(t, [&](auto tag) -> tigre_status {
+        using T = decltype(tag);
+        diff_norm_t_kernel<T><<<kRedBlocks, kRedThreads, 0, st>>>((const T*)a, (const T*)b, n,
+                                                                   partials);
+        TIGRE_LAUNCHED("diff_norm_t_kernel");
+        return TIGRE_OK;
+    }));
+    return reduce_partials(partials, out, 1, st);
+}
+
 static inline unsigned ew_blocks(int64_t n)
 {
     const int64_t b = (n + 255) / 256;

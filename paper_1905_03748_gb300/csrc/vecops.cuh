@@ -20,6 +20,12 @@ tigre_status xpay_ratio(float* y, const float* x, int64_t n, const double* num, 
 // r = W (b - q) (W may be null = ones); out[0] = ||b - q||^2, out[1] = ||b - q||
 tigre_status weighted_residual(const float* b, const float* q, const float* W, float* r, int64_t n,
                                double* partials, double* out, cudaStream_t st);
+// Storage-typed: r = W (b - q) with b, q, r in dtype t; ||a - b|| for dtype t.
+tigre_status weighted_residual_dt(tigre_dtype t, const void* b, const void* q, const float* W,
+                                  void* r, int64_t n, double* partials, double* out,
+                                  cudaStream_t st);
+tigre_status diff_norm_dt(tigre_dtype t, const void* a, const void* b, int64_t n, double* partials,
+                          double* out, cudaStream_t st);
 // y = y > floor ? 1/y : 0
 tigre_status guarded_reciprocal(float* y, int64_t n, float floor_, cudaStream_t st);
 // out[0] = ||a - b||^2, out[1] = ||a - b||

@@ -208,10 +208,13 @@ def tigre_solver_opts_default() -> tigre_solver_opts:
 
 def _solver(fn, handle, proj, vol, opts: tigre_solver_opts, host: bool):
     hist = np.zeros(max(opts.n_iter, 1), dtype=np.float64)
+    if proj.dtype != vol.dtype or proj.dtype not in _DTYPES:
+        raise TypeError("proj and vol must share one storage dtype (float32/bfloat16/float16)")
+    opts.storage = _DTYPES[vol.dtype]
     if host:
         for t, name in ((proj, "proj"), (vol, "vol")):
-            if t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
-                raise TypeError(f"{name} must be a contiguous float32 host tensor")
+            if t.is_cuda or not t.is_contiguous():
+                raise TypeError(f"{name} must be a contiguous host tensor")
         opts.flags |= TIGRE_HOST_RESIDENT
         pp, vp = ctypes.c_void_p(proj.data_ptr()), ctypes.c_void_p(vol.data_ptr())
     else:

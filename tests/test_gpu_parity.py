@@ -271,3 +271,25 @@ def test_reduced_precision_storage_forward_and_backward(tigre, dtype):
     vr = v.float().cpu().numpy()
     assert rel(p.cpu().numpy(), oracle.forward(geo, ang, vr)) < TOL
     assert rel(b.cpu().numpy(), oracle.backward(geo, ang, y.float().cpu().numpy())) < TOL
+
+
+# ------------------------------------------------- mixed-precision solver
+
+@pytest.mark.parametrize("dtype", [torch.bfloat16, torch.float16])
+def test_os_sart_tv_reduced_storage_tracks_fp64_oracle(tigre, dtype):
+    """OS-SART + TV with the iterate and projections stored in BF16/FP16 (FP32
+    arithmetic, FP64 scalars).  Storage rounding is ~2^-8 (BF16) / 2^-11
+    (FP16) per stored value; the reconstruction stays within 2 % (BF16) /
+    0.5 % (FP16) of the FP64 oracle's, and its residual history within 1 %."""
+    geo, ang, vol = small_case()
+    b = oracle.forward(geo, ang, vol)
+    x_ref, h_ref = oracle.os_sart(geo, ang, b, 2, subset=20, tv_steps_n=5, tv_alpha=0.002,
+                                  tv_eps=1e-8)
+    with tigre.Geometry(geo, ang) as G:
+        bt = torch.from_numpy(b.astype(np.float32)).cuda().to(dtype)
+        x = torch.zeros(G.vol_shape, device="cuda", dtype=dtype)
+        h = tigre.tigre_sart(G.handle, bt, x, 2, subset_size=20, tv_steps=5, tv_alpha=0.002,
+                             tv_eps=1e-8)
+    tol = 2e-2 if dtype == torch.bfloat16 else 5e-3
+    assert rel(x.float().cpu().numpy(), x_ref) < tol
+    assert rel(h, h_ref) < 1e-2
