@@ -5,7 +5,9 @@
 
 Workload: N^3 volume (256 mm field of view), N^2 detector, A angles, seeded
 piecewise-constant phantom (random ellipsoids, seed 3), projections with
-Gaussian noise of 1 % of their maximum.  For each storage type it reports:
+Gaussian noise of 1 % of their maximum on every ray that crosses the object
+(rays that only graze the support would have their noise multiplied by the
+huge SART row weight 1/(A 1)).  For each storage type it reports:
   * forward / backprojection relative difference from the FP32-storage
     result (the error the storage type itself adds);
   * OS-SART (subsets of 20 angles) + TV (20 gradient steps, alpha 0.002)
@@ -39,12 +41,13 @@ def main():
     d = 256.0 / a.n
     x_true = synth.voxelize(synth.random_ellipsoids(a.n, d, 50, seed=3), geo["n_voxel"],
                             geo["d_voxel"])
-    out = {"n": a.n, "angles": a.angles, "iters": a.iters, "noise": "1% of max, seeded",
+    out = {"n": a.n, "angles": a.angles, "iters": a.iters,
+           "noise": "1% of max b, seeded, on rays crossing the object",
            "storage": {}}
     with tigre.Geometry(geo, ang) as G:
         xt = torch.from_numpy(x_true).cuda()
         b = G.forward(xt)
-        b_np = synth.add_noise(b.cpu().numpy(), 0.01, seed=4)
+        b_np = synth.add_noise(b.cpu().numpy(), 0.01, seed=4, object_only=True)
         b_noisy = torch.from_numpy(b_np).cuda()
         p32 = b
         bp32 = G.backward(b_noisy, weight="matched")

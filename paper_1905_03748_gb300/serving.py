@@ -64,6 +64,11 @@ def footprint_bytes(geo: dict, n_angles: int) -> int:
     return 3 * vol + 4 * proj + 10 * padded + (64 << 20)
 
 
+def work_estimate(req: Request) -> float:
+    """Voxel-angle pairs visited by the whole reconstruction."""
+    return float(np.prod(req.geo["n_voxel"])) * len(req.angles) * (req.n_iter + 1)
+
+
 @dataclass
 class _Slot:
     req: Request
@@ -80,7 +85,14 @@ class _Slot:
 
 class Server:
     def __init__(self, max_slots: int = 8, hbm_budget: int | None = None, graph: bool = True,
-                 iters_per_tick: int = 2, device: int = 0):
+                 iters_per_tick: int = 2, device: int = 0, policy: str = "fifo"):
+        """policy: "fifo" admits in arrival order; "sjf" admits the queued
+        request with the least estimated work (voxels x angles x iterations)
+        first, which shortens the typical latency when big and small
+        reconstructions are mixed."""
+        if policy not in ("fifo", "sjf"):
+            raise ValueError("policy must be 'fifo' or 'sjf'")
+        self.policy = policy
         self.max_slots = max_slots
         self.graph = graph
         self.iters_per_tick = max(1, iters_per_tick)
@@ -121,7 +133,10 @@ class Server:
             now = time.perf_counter() - t0
             while pending and (pending[0].arrival <= now or not realtime):
                 queue.append(pending.pop(0))
-            # Admission: arrival order, as slots and memory free up.
+            # Admission as slots and memory free up (arrival order, or least
+            # work first).
+            if self.policy == "sjf":
+                queue.sort(key=lambda r: (work_estimate(r), r.arrival))
             while queue and len(active) < self.max_slots:
                 need = footprint_bytes(queue[0].geo, len(queue[0].angles))
                 if used + need > self.hbm_budget and active:

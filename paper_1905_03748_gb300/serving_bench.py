@@ -46,7 +46,7 @@ def work(reqs):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--n", type=int, default=16)
+    ap.add_argument("--n", type=int, default=24)
     ap.add_argument("--rate", type=float, default=20.0)
     ap.add_argument("--seed", type=int, default=5)
     ap.add_argument("--iters", type=int, default=15)
@@ -57,20 +57,21 @@ def main():
     # warm both paths on one small request (module load, first allocations)
     serving.run_plain(reqs[:1], realtime=False)
     plain = serving.run_plain(reqs, realtime=True)
-    server = serving.Server(max_slots=a.slots, graph=True, iters_per_tick=2)
-    mixed = server.run(reqs, realtime=True)
     by_id = {r.rid: r for r in plain}
-    maxdiff = max(float((r.x - by_id[r.rid].x).abs().max()) for r in mixed)
     total = work(reqs)
-    sp, sm = serving.latency_stats(plain), serving.latency_stats(mixed)
+    sp = serving.latency_stats(plain)
     out = {"requests": a.n, "rate_per_s": a.rate, "cgls_iters": a.iters,
            "sizes": sorted(int(r.geo["n_voxel"][0]) for r in reqs),
-           "plain": dict(sp, gvox_ang_s=total / sp["makespan_s"] / 1e9),
-           "continuous_batching": dict(sm, gvox_ang_s=total / sm["makespan_s"] / 1e9,
-                                       slots=a.slots),
-           "p50_speedup": sp["p50_s"] / sm["p50_s"], "p99_speedup": sp["p99_s"] / sm["p99_s"],
-           "throughput_ratio": sm["throughput_req_s"] / sp["throughput_req_s"],
-           "max_abs_diff_vs_alone": maxdiff}
+           "plain": dict(sp, gvox_ang_s=total / sp["makespan_s"] / 1e9)}
+    for policy in ("fifo", "sjf"):
+        server = serving.Server(max_slots=a.slots, graph=True, iters_per_tick=2, policy=policy)
+        mixed = server.run(reqs, realtime=True)
+        sm = serving.latency_stats(mixed)
+        out[f"continuous_batching_{policy}"] = dict(
+            sm, gvox_ang_s=total / sm["makespan_s"] / 1e9, slots=a.slots,
+            p50_speedup=sp["p50_s"] / sm["p50_s"], p99_speedup=sp["p99_s"] / sm["p99_s"],
+            throughput_ratio=sm["throughput_req_s"] / sp["throughput_req_s"],
+            max_abs_diff_vs_alone=max(float((r.x - by_id[r.rid].x).abs().max()) for r in mixed))
     print(json.dumps(out))
 
 

@@ -209,11 +209,18 @@ def phantom(name: str, n: int, d: float, seed: int | None = None, dtype=np.float
     return voxelize(ells, (n, n, n), (d, d, d), dtype=dtype, z_range=z_range)
 
 
-def add_noise(b: np.ndarray, sigma_rel: float, seed: int) -> np.ndarray:
-    """Gaussian noise with standard deviation sigma_rel * max(b), seeded."""
+def add_noise(b: np.ndarray, sigma_rel: float, seed: int, object_only: bool = False) -> np.ndarray:
+    """Gaussian noise with standard deviation sigma_rel * max(b), seeded.
+
+    object_only=True adds it only to rays that cross the object (b > 0): rays
+    that only graze the volume's support have a near-zero length, and noise
+    there is amplified by SART's row weights 1/(A 1)."""
     rng = np.random.default_rng(seed)
     sigma = sigma_rel * float(np.max(b))
-    return (b + rng.normal(0.0, sigma, size=b.shape)).astype(b.dtype)
+    noise = rng.normal(0.0, sigma, size=b.shape)
+    if object_only:
+        noise = np.where(b > 0, noise, 0.0)
+    return (b + noise).astype(b.dtype)
 
 
 def random_volume(shape, seed: int, dtype=np.float32) -> np.ndarray:
