@@ -21,7 +21,9 @@ from . import synth, tigre
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--op", choices=["forward", "backward", "adjoint", "tv"], default="forward")
+    ap.add_argument("--op", choices=["forward", "backward", "adjoint", "tv", "forward_ooc",
+                                     "backward_ooc"], default="forward")
+    ap.add_argument("--slab", type=int, default=0, help="out-of-core slab planes (0 = auto)")
     ap.add_argument("--weight", choices=["matched", "fdk"], default="matched")
     ap.add_argument("--n", type=int, default=512)
     ap.add_argument("--angles", type=int, default=360)
@@ -39,10 +41,19 @@ def main():
     vol = torch.from_numpy(synth.phantom("ellipsoids50", a.n, 256.0 / a.n)).cuda().to(dt)
     proj = torch.empty(G.proj_shape, device="cuda", dtype=dt)
     out = torch.empty(G.vol_shape, device="cuda", dtype=dt)
-    if a.op in ("backward", "adjoint"):
+    if a.op in ("backward", "adjoint", "backward_ooc"):
         G.forward(vol, out=proj)
+    if a.op in ("forward_ooc", "backward_ooc"):
+        vol_host = vol.float().cpu().pin_memory()
+        out_host = torch.empty(G.vol_shape, dtype=torch.float32).pin_memory()
     if a.op == "forward":
         fn = lambda: G.forward(vol, out=proj)  # noqa: E731
+    elif a.op == "forward_ooc":
+        fn = lambda: tigre.tigre_forward_ooc(G.handle, vol_host, proj, 0, a.angles,  # noqa
+                                             slab_planes=a.slab)
+    elif a.op == "backward_ooc":
+        fn = lambda: tigre.tigre_backward_ooc(G.handle, proj, out_host, 0, a.angles,  # noqa
+                                              weight=a.weight, slab_planes=a.slab)
     elif a.op == "backward":
         fn = lambda: G.backward(proj, out=out, weight=a.weight)  # noqa: E731
     elif a.op == "adjoint":
