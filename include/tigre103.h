@@ -174,7 +174,13 @@ TIGRE_API tigre_status tigre_backward_ooc(tigre_geometry_t geo, const float* pro
 
 /* Solver flags. */
 #define TIGRE_HOST_RESIDENT 0x1u /* proj / vol are host pointers (out-of-core mode) */
-#define TIGRE_GRAPH 0x2u         /* capture each iteration in a CUDA graph */
+#define TIGRE_GRAPH 0x2u         /* stepwise CGLS: replay captured iteration pairs (CUDA graphs) */
+/* tigre_cgls only: proj and vol are HOST pointers (F32); the volume-sized
+ * vectors stay in host memory and reach the GPU through the out-of-core
+ * operators (z-slabs sized from device_budget_bytes, or from free memory when
+ * 0), the projection-sized vectors stay on the device (paper Alg. 1 and 2 on
+ * one GPU). */
+#define TIGRE_OUT_OF_CORE 0x4u
 
 typedef struct {
     int n_iter;                 /* iterations (default 10) */

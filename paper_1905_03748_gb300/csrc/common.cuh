@@ -151,9 +151,16 @@ size_t padded_elems(const tigre_geometry_desc& d);
 // [z_first, z_end) into a slab buffer whose first plane is z_first.
 tigre_status fill_padded_f32(const tigre_geometry_desc& d, const float* vol, float* out, int layout,
                              cudaStream_t st);
+tigre_status forward_slab_impl(tigre_geometry* g, const tigre_geometry_desc& sd, float* const pad[2],
+                               float4* const quad[2], float* proj, int64_t a0, int64_t na,
+                               int cell_lo, int cell_hi, int plane0, cudaStream_t st);
 tigre_status backward_slab_impl(tigre_geometry* g, const float* proj, float* vol_slab, int64_t a0,
                                 int64_t na, tigre_bp_weight w, int accumulate, int z_first,
                                 int z_end, cudaStream_t st);
+
+// CGLS with host-resident volume vectors (ooc.cu).
+tigre_status cgls_ooc_impl(tigre_geometry* g, const float* b_host, float* x_host,
+                           const tigre_solver_opts* o, double* h_hist);
 
 // Shared-memory slab forward projector (forward_tma.cu).
 bool tma_forward_fits(const tigre_geometry_desc& d, size_t elem);

@@ -223,14 +223,15 @@ __global__ void quad_kernel(const T* __restrict__ pad, typename QuadOf<T>::type*
 
 template <typename TV>
 __device__ __forceinline__ float tri_sample_quad(const typename QuadOf<TV>::type* __restrict__ qv,
-                                                 const Ray& R, float kf, int PF, int PFM)
+                                                 const Ray& R, float kf, int PF, int PFM,
+                                                 int s_off = 0)
 {
     int i_f, i_m, i_s;
     float af, am, as;
     split_floor(fmaf(kf, R.d[0], R.x0[0]), i_f, af);
     split_floor(fmaf(kf, R.d[1], R.x0[1]), i_m, am);
     split_floor(fmaf(kf, R.d[2], R.x0[2]), i_s, as);
-    const typename QuadOf<TV>::type* b = qv + (i_s * PFM + i_m * PF + i_f);
+    const typename QuadOf<TV>::type* b = qv + ((i_s - s_off) * PFM + i_m * PF + i_f);
     const float4 lo = load_quad(b, (TV*)nullptr);        // plane s: v000 v100 v010 v110
     const float4 hi = load_quad(b + PFM, (TV*)nullptr);  // plane s+1: v001 v101 v011 v111
     const float c00 = fmaf(af, lo.y - lo.x, lo.x);
@@ -242,12 +243,45 @@ __device__ __forceinline__ float tri_sample_quad(const typename QuadOf<TV>::type
     return fmaf(as, c1 - c0, c0);
 }
 
-// The L1 kernel's depth-ordered march, gathering from quad volumes.
-template <typename TV, typename TP>
+// Restriction of a projection to one axial slab (out-of-core mode): only the
+// samples whose z cell (padded index) lies in [cell_lo, cell_hi) count, the
+// volume buffer's plane 0 is padded plane plane0, and results add into the
+// output.
+struct SlabRange {
+    int cell_lo, cell_hi, plane0;
+};
+
+// First k in [0, K] whose z cell satisfies pred (pred monotone along the ray).
+template <typename P>
+__device__ __forceinline__ int first_k(int K, P pred)
+{
+    int lo = 0, hi = K;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (pred(mid))
+            hi = mid;
+        else
+            lo = mid + 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int z_cell(const Ray& R, int k)
+{
+    int i;
+    float f;
+    split_floor(fmaf((float)k, R.d[2], R.x0[2]), i, f);
+    return i;
+}
+
+// The L1 kernel's depth-ordered march, gathering from quad volumes.  With
+// SLAB, each ray processes only its samples [kb, ke) inside the slab.
+template <typename TV, typename TP, bool SLAB = false>
 __global__ void __launch_bounds__(256) fwd_quad_kernel(
     const typename QuadOf<TV>::type* __restrict__ qxy,
     const typename QuadOf<TV>::type* __restrict__ qyx, TP* __restrict__ proj,
-    const FwdAngle* __restrict__ params, FwdConst c, int a_first, const int* __restrict__ order)
+    const FwdAngle* __restrict__ params, FwdConst c, int a_first, const int* __restrict__ order,
+    SlabRange sr = SlabRange{0, 0, 0})
 {
     using Q = typename QuadOf<TV>::type;
     const unsigned full = 0xffffffffu;
@@ -260,26 +294,41 @@ __global__ void __launch_bounds__(256) fwd_quad_kernel(
     R.K = 0;
     R.ok = true;
     if (inside) setup_ray(params + a_first + a, c, p, q, R);
-    const bool active = inside && R.ok && R.K > 0;
+    int kb = 0, ke = R.K;
+    if (SLAB && inside && R.ok && R.K > 0) {
+        if (R.d[2] > 0.0f) {
+            kb = first_k(R.K, [&](int k) { return z_cell(R, k) >= sr.cell_lo; });
+            ke = first_k(R.K, [&](int k) { return z_cell(R, k) >= sr.cell_hi; });
+        } else if (R.d[2] < 0.0f) {
+            kb = first_k(R.K, [&](int k) { return z_cell(R, k) < sr.cell_hi; });
+            ke = first_k(R.K, [&](int k) { return z_cell(R, k) < sr.cell_lo; });
+        } else {
+            const int cz = z_cell(R, 0);
+            ke = (cz >= sr.cell_lo && cz < sr.cell_hi) ? R.K : 0;
+        }
+    }
+    const bool active = inside && R.ok && ke > kb;
     const unsigned act = __ballot_sync(full, active);
     const int layout = params[a_first + a].layout;  // uniform per block
     const Q* __restrict__ vol = layout ? qyx : qxy;
     const int PF = (layout ? c.ny : c.nx) + 2 * kPad;
     const int PFM = PF * ((layout ? c.nx : c.ny) + 2 * kPad);
+    const int s_off = SLAB ? sr.plane0 : 0;
 
     float acc = 0.0f;
     if (act) {
         const unsigned pos = __ballot_sync(full, active && R.d[1] > 0.0f);
         const unsigned neg = __ballot_sync(full, active && R.d[1] < 0.0f);
-        int k = 0;
-        float kf = 0.0f;
+        int k = kb;
+        float kf = (float)kb;
         if (pos == act || neg == act) {
             const float sgn = pos == act ? 1.0f : -1.0f;
             const float y0 = sgn * R.x0[1], dy = sgn * R.d[1];
-            const float y1 = fmaf((float)(R.K - 1), dy, y0);
-            float D = active ? dy : 3.0e38f, Y0 = active ? y0 : 3.0e38f;
+            const float ys = fmaf((float)kb, dy, y0);
+            const float y1 = fmaf((float)(ke - 1), dy, y0);
+            float D = active ? dy : 3.0e38f, Y0 = active ? ys : 3.0e38f;
             float Y1 = active ? y1 : -3.0e38f;
-            int kmax = active ? R.K : 0;
+            int kmax = active ? ke - kb : 0;
             for (int o = 16; o > 0; o >>= 1) {
                 D = fminf(D, __shfl_xor_sync(full, D, o));
                 Y0 = fminf(Y0, __shfl_xor_sync(full, Y0, o));
@@ -290,18 +339,25 @@ __global__ void __launch_bounds__(256) fwd_quad_kernel(
             const int nslab = ns < (float)(2 * kmax + 64) ? (int)ns + 1 : 0;
             for (int j = 1; j <= nslab; ++j) {
                 const float bound = fmaf((float)j, D, Y0);
-                if (k < R.K && fmaf(kf, dy, y0) < bound) {
-                    acc += tri_sample_quad<TV>(vol, R, kf, PF, PFM);
+                if (k < ke && fmaf(kf, dy, y0) < bound) {
+                    acc += tri_sample_quad<TV>(vol, R, kf, PF, PFM, s_off);
                     ++k;
                     kf += 1.0f;
                 }
             }
         }
-        for (; active && k < R.K; ++k, kf += 1.0f) acc += tri_sample_quad<TV>(vol, R, kf, PF, PFM);
+        for (; active && k < ke; ++k, kf += 1.0f)
+            acc += tri_sample_quad<TV>(vol, R, kf, PF, PFM, s_off);
     }
     if (!inside) return;
-    const float out = !R.ok ? __int_as_float(0x7fc00000) : acc * R.h;
-    proj[((int64_t)a * c.nv + q) * c.nu + p] = from_f32<TP>(out);
+    TP* o = proj + ((int64_t)a * c.nv + q) * c.nu + p;
+    if (!R.ok) {
+        *o = from_f32<TP>(__int_as_float(0x7fc00000));
+    } else if (SLAB) {
+        if (active) *o = from_f32<TP>(to_f32<TP>(*o) + acc * R.h);
+    } else {
+        *o = from_f32<TP>(acc * R.h);
+    }
 }
 
 // out (padded, x fastest): out[z+P][y+P][x+P] = vol[z][y][x].
@@ -478,6 +534,37 @@ tigre_status forward_impl(tigre_geometry* g, const void* vol, tigre_dtype vt, vo
             return TIGRE_OK;
         });
     });
+}
+
+// One axial slab of an out-of-core projection: pad[l] hold the slab's
+// zero-padded F32 layouts (planes of padded index plane0 .. for the
+// sub-volume description sd), quad[l] receive their quad volumes, and the
+// samples with z cells in [cell_lo, cell_hi) add into proj.
+tigre_status forward_slab_impl(tigre_geometry* g, const tigre_geometry_desc& sd, float* const pad[2],
+                               float4* const quad[2], float* proj, int64_t a0, int64_t na,
+                               int cell_lo, int cell_hi, int plane0, cudaStream_t st)
+{
+    const tigre_geometry_desc& d = g->desc;
+    const FwdConst c = make_fwd_const(d);
+    for (int l = 0; l < 2; ++l) {
+        if (!pad[l]) continue;
+        const int PF = (int)(l ? sd.n_voxel[1] : sd.n_voxel[0]) + 2 * kPad;
+        const int PM = (int)(l ? sd.n_voxel[0] : sd.n_voxel[1]) + 2 * kPad;
+        const int64_t rows = (int64_t)PM * (sd.n_voxel[2] + 2 * kPad);
+        quad_kernel<float><<<(unsigned)rows, 128, 0, st>>>(pad[l], quad[l], PF, PM, rows);
+        TIGRE_LAUNCHED("quad_kernel");
+    }
+    const SlabRange sr{cell_lo, cell_hi, plane0};
+    ProfScope prof(kProfForward, st);
+    for (int64_t s = 0; s < na; s += 65535) {
+        const int64_t cnt = std::min<int64_t>(65535, na - s);
+        dim3 grid((unsigned)((c.nu + 31) / 32), (unsigned)cnt, (unsigned)((c.nv + 7) / 8));
+        fwd_quad_kernel<float, float, true><<<grid, dim3(32, 8), 0, st>>>(
+            quad[0], quad[1], proj + s * (int64_t)c.nu * c.nv, (const FwdAngle*)g->fwd_params.ptr,
+            c, (int)(a0 + s), nullptr, sr);
+        TIGRE_LAUNCHED("fwd_quad_kernel(slab)");
+    }
+    return TIGRE_OK;
 }
 
 // Sum of K over the rays of a launch-sized block of angles (ray setup only).

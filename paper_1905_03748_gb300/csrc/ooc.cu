@@ -24,97 +24,14 @@
 // page-locking step (Alg. 1/2, "page-lock image memory").
 #include <algorithm>
 #include <cmath>
+#include <thread>
 
 #include "ray.cuh"
+#include "vecops.cuh"
 
 namespace tigre {
 
 namespace {
-
-__device__ __forceinline__ int cell_at(const Ray& R, int axis, int k)
-{
-    int i;
-    float f;
-    split_floor(fmaf((float)k, R.d[axis], R.x0[axis]), i, f);
-    return i;
-}
-
-// First k in [0, K] with pred(k) true, for pred monotone false -> true.
-template <typename P>
-__device__ __forceinline__ int first_true(int K, P pred)
-{
-    int lo = 0, hi = K;
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (pred(mid))
-            hi = mid;
-        else
-            lo = mid + 1;
-    }
-    return lo;
-}
-
-// Adds to proj the samples whose z cell (padded) lies in [cell_lo, cell_hi),
-// reading a padded slab layout whose plane 0 is full padded plane plane0.
-__global__ void __launch_bounds__(256) fwd_slab_kernel(const float* __restrict__ vxy,
-                                                       const float* __restrict__ vyx,
-                                                       float* __restrict__ proj,
-                                                       const FwdAngle* __restrict__ params,
-                                                       FwdConst c, int a_first, int cell_lo,
-                                                       int cell_hi, int plane0)
-{
-    const int p = blockIdx.x * 32 + threadIdx.x;
-    const int q = blockIdx.z * blockDim.y + threadIdx.y;
-    const int a = blockIdx.y;
-    if (p >= c.nu || q >= c.nv) return;
-    Ray R;
-    setup_ray(params + a_first + a, c, p, q, R);
-    float* out = proj + ((int64_t)a * c.nv + q) * c.nu + p;
-    if (!R.ok) {
-        *out = __int_as_float(0x7fc00000);
-        return;
-    }
-    if (R.K == 0) return;
-    int kb, ke;
-    if (R.d[2] > 0.0f) {
-        kb = first_true(R.K, [&](int k) { return cell_at(R, 2, k) >= cell_lo; });
-        ke = first_true(R.K, [&](int k) { return cell_at(R, 2, k) >= cell_hi; });
-    } else if (R.d[2] < 0.0f) {
-        kb = first_true(R.K, [&](int k) { return cell_at(R, 2, k) < cell_hi; });
-        ke = first_true(R.K, [&](int k) { return cell_at(R, 2, k) < cell_lo; });
-    } else {
-        const int cz = cell_at(R, 2, 0);
-        const bool in = cz >= cell_lo && cz < cell_hi;
-        kb = 0;
-        ke = in ? R.K : 0;
-    }
-    if (ke <= kb) return;
-    const float* __restrict__ vol = R.layout ? vyx : vxy;
-    const int PF = R.nf + 2 * kPad;
-    const int PFM = PF * (R.nm + 2 * kPad);
-    float acc = 0.0f;
-    float kf = (float)kb;
-    for (int k = kb; k < ke; ++k, kf += 1.0f) {
-        int i_f, i_m, i_s;
-        float af, am, as;
-        split_floor(fmaf(kf, R.d[0], R.x0[0]), i_f, af);
-        split_floor(fmaf(kf, R.d[1], R.x0[1]), i_m, am);
-        split_floor(fmaf(kf, R.d[2], R.x0[2]), i_s, as);
-        const float* b = vol + ((i_s - plane0) * PFM + i_m * PF + i_f);
-        const float v000 = __ldg(b), v100 = __ldg(b + 1);
-        const float v010 = __ldg(b + PF), v110 = __ldg(b + PF + 1);
-        const float v001 = __ldg(b + PFM), v101 = __ldg(b + PFM + 1);
-        const float v011 = __ldg(b + PFM + PF), v111 = __ldg(b + PFM + PF + 1);
-        const float c00 = fmaf(af, v100 - v000, v000);
-        const float c10 = fmaf(af, v110 - v010, v010);
-        const float c01 = fmaf(af, v101 - v001, v001);
-        const float c11 = fmaf(af, v111 - v011, v011);
-        const float c0 = fmaf(am, c10 - c00, c00);
-        const float c1 = fmaf(am, c11 - c01, c01);
-        acc += fmaf(as, c1 - c0, c0);
-    }
-    *out += acc * R.h;
-}
 
 // Page-locks a host range for the lifetime of the object unless it already is.
 struct HostPin {
@@ -203,7 +120,7 @@ tigre_status forward_ooc_impl(tigre_geometry* g, const float* vol_host, float* p
     const tigre_geometry_desc& d = g->desc;
     const int64_t nx = d.n_voxel[0], ny = d.n_voxel[1], nz = d.n_voxel[2];
     const int64_t plane = nx * ny;
-    if (slab <= 0) slab = auto_slab_planes(d, 4 * (2 * plane + 2 * (nx + 4) * (ny + 4)));
+    if (slab <= 0) slab = auto_slab_planes(d, 4 * 2 * plane + 20 * 2 * (nx + 4) * (ny + 4));
     slab = std::min(slab, nz);
     tigre_geometry_desc sd = d;
     sd.n_voxel[2] = slab + 1;
@@ -220,9 +137,13 @@ tigre_status forward_ooc_impl(tigre_geometry* g, const float* vol_host, float* p
     Bufs B;
     float* raw[2];
     float* pad[2] = {nullptr, nullptr};
+    float4* quad[2] = {nullptr, nullptr};
     for (int i = 0; i < 2; ++i) TIGRE_TRY(B.alloc(&raw[i], (size_t)(plane * (slab + 1))));
     for (int l = 0; l < 2; ++l)
-        if (need[l]) TIGRE_TRY(B.alloc(&pad[l], padded_elems(sd)));
+        if (need[l]) {
+            TIGRE_TRY(B.alloc(&pad[l], padded_elems(sd)));
+            TIGRE_TRY(B.alloc(&quad[l], padded_elems(sd)));
+        }
     TIGRE_CUDA(cudaMemsetAsync(proj, 0, sizeof(float) * (size_t)(na * c.nu * c.nv), st));
     for (int l = 0; l < 2; ++l)
         if (pad[l]) TIGRE_CUDA(cudaMemsetAsync(pad[l], 0, sizeof(float) * padded_elems(sd), st));
@@ -257,16 +178,7 @@ tigre_status forward_ooc_impl(tigre_geometry* g, const float* vol_host, float* p
         // the cells below plane 0, the last the cells above plane nz-1.
         const int cell_lo = s == 0 ? -1000000 : (int)(z0 + kPad);
         const int cell_hi = s == nslab - 1 ? 1000000 : (int)(z1 + kPad);
-        ProfScope prof(kProfForward, st);
-        for (int64_t a = 0; a < na; a += 65535) {
-            const int64_t cnt = std::min<int64_t>(65535, na - a);
-            dim3 grid((unsigned)((c.nu + 31) / 32), (unsigned)cnt, (unsigned)((c.nv + 7) / 8));
-            fwd_slab_kernel<<<grid, dim3(32, 8), 0, st>>>(pad[0], pad[1],
-                                                          proj + a * (int64_t)c.nu * c.nv,
-                                                          (const FwdAngle*)g->fwd_params.ptr, c,
-                                                          (int)(a0 + a), cell_lo, cell_hi, (int)z0);
-            TIGRE_LAUNCHED("fwd_slab_kernel");
-        }
+        TIGRE_TRY(forward_slab_impl(g, sd, pad, quad, proj, a0, na, cell_lo, cell_hi, (int)z0, st));
     }
     TIGRE_CUDA(cudaStreamSynchronize(st));
     return TIGRE_OK;
@@ -363,3 +275,118 @@ extern "C" tigre_status tigre_backward_ooc(tigre_geometry_t geo, const float* pr
     return tigre::backward_ooc_impl(geo, proj, proj_on_host, vol_host, angle_begin, angle_count,
                                     weight, slab_planes, angle_chunk, (cudaStream_t)cuda_stream);
 }
+
+// ------------------------------------------------------- out-of-core CGLS
+//
+// CGLS (same iteration as tigre_cgls) for volumes kept in host memory: the
+// volume-sized vectors x, p, s live in pinned host memory and reach the GPU
+// only through the out-of-core operators (z-slabs streamed on a copy stream);
+// the projection-sized vectors b, r, q stay on the device.  Volume-sized
+// vector updates and their FP64 inner products run on the host cores.
+
+namespace tigre {
+namespace {
+
+// Parallel loop over [0, n) on the host cores (fixed split: deterministic sums).
+template <typename F>
+void host_parallel(int64_t n, F&& f)
+{
+    const int nt = (int)std::max(1u, std::min(64u, std::thread::hardware_concurrency()));
+    std::vector<std::thread> th;
+    for (int t = 0; t < nt; ++t)
+        th.emplace_back([&, t] { f(n * t / nt, n * (t + 1) / nt, t); });
+    for (auto& x : th) x.join();
+}
+
+double host_dot(const float* a, const float* b, int64_t n)
+{
+    std::vector<double> part(64, 0.0);
+    host_parallel(n, [&](int64_t lo, int64_t hi, int t) {
+        double s = 0.0;
+        for (int64_t i = lo; i < hi; ++i) s += (double)a[i] * (double)b[i];
+        part[(size_t)t] = s;
+    });
+    double s = 0.0;
+    for (double v : part) s += v;
+    return s;
+}
+
+__global__ void set_dscalar_kernel(double* dst, double v) { *dst = v; }
+
+}  // namespace
+
+tigre_status cgls_ooc_impl(tigre_geometry* g, const float* b_host, float* x_host,
+                           const tigre_solver_opts* o, double* h_hist)
+{
+    TIGRE_TRY(check_geometry(g));
+    cudaStream_t st = (cudaStream_t)o->cuda_stream;
+    const tigre_geometry_desc& d = g->desc;
+    const int64_t nvox = n_vox(g), na = (int64_t)g->angles.size(), m = n_pix(g) * na;
+    const int64_t plane = d.n_voxel[0] * d.n_voxel[1];
+    int64_t slab = 0;
+    if (o->device_budget_bytes > 0) {
+        const int64_t per_plane = 4 * 2 * plane + 20 * 2 * (d.n_voxel[0] + 4) * (d.n_voxel[1] + 4);
+        slab = std::max<int64_t>(1, o->device_budget_bytes / per_plane - 5);
+    }
+    HostPin pin_x;
+    TIGRE_TRY(pin_x.pin(x_host, sizeof(float) * (size_t)nvox));
+    float *hp = nullptr, *hs = nullptr;
+    TIGRE_CUDA(cudaHostAlloc((void**)&hp, sizeof(float) * (size_t)nvox, cudaHostAllocDefault));
+    struct HostFree {
+        float* p;
+        ~HostFree() { if (p) cudaFreeHost(p); }
+    } free_p{hp};
+    TIGRE_CUDA(cudaHostAlloc((void**)&hs, sizeof(float) * (size_t)nvox, cudaHostAllocDefault));
+    HostFree free_s{hs};
+    Bufs B;
+    float *b, *r, *q;
+    double* sc;
+    TIGRE_TRY(B.alloc(&b, (size_t)m));
+    TIGRE_TRY(B.alloc(&r, (size_t)m));
+    TIGRE_TRY(B.alloc(&q, (size_t)m));
+    TIGRE_TRY(B.alloc(&sc, (size_t)(kRedBlocks + 16)));
+    double* partials = sc;
+    double* qq = sc + kRedBlocks;       // [2]
+    double* rr = sc + kRedBlocks + 2;   // [2]
+    double* gam = sc + kRedBlocks + 4;  // gamma (host-set)
+    TIGRE_CUDA(cudaMemcpyAsync(b, b_host, sizeof(float) * (size_t)m, cudaMemcpyHostToDevice, st));
+    // r = b - A x0; p = A^T r; gamma = ||p||^2
+    TIGRE_TRY(forward_ooc_impl(g, x_host, q, 0, na, slab, st));
+    TIGRE_TRY(weighted_residual(b, q, nullptr, r, m, partials, rr, st));
+    TIGRE_TRY(backward_ooc_impl(g, r, 0, hp, 0, na, o->bp_weight, slab, 0, st));
+    double gamma = host_dot(hp, hp, nvox);
+    for (int it = 0; it < o->n_iter; ++it) {
+        TIGRE_TRY(forward_ooc_impl(g, hp, q, 0, na, slab, st));
+        TIGRE_TRY(dot_f64(q, q, m, partials, qq, st));
+        double hqq = 0.0;
+        TIGRE_CUDA(cudaMemcpyAsync(&hqq, qq, sizeof(double), cudaMemcpyDeviceToHost, st));
+        TIGRE_CUDA(cudaStreamSynchronize(st));
+        const double alpha = hqq != 0.0 ? gamma / hqq : 0.0;
+        // r -= alpha q on the device (alpha = gamma / qq from device slots)
+        set_dscalar_kernel<<<1, 1, 0, st>>>(gam, gamma);
+        TIGRE_LAUNCHED("set_dscalar_kernel");
+        TIGRE_TRY(axpy_ratio_norm(r, q, m, gam, qq, -1.0f, partials, rr, st));
+        // x += alpha p on the host, while the device updates r
+        const float af = (float)alpha;
+        host_parallel(nvox, [&](int64_t lo, int64_t hi, int) {
+            for (int64_t i = lo; i < hi; ++i) x_host[i] = fmaf(af, hp[i], x_host[i]);
+        });
+        if (h_hist) {
+            double rn[2];
+            TIGRE_CUDA(cudaMemcpyAsync(rn, rr, sizeof(rn), cudaMemcpyDeviceToHost, st));
+            TIGRE_CUDA(cudaStreamSynchronize(st));
+            h_hist[it] = rn[1];
+        }
+        TIGRE_TRY(backward_ooc_impl(g, r, 0, hs, 0, na, o->bp_weight, slab, 0, st));
+        const double gamma_new = host_dot(hs, hs, nvox);
+        const float beta = (float)(gamma != 0.0 ? gamma_new / gamma : 0.0);
+        host_parallel(nvox, [&](int64_t lo, int64_t hi, int) {
+            for (int64_t i = lo; i < hi; ++i) hp[i] = fmaf(beta, hp[i], hs[i]);
+        });
+        gamma = gamma_new;
+    }
+    TIGRE_CUDA(cudaStreamSynchronize(st));
+    return TIGRE_OK;
+}
+
+}  // namespace tigre

@@ -73,7 +73,7 @@ tigre_status check_opts(const tigre_geometry* g, const tigre_solver_opts* o, con
     if (o->n_iter < 0) return fail(TIGRE_ERR_INVALID_ARG, "n_iter must be >= 0");
     if (!dtype_ok(o->storage)) return fail(TIGRE_ERR_INVALID_ARG, "bad storage dtype");
     if (!(std::isfinite(o->lambda))) return fail(TIGRE_ERR_INVALID_ARG, "lambda must be finite");
-    if (o->flags & ~(TIGRE_HOST_RESIDENT | TIGRE_GRAPH))
+    if (o->flags & ~(TIGRE_HOST_RESIDENT | TIGRE_GRAPH | TIGRE_OUT_OF_CORE))
         return fail(TIGRE_ERR_INVALID_ARG, "unknown flags");
     return TIGRE_OK;
 }
@@ -387,6 +387,14 @@ tigre_status tigre_sart(tigre_geometry_t geo, const void* proj, void* vol,
 tigre_status tigre_cgls(tigre_geometry_t geo, const void* proj, void* vol,
                         const tigre_solver_opts* opts, double* resid_hist)
 {
+    if (opts && (opts->flags & TIGRE_OUT_OF_CORE)) {
+        TIGRE_TRY(check_opts(geo, opts, proj, vol));
+        if (opts->storage != TIGRE_F32)
+            return fail(TIGRE_ERR_UNSUPPORTED, "out-of-core CGLS stores F32");
+        if (opts->bp_weight == TIGRE_BP_EXACT_ADJOINT)
+            return fail(TIGRE_ERR_UNSUPPORTED, "out-of-core backprojection is voxel-driven");
+        return cgls_ooc_impl(geo, (const float*)proj, (float*)vol, opts, resid_hist);
+    }
     return with_device_problem(geo, proj, vol, opts,
                                [&](const Problem& P) { return run_cgls(P, resid_hist); });
 }

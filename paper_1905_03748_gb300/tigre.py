@@ -252,9 +252,26 @@ def tigre_sart(handle, proj, vol, n_iter, subset_size=20, lam=1.0, nonneg=False,
     return _solver(_lib.tigre_sart, handle, proj, vol, o, host)
 
 
+TIGRE_OUT_OF_CORE = 0x4
+
+
 def tigre_cgls(handle, proj, vol, n_iter, bp_weight="matched", stream=None,
-               host=False) -> np.ndarray:
-    o = _opts(n_iter, stream, bp_weight=bp_weight)
+               host=False, out_of_core=False, device_budget_bytes=0) -> np.ndarray:
+    """CGLS.  host=True stages host tensors through the device; with
+    out_of_core=True the volume-sized vectors stay in host memory and stream
+    through the GPU in z-slabs (sized by device_budget_bytes, 0 = automatic)."""
+    o = _opts(n_iter, stream, bp_weight=bp_weight,
+              device_budget_bytes=int(device_budget_bytes))
+    if out_of_core:
+        o.flags |= TIGRE_OUT_OF_CORE
+        hist = np.zeros(max(n_iter, 1), dtype=np.float64)
+        for t, name in ((proj, "proj"), (vol, "vol")):
+            if t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
+                raise TypeError(f"{name} must be a contiguous float32 host tensor")
+        _check(_lib.tigre_cgls(handle, ctypes.c_void_p(proj.data_ptr()),
+                               ctypes.c_void_p(vol.data_ptr()), ctypes.byref(o),
+                               hist.ctypes.data_as(_P)))
+        return hist[:n_iter]
     return _solver(_lib.tigre_cgls, handle, proj, vol, o, host)
 
 
