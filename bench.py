@@ -146,6 +146,23 @@ def dist_init(backend):
     return dist.get_rank(), ws, dist
 
 
+def max_over_ranks(x: float, dist, device=None) -> float:
+    """Largest value of x over all ranks (the job's step time); identity
+    without a process group.  No data-path collective: timings only."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(work_per_rank: float, world: int, seconds: float) -> float:
+    """Whole-job throughput for independent per-rank problems (weak
+    scaling): all ranks' work over the slowest rank's time, in G/s."""
+    return world * work_per_rank / seconds / 1e9
+
+
 def cpu_baseline(geo, ang, x_true, n_angles):
     """The FP64 oracle, as it stands, on a bounded sample of the workload:
     one forward projection and one matched backprojection over the first
@@ -242,16 +259,12 @@ def run_ours(args):
     fwd_n, fwd_ms = tigre.tigre_profile_read(tigre.PROF_FORWARD)
     bp_n, bp_ms = tigre.tigre_profile_read(tigre.PROF_BACKPROJECT)
     tigre.tigre_profile_enable(False)
-    ms = e0.elapsed_time(e1) / args.steps
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, dist, dev)
     hist = tigre.tigre_cgls_history(state, args.warmup + args.steps)
     tigre.tigre_cgls_end(state)
 
     vox_ang = float(nvox) * len(ang)
-    value = world * 2.0 * vox_ang / (ms / 1e3) / 1e9
+    value = job_rate(2.0 * vox_ang, world, ms / 1e3)
     samples = tigre.tigre_forward_samples(G.handle, 0, len(ang))
     fwd_avg = fwd_ms / max(fwd_n, 1)
     bp_avg = bp_ms / max(bp_n, 1)
@@ -297,12 +310,8 @@ def run_ours(args):
             dist.barrier()
         t0 = time.perf_counter()
         tigre.tigre_cgls(G.handle, bh, xh, n_e2e, host=True)
-        dt = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([dt], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
-        out["e2e"] = {"value": world * 2.0 * vox_ang * n_e2e / dt / 1e9, "unit": UNIT,
+        dt = max_over_ranks(time.perf_counter() - t0, dist, dev)
+        out["e2e"] = {"value": job_rate(2.0 * vox_ang * n_e2e, world, dt), "unit": UNIT,
                       "h2d_bytes_per_step": bh.numel() * 4 + xh.numel() * 4,
                       "d2h_bytes_per_step": xh.numel() * 4,
                       "step": f"tigre_cgls call on pinned host buffers: copy b and x0 in, "
