@@ -150,6 +150,15 @@ TIGRE_API tigre_status tigre_tv_step_noalloc(const int64_t n_voxel[3], void* vol
                                              int n_steps, double alpha, double eps,
                                              void* cuda_stream);
 
+/* The placement (1 or 2, see TIGRE_OUT_OF_CORE) and the slab thickness in
+ * z planes that an out-of-core tigre_cgls on this geometry uses under
+ * device_budget_bytes (0 = free device memory less 1 GiB).  Sec. 2 sizes the
+ * paper's splits from the memory each GPU has; this is that decision for one
+ * GPU.  TIGRE_ERR_OOM when the budget is below three projection sets plus
+ * one-plane slabs.  Queries free memory only; allocates nothing. */
+TIGRE_API tigre_status tigre_cgls_ooc_plan(tigre_geometry_t geo, int64_t device_budget_bytes,
+                                           int* placement, int64_t* slab_planes);
+
 /* Out-of-core forward projection (paper Alg. 1 on one GPU): vol_host is a
  * HOST pointer (F32, (nz, ny, nx)), streamed to the device in axial slabs of
  * slab_planes planes (0 = sized from free device memory) on a copy stream,
@@ -175,11 +184,18 @@ TIGRE_API tigre_status tigre_backward_ooc(tigre_geometry_t geo, const float* pro
 /* Solver flags. */
 #define TIGRE_HOST_RESIDENT 0x1u /* proj / vol are host pointers (out-of-core mode) */
 #define TIGRE_GRAPH 0x2u         /* stepwise CGLS: replay captured iteration pairs (CUDA graphs) */
-/* tigre_cgls only: proj and vol are HOST pointers (F32); the volume-sized
- * vectors stay in host memory and reach the GPU through the out-of-core
- * operators (z-slabs sized from device_budget_bytes, or from free memory when
- * 0), the projection-sized vectors stay on the device (paper Alg. 1 and 2 on
- * one GPU). */
+/* tigre_cgls only: proj and vol are HOST pointers (F32) and CGLS runs with
+ * part of its state in host memory, the volume streamed through the device in
+ * axial slabs (paper Alg. 1 and 2 on one GPU).  device_budget_bytes (0 = free
+ * device memory less 1 GiB) bounds ALL device memory the call uses and picks
+ * the placement (see tigre_cgls_ooc_plan):
+ *   2, when x and two projection sets fit: x, r, q on the device, only the
+ *      search direction in host memory -- inside the caller's vol buffer,
+ *      which holds x again on return -- and s = A^T r recomputed instead of
+ *      stored (two backprojections per iteration); no host allocation;
+ *   1, otherwise: x, p, s in host memory (two volumes of pinned host memory
+ *      allocated for the call), b, r, q on the device.
+ * Both give the in-core iterates up to FP32 summation order. */
 #define TIGRE_OUT_OF_CORE 0x4u
 
 typedef struct {

@@ -304,6 +304,32 @@ static BpConst make_bp_const(const tigre_geometry_desc& d)
     return c;
 }
 
+// A launch over planes [z_first, z_end) pads only the detector rows those
+// planes reach (its last chunk of kBpNZ planes may run past z_end), with two
+// rows of margin on either side for FP32 rounding.
+static void bp_slab_band(BpConst& c, const tigre_geometry_desc& d, int z_first, int z_end)
+{
+    const int64_t z_last = z_first + ((int64_t)(z_end - z_first) + kBpNZ - 1) / kBpNZ * kBpNZ - 1;
+    double lo, hi;
+    if (!detector_row_range(d, (double)z_first, (double)z_last, &lo, &hi)) return;
+    const int r_lo = (int)std::floor(lo) - 2;
+    const int r_hi = (int)std::ceil(hi) + 3;
+    c.pv_lo = -r_lo;
+    c.PV = r_hi - r_lo + 1;
+}
+
+size_t bp_slab_pad_bytes(const tigre_geometry_desc& d, int64_t slab, int64_t na)
+{
+    size_t most = 0;
+    const int64_t nz = d.n_voxel[2];
+    for (int64_t z0 = 0; z0 < nz; z0 += slab) {
+        BpConst c = make_bp_const(d);
+        bp_slab_band(c, d, (int)z0, (int)std::min(nz, z0 + slab));
+        most = std::max(most, (size_t)na * (size_t)c.PU * (size_t)c.PV * sizeof(float));
+    }
+    return most;
+}
+
 // Voxel planes [z_first, z_end) into an output buffer whose first plane is
 // z_out0 (in-core: 0, nz, 0; out-of-core slabs: the slab's planes).
 template <typename TP, typename TV>
@@ -320,6 +346,7 @@ tigre_status launch_voxel_bp(tigre_geometry* g, const TP* proj, TV* vol, int64_t
         c.z_first = z_first;
         c.z_end = z_end;
         c.z_out0 = z_out0;
+        bp_slab_band(c, d, z_first, z_end);
     }
     const size_t pelems = (size_t)na * (size_t)c.PU * (size_t)c.PV;
     TIGRE_TRY(g->proj_pad.ensure(pelems * sizeof(TP)));

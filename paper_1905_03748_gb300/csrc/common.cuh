@@ -145,6 +145,10 @@ namespace tigre {
 constexpr int kPad = 2;  // zero voxels around the volume in the padded layouts
 
 tigre_status upload_params(tigre_geometry* g);
+// Detector row coordinates [lo, hi] (row index units, continuous) that any
+// point of the support with z in [za, zb] (voxel index units) projects to,
+// over all angles; false when the source can be inside the support (no bound).
+bool detector_row_range(const tigre_geometry_desc& d, double za, double zb, double* lo, double* hi);
 size_t padded_elems(const tigre_geometry_desc& d);
 // Out-of-core building blocks: the zero-padded layout of a (sub-)volume
 // described by d, and the voxel-driven backprojection of planes
@@ -154,6 +158,9 @@ tigre_status fill_padded_f32(const tigre_geometry_desc& d, const float* vol, flo
 tigre_status forward_slab_impl(tigre_geometry* g, const tigre_geometry_desc& sd, float* const pad[2],
                                float4* const quad[2], float* proj, int64_t a0, int64_t na,
                                int cell_lo, int cell_hi, int plane0, cudaStream_t st);
+// Bytes of the zero-bordered F32 projection buffer that slab launches of
+// `slab` planes over na angles need at most (the largest row band).
+size_t bp_slab_pad_bytes(const tigre_geometry_desc& d, int64_t slab, int64_t na);
 tigre_status backward_slab_impl(tigre_geometry* g, const float* proj, float* vol_slab, int64_t a0,
                                 int64_t na, tigre_bp_weight w, int accumulate, int z_first,
                                 int z_end, cudaStream_t st);

@@ -245,10 +245,11 @@ __device__ __forceinline__ float tri_sample_quad(const typename QuadOf<TV>::type
 
 // Restriction of a projection to one axial slab (out-of-core mode): only the
 // samples whose z cell (padded index) lies in [cell_lo, cell_hi) count, the
-// volume buffer's plane 0 is padded plane plane0, and results add into the
-// output.
+// volume buffer's plane 0 is padded plane plane0, results add into the
+// output, and the launch covers detector rows from q0 (the rows the slab can
+// reach).
 struct SlabRange {
-    int cell_lo, cell_hi, plane0;
+    int cell_lo, cell_hi, plane0, q0;
 };
 
 // First k in [0, K] whose z cell satisfies pred (pred monotone along the ray).
@@ -281,12 +282,12 @@ __global__ void __launch_bounds__(256) fwd_quad_kernel(
     const typename QuadOf<TV>::type* __restrict__ qxy,
     const typename QuadOf<TV>::type* __restrict__ qyx, TP* __restrict__ proj,
     const FwdAngle* __restrict__ params, FwdConst c, int a_first, const int* __restrict__ order,
-    SlabRange sr = SlabRange{0, 0, 0})
+    SlabRange sr = SlabRange{0, 0, 0, 0})
 {
     using Q = typename QuadOf<TV>::type;
     const unsigned full = 0xffffffffu;
     const int p = blockIdx.x * 32 + threadIdx.x;
-    const int q = blockIdx.z * blockDim.y + threadIdx.y;
+    const int q = (SLAB ? sr.q0 : 0) + (int)(blockIdx.z * blockDim.y + threadIdx.y);
     const int a = order ? order[blockIdx.y] : (int)blockIdx.y;
     const bool inside = p < c.nu && q < c.nv;
 
@@ -554,11 +555,24 @@ tigre_status forward_slab_impl(tigre_geometry* g, const tigre_geometry_desc& sd,
         quad_kernel<float><<<(unsigned)rows, 128, 0, st>>>(pad[l], quad[l], PF, PM, rows);
         TIGRE_LAUNCHED("quad_kernel");
     }
-    const SlabRange sr{cell_lo, cell_hi, plane0};
+    // Rows whose rays can have samples in the slab's cells: z (unpadded
+    // index) in [cell_lo - P, cell_hi - P), within the support [-1, nz].
+    int q_lo = 0, q_hi = c.nv;
+    {
+        const double za = std::max((double)(cell_lo - kPad), -1.5);
+        const double zb = std::min((double)(cell_hi - kPad), (double)d.n_voxel[2] + 0.5);
+        double lo, hi;
+        if (detector_row_range(d, za, zb, &lo, &hi)) {
+            q_lo = (int)std::max(0.0, std::floor(lo) - 2.0);
+            q_hi = (int)std::min((double)c.nv, std::ceil(hi) + 3.0);
+        }
+    }
+    if (q_hi <= q_lo) return TIGRE_OK;
+    const SlabRange sr{cell_lo, cell_hi, plane0, q_lo};
     ProfScope prof(kProfForward, st);
     for (int64_t s = 0; s < na; s += 65535) {
         const int64_t cnt = std::min<int64_t>(65535, na - s);
-        dim3 grid((unsigned)((c.nu + 31) / 32), (unsigned)cnt, (unsigned)((c.nv + 7) / 8));
+        dim3 grid((unsigned)((c.nu + 31) / 32), (unsigned)cnt, (unsigned)((q_hi - q_lo + 7) / 8));
         fwd_quad_kernel<float, float, true><<<grid, dim3(32, 8), 0, st>>>(
             quad[0], quad[1], proj + s * (int64_t)c.nu * c.nv, (const FwdAngle*)g->fwd_params.ptr,
             c, (int)(a0 + s), nullptr, sr);

@@ -4,6 +4,7 @@
 // circular cone-beam frame (source S = DSO (cos t, sin t, 0), detector centre
 // D = -(DSD - DSO)(cos t, sin t, 0), e_u = (-sin t, cos t, 0), e_v = z) and
 // rounded once to FP32 for the kernels.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -103,6 +104,37 @@ tigre_status check_range(const tigre_geometry* g, int64_t begin, int64_t count)
     if (begin < 0 || count <= 0 || begin + count > (int64_t)g->angles.size())
         return fail(TIGRE_ERR_INVALID_ARG, "angle range outside the geometry's angles");
     return TIGRE_OK;
+}
+
+bool detector_row_range(const tigre_geometry_desc& d, double za, double zb, double* lo, double* hi)
+{
+    // Farthest distance from the rotation axis of the support box (voxel
+    // centres -1 .. n along x and y, offsets included).
+    double r2 = 0.0;
+    for (int k = 0; k < 2; ++k) {
+        const double h = 0.5 * (double)(d.n_voxel[k] + 1) * d.d_voxel[k];
+        const double e = std::max(std::fabs(d.off_origin[k] - h), std::fabs(d.off_origin[k] + h));
+        r2 += e * e;
+    }
+    const double R = std::sqrt(r2);
+    if (!(R < d.DSO)) return false;
+    // A point at depth L = DSO - X.(cos, sin) in [DSO - R, DSO + R] and height
+    // z lies on the ray of detector height v = z DSD / L (the source is at z = 0).
+    const double mags[2] = {d.DSD / (d.DSO + R), d.DSD / (d.DSO - R)};
+    const double zc = 0.5 * (double)(d.n_voxel[2] - 1);
+    const double pv_off = 0.5 * (double)(d.n_det[1] - 1) - d.off_det[1] / d.d_det[1];
+    double vlo = 1e300, vhi = -1e300;
+    for (double zi : {za, zb}) {
+        const double Z = (zi - zc) * d.d_voxel[2] + d.off_origin[2];
+        for (double m : mags) {
+            const double q = Z * m / d.d_det[1] + pv_off;
+            vlo = std::min(vlo, q);
+            vhi = std::max(vhi, q);
+        }
+    }
+    *lo = vlo;
+    *hi = vhi;
+    return true;
 }
 
 tigre_status upload_params(tigre_geometry* g)

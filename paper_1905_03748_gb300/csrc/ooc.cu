@@ -60,7 +60,7 @@ struct HostPin {
 
 struct Streams {
     cudaStream_t copy = nullptr;
-    cudaEvent_t ev[8] = {};
+    cudaEvent_t ev[12] = {};
     ~Streams()
     {
         for (cudaEvent_t e : ev)
@@ -97,6 +97,13 @@ struct Bufs {
     }
 };
 
+// Thickest slab whose zero-padded buffers (slab + 1 planes) index in 32 bits.
+int64_t max_slab_planes(const tigre_geometry_desc& d)
+{
+    const int64_t per = (d.n_voxel[0] + 2 * kPad) * (d.n_voxel[1] + 2 * kPad);
+    return std::max<int64_t>(1, ((int64_t)INT32_MAX - 1) / per - 2 - 2 * kPad);
+}
+
 int64_t auto_slab_planes(const tigre_geometry_desc& d, int64_t per_plane_bytes)
 {
     size_t free_b = 0, total_b = 0;
@@ -106,7 +113,82 @@ int64_t auto_slab_planes(const tigre_geometry_desc& d, int64_t per_plane_bytes)
     }
     const int64_t budget = (int64_t)(free_b / 2);
     const int64_t s = std::max<int64_t>(1, budget / std::max<int64_t>(per_plane_bytes, 1) - 6);
-    return std::min<int64_t>(s, d.n_voxel[2]);
+    return std::min<int64_t>(std::min<int64_t>(s, d.n_voxel[2]), max_slab_planes(d));
+}
+
+// The forward projection of a volume cut into z-slabs of `slab` planes:
+// zero-padded and quad buffers for slab + 1 planes (the halo plane) in the
+// layouts the angles use.
+struct FwdSlabs {
+    tigre_geometry* g = nullptr;
+    tigre_geometry_desc sd{};
+    int64_t slab = 0, nslab = 0;
+    float* pad[2] = {nullptr, nullptr};
+    float4* quad[2] = {nullptr, nullptr};
+
+    static size_t bytes(const tigre_geometry_desc& d, int64_t slab, const bool need[2])
+    {
+        tigre_geometry_desc t = d;
+        t.n_voxel[2] = slab + 1;
+        return (size_t)((need[0] ? 1 : 0) + (need[1] ? 1 : 0)) * padded_elems(t) *
+               (sizeof(float) + sizeof(float4));
+    }
+
+    tigre_status init(tigre_geometry* g_, int64_t slab_, const bool need[2], Bufs& B,
+                      cudaStream_t st)
+    {
+        g = g_;
+        const int64_t nz = g->desc.n_voxel[2];
+        slab = std::min(slab_, nz);
+        nslab = (nz + slab - 1) / slab;
+        sd = g->desc;
+        sd.n_voxel[2] = slab + 1;
+        if (padded_elems(sd) >= (size_t)INT32_MAX)
+            return fail(TIGRE_ERR_UNSUPPORTED, "slab too large for 32-bit indexing; use thinner slabs");
+        for (int l = 0; l < 2; ++l)
+            if (need[l]) {
+                TIGRE_TRY(B.alloc(&pad[l], padded_elems(sd)));
+                TIGRE_TRY(B.alloc(&quad[l], padded_elems(sd)));
+                TIGRE_CUDA(cudaMemsetAsync(pad[l], 0, sizeof(float) * padded_elems(sd), st));
+            }
+        return TIGRE_OK;
+    }
+
+    // Adds the partial projections of slab s into proj.  src (device) holds
+    // the slab's planes z0 .. z0 + planes - 1, the halo plane included; after
+    // the zero-padded copies are made, `filled` (if any) is recorded on st.
+    tigre_status project(int64_t s, const float* src, float* proj, int64_t a0, int64_t na,
+                         cudaStream_t st, cudaEvent_t filled = nullptr)
+    {
+        const tigre_geometry_desc& d = g->desc;
+        const int64_t nx = d.n_voxel[0], ny = d.n_voxel[1], nz = d.n_voxel[2];
+        const int64_t z0 = s * slab, z1 = std::min(nz, z0 + slab);
+        const int64_t planes = std::min(z1 + 1, nz) - z0;  // with the halo plane
+        tigre_geometry_desc pd = d;
+        pd.n_voxel[2] = planes;
+        for (int l = 0; l < 2; ++l)
+            if (pad[l]) TIGRE_TRY(fill_padded_f32(pd, src, pad[l], l, st));
+        if (planes < slab + 1)  // a shorter last slab: clear the stale planes above it
+            for (int l = 0; l < 2; ++l)
+                if (pad[l]) {
+                    const int64_t pp = (l ? ny : nx) + 2 * kPad, pm = (l ? nx : ny) + 2 * kPad;
+                    const int64_t from = (planes + kPad) * pp * pm;
+                    TIGRE_CUDA(cudaMemsetAsync(pad[l] + from, 0,
+                                               sizeof(float) * (size_t)(padded_elems(sd) - from), st));
+                }
+        if (filled) TIGRE_CUDA(cudaEventRecord(filled, st));
+        // Cells of this slab in padded z: [z0+P, z1+P); the first slab also owns
+        // the cells below plane 0, the last the cells above plane nz-1.
+        const int cell_lo = s == 0 ? -1000000 : (int)(z0 + kPad);
+        const int cell_hi = s == nslab - 1 ? 1000000 : (int)(z1 + kPad);
+        return forward_slab_impl(g, sd, pad, quad, proj, a0, na, cell_lo, cell_hi, (int)z0, st);
+    }
+};
+
+void layouts_used(const tigre_geometry* g, int64_t a0, int64_t na, bool need[2])
+{
+    need[0] = need[1] = false;
+    for (int64_t a = a0; a < a0 + na; ++a) need[g->layout[(size_t)a]] = true;
 }
 
 }  // namespace
@@ -122,13 +204,8 @@ tigre_status forward_ooc_impl(tigre_geometry* g, const float* vol_host, float* p
     const int64_t plane = nx * ny;
     if (slab <= 0) slab = auto_slab_planes(d, 4 * 2 * plane + 20 * 2 * (nx + 4) * (ny + 4));
     slab = std::min(slab, nz);
-    tigre_geometry_desc sd = d;
-    sd.n_voxel[2] = slab + 1;
-    if (padded_elems(sd) >= (size_t)INT32_MAX)
-        return fail(TIGRE_ERR_UNSUPPORTED, "slab too large for 32-bit indexing; use thinner slabs");
-    const FwdConst c = make_fwd_const(d);
-    bool need[2] = {false, false};
-    for (int64_t a = a0; a < a0 + na; ++a) need[g->layout[(size_t)a]] = true;
+    bool need[2];
+    layouts_used(g, a0, na, need);
 
     HostPin pin;
     TIGRE_TRY(pin.pin(vol_host, sizeof(float) * (size_t)(plane * nz)));
@@ -136,23 +213,15 @@ tigre_status forward_ooc_impl(tigre_geometry* g, const float* vol_host, float* p
     TIGRE_TRY(S.init());
     Bufs B;
     float* raw[2];
-    float* pad[2] = {nullptr, nullptr};
-    float4* quad[2] = {nullptr, nullptr};
     for (int i = 0; i < 2; ++i) TIGRE_TRY(B.alloc(&raw[i], (size_t)(plane * (slab + 1))));
-    for (int l = 0; l < 2; ++l)
-        if (need[l]) {
-            TIGRE_TRY(B.alloc(&pad[l], padded_elems(sd)));
-            TIGRE_TRY(B.alloc(&quad[l], padded_elems(sd)));
-        }
-    TIGRE_CUDA(cudaMemsetAsync(proj, 0, sizeof(float) * (size_t)(na * c.nu * c.nv), st));
-    for (int l = 0; l < 2; ++l)
-        if (pad[l]) TIGRE_CUDA(cudaMemsetAsync(pad[l], 0, sizeof(float) * padded_elems(sd), st));
+    FwdSlabs F;
+    TIGRE_TRY(F.init(g, slab, need, B, st));
+    TIGRE_CUDA(cudaMemsetAsync(proj, 0, sizeof(float) * (size_t)(na * n_pix(g)), st));
     cudaEvent_t* copied = S.ev;       // [2]
     cudaEvent_t* consumed = S.ev + 2; // [2]
     TIGRE_CUDA(cudaEventRecord(consumed[0], st));
     TIGRE_CUDA(cudaEventRecord(consumed[1], st));
-    const int64_t nslab = (nz + slab - 1) / slab;
-    for (int64_t s = 0; s < nslab; ++s) {
+    for (int64_t s = 0; s < F.nslab; ++s) {
         const int b = (int)(s & 1);
         const int64_t z0 = s * slab, z1 = std::min(nz, z0 + slab);
         const int64_t planes = std::min(z1 + 1, nz) - z0;  // with the halo plane
@@ -161,24 +230,7 @@ tigre_status forward_ooc_impl(tigre_geometry* g, const float* vol_host, float* p
                                    cudaMemcpyHostToDevice, S.copy));
         TIGRE_CUDA(cudaEventRecord(copied[b], S.copy));
         TIGRE_CUDA(cudaStreamWaitEvent(st, copied[b], 0));
-        tigre_geometry_desc pd = d;
-        pd.n_voxel[2] = planes;
-        for (int l = 0; l < 2; ++l)
-            if (pad[l]) TIGRE_TRY(fill_padded_f32(pd, raw[b], pad[l], l, st));
-        if (planes < slab + 1)  // a shorter last slab: clear the stale planes above it
-            for (int l = 0; l < 2; ++l)
-                if (pad[l]) {
-                    const int64_t pp = (l ? ny : nx) + 2 * kPad, pm = (l ? nx : ny) + 2 * kPad;
-                    const int64_t from = (planes + kPad) * pp * pm;
-                    TIGRE_CUDA(cudaMemsetAsync(pad[l] + from, 0,
-                                               sizeof(float) * (size_t)(padded_elems(sd) - from), st));
-                }
-        TIGRE_CUDA(cudaEventRecord(consumed[b], st));
-        // Cells of this slab in padded z: [z0+P, z1+P); the first slab also owns
-        // the cells below plane 0, the last the cells above plane nz-1.
-        const int cell_lo = s == 0 ? -1000000 : (int)(z0 + kPad);
-        const int cell_hi = s == nslab - 1 ? 1000000 : (int)(z1 + kPad);
-        TIGRE_TRY(forward_slab_impl(g, sd, pad, quad, proj, a0, na, cell_lo, cell_hi, (int)z0, st));
+        TIGRE_TRY(F.project(s, raw[b], proj, a0, na, st, consumed[b]));
     }
     TIGRE_CUDA(cudaStreamSynchronize(st));
     return TIGRE_OK;
@@ -278,11 +330,27 @@ extern "C" tigre_status tigre_backward_ooc(tigre_geometry_t geo, const float* pr
 
 // ------------------------------------------------------- out-of-core CGLS
 //
-// CGLS (same iteration as tigre_cgls) for volumes kept in host memory: the
-// volume-sized vectors x, p, s live in pinned host memory and reach the GPU
-// only through the out-of-core operators (z-slabs streamed on a copy stream);
-// the projection-sized vectors b, r, q stay on the device.  Volume-sized
-// vector updates and their FP64 inner products run on the host cores.
+// CGLS (same iteration as tigre_cgls) when its six vectors do not fit on the
+// device.  Two placements, chosen from the device budget:
+//
+// Placement 1 ("host vectors"): the volume-sized vectors x, p, s live in
+// pinned host memory and reach the GPU only through the out-of-core
+// operators; the projection-sized b, r, q stay on the device.  Volume-sized
+// updates and their FP64 inner products run on the host cores.  Device
+// memory: three projection sets plus slab buffers.
+//
+// Placement 2 ("streamed direction"): x, r, q stay on the device; only the
+// search direction p lives in host memory (in the caller's x buffer, which
+// is free while x is on the device), streamed through in z-slabs.  s = A^T r
+// is never stored: one pass backprojects slab by slab for ||s||^2 only, and
+// a second pass recomputes each slab of s (bitwise the same), updates
+// x += alpha p and p = s + beta p there, copies the new p slab out, and
+// projects it into q = A p for the next iteration (the slab's halo plane is
+// the first plane of the next slab, so a slab is projected once its
+// successor's p is known).  Device memory: one volume, two projection sets
+// and slab buffers; host memory: none beyond the caller's b and x.  An
+// iteration costs one projection and two backprojections instead of one of
+// each; the last iteration only streams p for x += alpha p.
 
 namespace tigre {
 namespace {
@@ -313,21 +381,85 @@ double host_dot(const float* a, const float* b, int64_t n)
 
 __global__ void set_dscalar_kernel(double* dst, double v) { *dst = v; }
 
+tigre_status set_dscalar(double* dst, double v, cudaStream_t st)
+{
+    set_dscalar_kernel<<<1, 1, 0, st>>>(dst, v);
+    TIGRE_LAUNCHED("set_dscalar_kernel");
+    return TIGRE_OK;
+}
+
+constexpr int64_t kMaxSlabPlanes = 256;
+constexpr int kScalarSlots = 16;
+
+struct OocPlan {
+    int placement = 0;  // 1 host vectors, 2 streamed direction
+    int64_t slab = 0;   // z planes per slab
+};
+
+// Device bytes of placement 2 besides x, r, q: three direction slabs with
+// their halo plane, one s slab, the forward slab buffers, the
+// backprojector's padded projection band and the per-slab inner products.
+size_t placement2_workspace(const tigre_geometry* g, int64_t slab, const bool need[2])
+{
+    const tigre_geometry_desc& d = g->desc;
+    const int64_t plane = d.n_voxel[0] * d.n_voxel[1];
+    const int64_t nslab = (d.n_voxel[2] + slab - 1) / slab;
+    return sizeof(float) * (size_t)(plane * (3 * (slab + 1) + slab)) +
+           FwdSlabs::bytes(d, slab, need) +
+           bp_slab_pad_bytes(d, slab, (int64_t)g->angles.size()) +
+           sizeof(double) * (size_t)(nslab + kRedBlocks + kScalarSlots);
+}
+
+// Placement 1: the larger of the out-of-core projection's and
+// backprojection's slab buffers (they run one after the other).
+size_t placement1_workspace(const tigre_geometry* g, int64_t slab, const bool need[2])
+{
+    const tigre_geometry_desc& d = g->desc;
+    const int64_t plane = d.n_voxel[0] * d.n_voxel[1];
+    const size_t fwd = sizeof(float) * (size_t)(2 * plane * (slab + 1)) + FwdSlabs::bytes(d, slab, need);
+    const size_t bwd = sizeof(float) * (size_t)(2 * plane * slab) +
+                       bp_slab_pad_bytes(d, slab, (int64_t)g->angles.size());
+    return std::max(fwd, bwd) + sizeof(double) * (size_t)(kRedBlocks + kScalarSlots);
+}
+
+// The placement and slab thickness for a device budget (0: the free device
+// memory less 1 GiB): placement 2 with the thickest slab (at most
+// kMaxSlabPlanes) that fits, else placement 1 likewise, else OOM.
+tigre_status plan_ooc(const tigre_geometry* g, int64_t budget, OocPlan* out)
+{
+    if (budget <= 0) {
+        size_t free_b = 0, total_b = 0;
+        TIGRE_CUDA(cudaMemGetInfo(&free_b, &total_b));
+        budget = std::max<int64_t>(0, (int64_t)free_b - ((int64_t)1 << 30));
+    }
+    const int64_t nvox = n_vox(g), m = n_pix(g) * (int64_t)g->angles.size();
+    const int64_t nz = g->desc.n_voxel[2];
+    bool need[2];
+    layouts_used(g, 0, (int64_t)g->angles.size(), need);
+    const int64_t top = std::min(std::min(nz, kMaxSlabPlanes), max_slab_planes(g->desc));
+    const int64_t base2 = (int64_t)sizeof(float) * (nvox + 2 * m);
+    for (int64_t slab = top; slab >= 1; --slab)
+        if (base2 + (int64_t)placement2_workspace(g, slab, need) <= budget) {
+            *out = OocPlan{2, slab};
+            return TIGRE_OK;
+        }
+    const int64_t base1 = (int64_t)sizeof(float) * 3 * m;
+    for (int64_t slab = top; slab >= 1; --slab)
+        if (base1 + (int64_t)placement1_workspace(g, slab, need) <= budget) {
+            *out = OocPlan{1, slab};
+            return TIGRE_OK;
+        }
+    return fail(TIGRE_ERR_OOM, "device budget below three projection sets plus one-plane slabs");
+}
+
 }  // namespace
 
-tigre_status cgls_ooc_impl(tigre_geometry* g, const float* b_host, float* x_host,
-                           const tigre_solver_opts* o, double* h_hist)
+// Placement 1 (host vectors).
+static tigre_status cgls_host_vectors(tigre_geometry* g, const float* b_host, float* x_host,
+                                      const tigre_solver_opts* o, double* h_hist, int64_t slab)
 {
-    TIGRE_TRY(check_geometry(g));
     cudaStream_t st = (cudaStream_t)o->cuda_stream;
-    const tigre_geometry_desc& d = g->desc;
     const int64_t nvox = n_vox(g), na = (int64_t)g->angles.size(), m = n_pix(g) * na;
-    const int64_t plane = d.n_voxel[0] * d.n_voxel[1];
-    int64_t slab = 0;
-    if (o->device_budget_bytes > 0) {
-        const int64_t per_plane = 4 * 2 * plane + 20 * 2 * (d.n_voxel[0] + 4) * (d.n_voxel[1] + 4);
-        slab = std::max<int64_t>(1, o->device_budget_bytes / per_plane - 5);
-    }
     HostPin pin_x;
     TIGRE_TRY(pin_x.pin(x_host, sizeof(float) * (size_t)nvox));
     float *hp = nullptr, *hs = nullptr;
@@ -344,7 +476,7 @@ tigre_status cgls_ooc_impl(tigre_geometry* g, const float* b_host, float* x_host
     TIGRE_TRY(B.alloc(&b, (size_t)m));
     TIGRE_TRY(B.alloc(&r, (size_t)m));
     TIGRE_TRY(B.alloc(&q, (size_t)m));
-    TIGRE_TRY(B.alloc(&sc, (size_t)(kRedBlocks + 16)));
+    TIGRE_TRY(B.alloc(&sc, (size_t)(kRedBlocks + kScalarSlots)));
     double* partials = sc;
     double* qq = sc + kRedBlocks;       // [2]
     double* rr = sc + kRedBlocks + 2;   // [2]
@@ -363,8 +495,7 @@ tigre_status cgls_ooc_impl(tigre_geometry* g, const float* b_host, float* x_host
         TIGRE_CUDA(cudaStreamSynchronize(st));
         const double alpha = hqq != 0.0 ? gamma / hqq : 0.0;
         // r -= alpha q on the device (alpha = gamma / qq from device slots)
-        set_dscalar_kernel<<<1, 1, 0, st>>>(gam, gamma);
-        TIGRE_LAUNCHED("set_dscalar_kernel");
+        TIGRE_TRY(set_dscalar(gam, gamma, st));
         TIGRE_TRY(axpy_ratio_norm(r, q, m, gam, qq, -1.0f, partials, rr, st));
         // x += alpha p on the host, while the device updates r
         const float af = (float)alpha;
@@ -389,4 +520,180 @@ tigre_status cgls_ooc_impl(tigre_geometry* g, const float* b_host, float* x_host
     return TIGRE_OK;
 }
 
+// Placement 2 (streamed direction).
+static tigre_status cgls_streamed_direction(tigre_geometry* g, const float* b_host, float* x_host,
+                                            const tigre_solver_opts* o, double* h_hist,
+                                            int64_t slab)
+{
+    cudaStream_t st = (cudaStream_t)o->cuda_stream;
+    const tigre_geometry_desc& d = g->desc;
+    const int64_t nvox = n_vox(g), na = (int64_t)g->angles.size(), m = n_pix(g) * na;
+    const int64_t nz = d.n_voxel[2], plane = d.n_voxel[0] * d.n_voxel[1];
+    bool need[2];
+    layouts_used(g, 0, na, need);
+    HostPin pin_x, pin_b;
+    TIGRE_TRY(pin_x.pin(x_host, sizeof(float) * (size_t)nvox));
+    TIGRE_TRY(pin_b.pin(b_host, sizeof(float) * (size_t)m));
+    Streams S;
+    TIGRE_TRY(S.init());
+    Bufs B;
+    float *xd, *r, *q, *Sb, *P[3];
+    double *sc, *dots;
+    TIGRE_TRY(B.alloc(&xd, (size_t)nvox));
+    TIGRE_TRY(B.alloc(&r, (size_t)m));
+    TIGRE_TRY(B.alloc(&q, (size_t)m));
+    FwdSlabs F;
+    TIGRE_TRY(F.init(g, slab, need, B, st));
+    slab = F.slab;
+    const int64_t nslab = F.nslab;
+    for (int i = 0; i < 3; ++i) TIGRE_TRY(B.alloc(&P[i], (size_t)(plane * (slab + 1))));
+    TIGRE_TRY(B.alloc(&Sb, (size_t)(plane * slab)));
+    TIGRE_TRY(B.alloc(&sc, (size_t)(kRedBlocks + kScalarSlots)));
+    TIGRE_TRY(B.alloc(&dots, (size_t)nslab));
+    TIGRE_TRY(g->proj_pad.ensure(bp_slab_pad_bytes(d, slab, na)));
+    double* partials = sc;
+    double* qq = sc + kRedBlocks;        // ||q||^2
+    double* rr = sc + kRedBlocks + 2;    // [2] ||r||^2, ||r||
+    double* gam = sc + kRedBlocks + 4;   // gamma
+    double* gnew = sc + kRedBlocks + 5;  // gamma of the next direction
+    double* xx = sc + kRedBlocks + 6;    // ||x0||^2
+
+    TIGRE_CUDA(cudaMemcpyAsync(xd, x_host, sizeof(float) * (size_t)nvox, cudaMemcpyHostToDevice, st));
+    TIGRE_CUDA(cudaMemcpyAsync(r, b_host, sizeof(float) * (size_t)m, cudaMemcpyHostToDevice, st));
+    // r = b - A x0, skipped for x0 = 0 (then r = b exactly, as A 0 = 0).
+    TIGRE_TRY(dot_f64(xd, xd, nvox, partials, xx, st));
+    double hxx = 0.0;
+    TIGRE_CUDA(cudaMemcpyAsync(&hxx, xx, sizeof(double), cudaMemcpyDeviceToHost, st));
+    TIGRE_CUDA(cudaStreamSynchronize(st));
+    if (hxx != 0.0) {
+        TIGRE_CUDA(cudaMemsetAsync(q, 0, sizeof(float) * (size_t)m, st));
+        for (int64_t s = 0; s < nslab; ++s) TIGRE_TRY(F.project(s, xd + s * slab * plane, q, 0, na, st));
+        TIGRE_TRY(weighted_residual(r, q, nullptr, q, m, partials, rr, st));  // q = b - A x0
+        std::swap(r, q);
+    }
+
+    enum Pass { kInit, kNorm, kUpdate, kXOnly };
+    cudaEvent_t* h2d = S.ev;      // [3] direction slab landed in P[i]
+    cudaEvent_t* upd = S.ev + 3;  // [3] new direction slab ready in P[i]
+    cudaEvent_t* fwd = S.ev + 6;  // [3] P[i] no longer read by the device
+    cudaEvent_t* d2h = S.ev + 9;  // [3] P[i] copied out
+    auto planes_of = [&](int64_t s) { return std::min(nz, (s + 1) * slab) - s * slab; };
+    auto fetch = [&](int64_t s) -> tigre_status {  // old direction slab s into P[s % 3]
+        const int i = (int)(s % 3);
+        TIGRE_CUDA(cudaStreamWaitEvent(S.copy, fwd[i], 0));
+        TIGRE_CUDA(cudaMemcpyAsync(P[i], x_host + s * slab * plane,
+                                   sizeof(float) * (size_t)(planes_of(s) * plane),
+                                   cudaMemcpyHostToDevice, S.copy));
+        TIGRE_CUDA(cudaEventRecord(h2d[i], S.copy));
+        return TIGRE_OK;
+    };
+    // Project slab s of the new direction; `next` is the first plane of slab
+    // s + 1 (its halo plane), null for the last slab.
+    auto project = [&](int64_t s, const float* next) -> tigre_status {
+        const int i = (int)(s % 3);
+        if (next)
+            TIGRE_CUDA(cudaMemcpyAsync(P[i] + slab * plane, next, sizeof(float) * (size_t)plane,
+                                       cudaMemcpyDeviceToDevice, st));
+        TIGRE_TRY(F.project(s, P[i], q, 0, na, st));
+        TIGRE_CUDA(cudaEventRecord(fwd[i], st));
+        return TIGRE_OK;
+    };
+    auto sweep = [&](Pass pass, double* gamma_out) -> tigre_status {
+        for (int i = 0; i < 3; ++i) {
+            TIGRE_CUDA(cudaEventRecord(fwd[i], st));
+            TIGRE_CUDA(cudaEventRecord(d2h[i], S.copy));
+        }
+        const bool streams_p = pass == kUpdate || pass == kXOnly;
+        if (streams_p) TIGRE_TRY(fetch(0));
+        for (int64_t s = 0; s < nslab; ++s) {
+            const int i = (int)(s % 3);
+            const int64_t z0 = s * slab, n = planes_of(s) * plane;
+            if (streams_p && s + 1 < nslab) TIGRE_TRY(fetch(s + 1));  // overlaps this slab
+            if (streams_p) {
+                TIGRE_CUDA(cudaStreamWaitEvent(st, h2d[i], 0));
+                TIGRE_TRY(axpy_ratio(xd + z0 * plane, P[i], n, gam, qq, 1.0f, st));  // x += alpha p
+                if (pass == kXOnly) {
+                    TIGRE_CUDA(cudaEventRecord(fwd[i], st));
+                    continue;
+                }
+            }
+            if (pass == kInit) TIGRE_CUDA(cudaStreamWaitEvent(st, d2h[i], 0));
+            float* sl = pass == kInit ? P[i] : Sb;  // s = A^T r on this slab
+            TIGRE_TRY(backward_slab_impl(g, r, sl, 0, na, o->bp_weight, 0, (int)z0,
+                                         (int)(z0 + planes_of(s)), st));
+            if (pass != kUpdate) TIGRE_TRY(dot_f64(sl, sl, n, partials, dots + s, st));
+            if (pass == kNorm) continue;
+            if (pass == kUpdate) TIGRE_TRY(xpay_ratio(P[i], Sb, n, gnew, gam, st));  // p = s + beta p
+            TIGRE_CUDA(cudaEventRecord(upd[i], st));
+            TIGRE_CUDA(cudaStreamWaitEvent(S.copy, upd[i], 0));
+            TIGRE_CUDA(cudaMemcpyAsync(x_host + z0 * plane, P[i], sizeof(float) * (size_t)n,
+                                       cudaMemcpyDeviceToHost, S.copy));
+            TIGRE_CUDA(cudaEventRecord(d2h[i], S.copy));
+            if (s > 0) TIGRE_TRY(project(s - 1, P[i]));
+        }
+        if (pass == kInit || pass == kUpdate) TIGRE_TRY(project(nslab - 1, nullptr));
+        TIGRE_CUDA(cudaStreamSynchronize(S.copy));
+        TIGRE_CUDA(cudaStreamSynchronize(st));
+        if (gamma_out) {
+            std::vector<double> h((size_t)nslab);
+            TIGRE_CUDA(cudaMemcpy(h.data(), dots, sizeof(double) * (size_t)nslab, cudaMemcpyDeviceToHost));
+            double t = 0.0;
+            for (double v : h) t += v;
+            *gamma_out = t;
+        }
+        return TIGRE_OK;
+    };
+
+    // p = A^T r (into the host buffer), gamma = ||p||^2, q = A p
+    TIGRE_CUDA(cudaMemsetAsync(q, 0, sizeof(float) * (size_t)m, st));
+    double gamma = 0.0;
+    TIGRE_TRY(sweep(kInit, &gamma));
+    TIGRE_TRY(set_dscalar(gam, gamma, st));
+    for (int it = 0; it < o->n_iter; ++it) {
+        // alpha = gamma / ||q||^2: r -= alpha q here, x += alpha p in the sweep
+        TIGRE_TRY(dot_f64(q, q, m, partials, qq, st));
+        TIGRE_TRY(axpy_ratio_norm(r, q, m, gam, qq, -1.0f, partials, rr, st));
+        if (h_hist) {
+            TIGRE_CUDA(cudaMemcpyAsync(h_hist + it, rr + 1, sizeof(double), cudaMemcpyDeviceToHost, st));
+            TIGRE_CUDA(cudaStreamSynchronize(st));
+        }
+        if (it == o->n_iter - 1) {
+            TIGRE_TRY(sweep(kXOnly, nullptr));
+            break;
+        }
+        double gamma_new = 0.0;
+        TIGRE_TRY(sweep(kNorm, &gamma_new));
+        TIGRE_TRY(set_dscalar(gnew, gamma_new, st));
+        TIGRE_CUDA(cudaMemsetAsync(q, 0, sizeof(float) * (size_t)m, st));
+        TIGRE_TRY(sweep(kUpdate, nullptr));
+        TIGRE_TRY(set_dscalar(gam, gamma_new, st));
+    }
+    TIGRE_CUDA(cudaMemcpyAsync(x_host, xd, sizeof(float) * (size_t)nvox, cudaMemcpyDeviceToHost, st));
+    TIGRE_CUDA(cudaStreamSynchronize(st));
+    return TIGRE_OK;
+}
+
+tigre_status cgls_ooc_impl(tigre_geometry* g, const float* b_host, float* x_host,
+                           const tigre_solver_opts* o, double* h_hist)
+{
+    TIGRE_TRY(check_geometry(g));
+    OocPlan plan;
+    TIGRE_TRY(plan_ooc(g, o->device_budget_bytes, &plan));
+    if (plan.placement == 2) return cgls_streamed_direction(g, b_host, x_host, o, h_hist, plan.slab);
+    return cgls_host_vectors(g, b_host, x_host, o, h_hist, plan.slab);
+}
+
 }  // namespace tigre
+
+extern "C" tigre_status tigre_cgls_ooc_plan(tigre_geometry_t geo, int64_t device_budget_bytes,
+                                            int* placement, int64_t* slab_planes)
+{
+    using namespace tigre;
+    if (!placement || !slab_planes) return fail(TIGRE_ERR_INVALID_ARG, "null output");
+    TIGRE_TRY(check_geometry(geo));
+    OocPlan plan;
+    TIGRE_TRY(plan_ooc(geo, device_budget_bytes, &plan));
+    *placement = plan.placement;
+    *slab_planes = plan.slab;
+    return TIGRE_OK;
+}

@@ -197,6 +197,43 @@ def voxelize(ells: list[Ellipsoid], n_voxel, d_voxel, off_origin=(0.0, 0.0, 0.0)
     return vol.astype(dtype)
 
 
+def voxelize_torch(ells: list[Ellipsoid], n_voxel, d_voxel, z_range, device,
+                   off_origin=(0.0, 0.0, 0.0)):
+    """voxelize() for planes z_range[0] <= k < z_range[1], evaluated with torch
+    in FP64 on `device` (for volumes whose numpy voxelisation would take too
+    long); float32 tensor (z1 - z0, ny, nx).  Voxels exactly on an ellipsoid's
+    surface may fall on the other side than in voxelize()."""
+    import torch
+
+    nx, ny, nz = n_voxel
+    dx, dy, dz = d_voxel
+    z0, z1 = z_range
+    f64 = dict(dtype=torch.float64, device=device)
+    xs = (torch.arange(nx, **f64) - 0.5 * (nx - 1)) * dx + off_origin[0]
+    ys = (torch.arange(ny, **f64) - 0.5 * (ny - 1)) * dy + off_origin[1]
+    zs = (torch.arange(z0, z1, **f64) - 0.5 * (nz - 1)) * dz + off_origin[2]
+    vol = torch.zeros((z1 - z0, ny, nx), **f64)
+    for e in ells:
+        r = max(e.axes)
+        ix = torch.nonzero((xs - e.centre[0]).abs() <= r).flatten()
+        iy = torch.nonzero((ys - e.centre[1]).abs() <= r).flatten()
+        iz = torch.nonzero((zs - e.centre[2]).abs() <= r).flatten()
+        if len(ix) == 0 or len(iy) == 0 or len(iz) == 0:
+            continue
+        xa, xb = int(ix[0]), int(ix[-1]) + 1
+        ya, yb = int(iy[0]), int(iy[-1]) + 1
+        za, zb = int(iz[0]), int(iz[-1]) + 1
+        X = (xs[xa:xb] - e.centre[0])[None, None, :]
+        Y = (ys[ya:yb] - e.centre[1])[None, :, None]
+        Z = (zs[za:zb] - e.centre[2])[:, None, None]
+        q = 0.0
+        for a in range(3):
+            comp = e.rot[0, a] * X + e.rot[1, a] * Y + e.rot[2, a] * Z
+            q = q + (comp / e.axes[a]) ** 2
+        vol[za:zb, ya:yb, xa:xb] += torch.where(q <= 1.0, e.density, 0.0)
+    return vol.float()
+
+
 def phantom(name: str, n: int, d: float, seed: int | None = None, dtype=np.float32,
             z_range=None) -> np.ndarray:
     """Named phantoms: 'head10' (10 nested ellipsoids) or 'ellipsoids50'."""

@@ -35,7 +35,7 @@ EXPORTED = ["tigre_geometry_create", "tigre_geometry_destroy", "tigre_forward", 
             "tigre_sart",
             "tigre_cgls", "tigre_cgls_begin", "tigre_cgls_iterate", "tigre_cgls_history",
             "tigre_cgls_end", "tigre_forward_samples", "tigre_forward_ooc", "tigre_backward_ooc",
-            "tigre_geometry_set_forward_path",
+            "tigre_cgls_ooc_plan", "tigre_geometry_set_forward_path",
             "tigre_geometry_error_flags", "tigre_profile_enable",
             "tigre_profile_read", "tigre_launch_count", "tigre_last_error"]
 
@@ -82,6 +82,7 @@ _sigs = {
     "tigre_forward_samples": [_P, _I64, _I64, ctypes.POINTER(_I64)],
     "tigre_forward_ooc": [_P, _P, _P, _I64, _I64, _I64, _P],
     "tigre_backward_ooc": [_P, _P, ctypes.c_int, _P, _I64, _I64, ctypes.c_int, _I64, _I64, _P],
+    "tigre_cgls_ooc_plan": [_P, _I64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_I64)],
     "tigre_geometry_set_forward_path": [_P, ctypes.c_int],
     "tigre_geometry_error_flags": [_P, ctypes.POINTER(ctypes.c_int), ctypes.c_int],
     "tigre_profile_enable": [ctypes.c_int],
@@ -258,8 +259,10 @@ TIGRE_OUT_OF_CORE = 0x4
 def tigre_cgls(handle, proj, vol, n_iter, bp_weight="matched", stream=None,
                host=False, out_of_core=False, device_budget_bytes=0) -> np.ndarray:
     """CGLS.  host=True stages host tensors through the device; with
-    out_of_core=True the volume-sized vectors stay in host memory and stream
-    through the GPU in z-slabs (sized by device_budget_bytes, 0 = automatic)."""
+    out_of_core=True proj and vol are host tensors, part of the state stays in
+    host memory and the volume streams through the GPU in z-slabs; the
+    placement and slab thickness follow from device_budget_bytes (0 =
+    automatic), see tigre_cgls_ooc_plan."""
     o = _opts(n_iter, stream, bp_weight=bp_weight,
               device_budget_bytes=int(device_budget_bytes))
     if out_of_core:
@@ -273,6 +276,17 @@ def tigre_cgls(handle, proj, vol, n_iter, bp_weight="matched", stream=None,
                                hist.ctypes.data_as(_P)))
         return hist[:n_iter]
     return _solver(_lib.tigre_cgls, handle, proj, vol, o, host)
+
+
+def tigre_cgls_ooc_plan(handle, device_budget_bytes: int = 0) -> tuple:
+    """(placement, slab planes) of an out-of-core CGLS under the budget:
+    placement 2 keeps x, r, q on the device and streams the search direction;
+    placement 1 keeps x, p, s in host memory."""
+    pl = ctypes.c_int()
+    sl = _I64()
+    _check(_lib.tigre_cgls_ooc_plan(handle, int(device_budget_bytes), ctypes.byref(pl),
+                                    ctypes.byref(sl)))
+    return int(pl.value), int(sl.value)
 
 
 def tigre_cgls_begin(handle, proj, vol, n_iter_hint=16, bp_weight="matched", stream=None,

@@ -72,18 +72,83 @@ def test_backward_ooc_host_projections_in_chunks(tigre, chunk):
         assert rel(out.numpy(), oracle.backward(geo, ang, y_np)) < 1e-4
 
 
-@pytest.mark.parametrize("budget_mb", [0, 2])
-def test_cgls_out_of_core_equals_in_core(tigre, budget_mb):
-    """Volume vectors in host memory, streamed in z-slabs (2 MB budget: slabs
-    of a few planes); same iterates and residuals as the in-core CGLS up to
-    FP32 summation order."""
+def budgets_by_plan(tigre, G):
+    """Device budgets that give each (placement, slab planes) plan, smallest
+    budget per plan, scanning 64 KiB .. 64 MiB."""
+    plans = {}
+    b = 64 << 10
+    while b < (64 << 20):
+        try:
+            plans.setdefault(tigre.tigre_cgls_ooc_plan(G.handle, b), b)
+        except tigre.TigreError:
+            pass
+        b = int(b * 1.03) + 1
+    return plans
+
+
+def test_ooc_plan_orders_placements(tigre):
+    geo, ang, _ = case()
+    with tigre.Geometry(geo, ang) as G:
+        plans = budgets_by_plan(tigre, G)
+        with pytest.raises(tigre.TigreError):
+            tigre.tigre_cgls_ooc_plan(G.handle, 1024)
+        assert tigre.tigre_cgls_ooc_plan(G.handle, 0) == (2, 23)
+    ones = sorted(b for (pl, _), b in plans.items() if pl == 1)
+    twos = sorted(b for (pl, _), b in plans.items() if pl == 2)
+    assert ones and twos and max(ones) < min(twos)
+    # thicker slabs need more budget
+    for pl in (1, 2):
+        got = sorted((b, sl) for (p_, sl), b in plans.items() if p_ == pl)
+        assert [sl for _, sl in got] == sorted(sl for _, sl in got)
+
+
+def pick(plans, placement, max_slab):
+    cands = [(sl, b) for (pl, sl), b in plans.items() if pl == placement and sl <= max_slab]
+    assert cands, (placement, max_slab, plans)
+    return max(cands)
+
+
+@pytest.mark.parametrize("placement,max_slab,x0", [(0, 0, False), (2, 1, False), (2, 4, True),
+                                                   (1, 3, False), (1, 3, True)])
+def test_cgls_out_of_core_equals_in_core(tigre, placement, max_slab, x0):
+    """Placement 2 (x, r, q on the device, direction streamed through the
+    host buffer, s recomputed) and placement 1 (x, p, s in host memory), with
+    slabs forced thin so that many slabs, the three-buffer ring and a short
+    last slab are exercised; same iterates and residuals as the in-core CGLS
+    up to FP32 summation order."""
+    geo, ang, vol = case()
+    b = oracle.forward(geo, ang, vol).astype(np.float32)
+    start = (0.3 * synth.random_volume((23, 29, 37), seed=9)).astype(np.float32) if x0 else \
+        np.zeros((23, 29, 37), np.float32)
+    with tigre.Geometry(geo, ang) as G:
+        budget = 0
+        if placement:
+            slab, budget = pick(budgets_by_plan(tigre, G), placement, max_slab)
+            assert tigre.tigre_cgls_ooc_plan(G.handle, budget) == (placement, slab)
+        xd = torch.from_numpy(start.copy()).cuda()
+        hd = tigre.tigre_cgls(G.handle, torch.from_numpy(b).cuda(), xd, 6)
+        xh = torch.from_numpy(start.copy())
+        hh = tigre.tigre_cgls(G.handle, torch.from_numpy(b), xh, 6, out_of_core=True,
+                              device_budget_bytes=budget)
+    np.testing.assert_allclose(hh, hd, rtol=1e-5)
+    assert rel(xh.numpy(), xd.cpu().numpy()) < 1e-5
+
+
+@pytest.mark.parametrize("n_iter", [0, 1, 2])
+def test_cgls_streamed_direction_short_runs(tigre, n_iter):
+    """0 iterations leave x as given; 1 iteration is the first sweep plus the
+    x-only pass; 2 adds one full norm and update sweep."""
     geo, ang, vol = case()
     b = oracle.forward(geo, ang, vol).astype(np.float32)
     with tigre.Geometry(geo, ang) as G:
+        slab, budget = pick(budgets_by_plan(tigre, G), 2, 5)
         xd = torch.zeros(G.vol_shape, device="cuda")
-        hd = tigre.tigre_cgls(G.handle, torch.from_numpy(b).cuda(), xd, 6)
+        hd = tigre.tigre_cgls(G.handle, torch.from_numpy(b).cuda(), xd, n_iter)
         xh = torch.zeros(G.vol_shape)
-        hh = tigre.tigre_cgls(G.handle, torch.from_numpy(b), xh, 6, out_of_core=True,
-                              device_budget_bytes=budget_mb << 20)
+        hh = tigre.tigre_cgls(G.handle, torch.from_numpy(b), xh, n_iter, out_of_core=True,
+                              device_budget_bytes=budget)
     np.testing.assert_allclose(hh, hd, rtol=1e-5)
-    assert rel(xh.numpy(), xd.cpu().numpy()) < 1e-5
+    if n_iter == 0:
+        assert not xh.any()
+    else:
+        assert rel(xh.numpy(), xd.cpu().numpy()) < 1e-5
