@@ -8,6 +8,8 @@ Operators (``oracle.c``, plain C, FP64, OpenMP over independent rays/voxels):
     forward, forward_rays          interpolated ray-driven projector (Sec. 2.1)
     backward, backward_voxels      voxel-driven BP, FDK / matched weights (Sec. 2.2)
     adjoint, adjoint_voxels        exact transpose of the projector
+    siddon_forward, siddon_forward_rays, siddon_adjoint
+                                   ray-voxel intersection (Siddon) projector
     tv_value, tv_grad, tv_steps    gradient-descent TV (Sec. 2.3)
 Solvers (this file, numpy FP64, written as the textbook iterations):
     sirt, os_sart (with optional TV after each iteration), cgls.
@@ -58,6 +60,9 @@ def _load():
                 "oracle_backward_voxels": [P, P, I, P, P, I, P, ctypes.c_int],
                 "oracle_adjoint": [P, P, I, P, P],
                 "oracle_adjoint_voxels": [P, P, I, P, P, I, P],
+                "oracle_siddon_forward": [P, P, I, P, P],
+                "oracle_siddon_forward_rays": [P, P, P, P, I, P],
+                "oracle_siddon_adjoint": [P, P, I, P, P],
                 "oracle_tv_value": [P, I, I, I, ctypes.c_double],
                 "oracle_tv_grad": [P, I, I, I, ctypes.c_double, P],
                 "oracle_tv_grad_voxels": [P, I, I, I, ctypes.c_double, P, I, P],
@@ -154,6 +159,40 @@ def backward_voxels(geo: dict, angles, proj, voxels, mode: int = BP_MATCHED) -> 
     out = np.empty(len(idx), dtype=np.float64)
     lib.oracle_backward_voxels(_ptr(_geo_array(geo)), _ptr(ang), len(ang), _ptr(p), _ptr(idx),
                                len(idx), _ptr(out), int(mode))
+    return out
+
+
+def siddon_forward(geo: dict, angles, vol) -> np.ndarray:
+    """Ray-voxel intersection projection of a piecewise-constant volume."""
+    lib = _load()
+    vshape, dshape = _shapes(geo)
+    ang = _f64(angles)
+    v = _f64(vol).reshape(vshape)
+    out = np.empty((len(ang),) + dshape, dtype=np.float64)
+    lib.oracle_siddon_forward(_ptr(_geo_array(geo)), _ptr(ang), len(ang), _ptr(v), _ptr(out))
+    return out
+
+
+def siddon_forward_rays(geo: dict, angles, vol, rays) -> np.ndarray:
+    """Siddon projection at selected rays given as (a, q, p) rows."""
+    lib = _load()
+    vshape, _ = _shapes(geo)
+    v = _f64(vol).reshape(vshape)
+    idx = np.ascontiguousarray(rays, dtype=np.int64)
+    out = np.empty(len(idx), dtype=np.float64)
+    lib.oracle_siddon_forward_rays(_ptr(_geo_array(geo)), _ptr(_f64(angles)), _ptr(v), _ptr(idx),
+                                   len(idx), _ptr(out))
+    return out
+
+
+def siddon_adjoint(geo: dict, angles, proj) -> np.ndarray:
+    """Exact transpose of siddon_forward (serial scatter)."""
+    lib = _load()
+    vshape, dshape = _shapes(geo)
+    ang = _f64(angles)
+    p = _f64(proj).reshape((len(ang),) + dshape)
+    out = np.empty(vshape, dtype=np.float64)
+    lib.oracle_siddon_adjoint(_ptr(_geo_array(geo)), _ptr(ang), len(ang), _ptr(p), _ptr(out))
     return out
 
 

@@ -150,3 +150,35 @@ def voxel_centre(geo: dict, i, j, k) -> np.ndarray:
     d = np.array(geo["d_voxel"])
     o = np.array(geo["off_origin"])
     return (np.array([i, j, k], dtype=float) - (n - 1) / 2.0) * d + o
+
+
+def box_chord(S: np.ndarray, P: np.ndarray, lo, hi) -> float:
+    """Length (mm) of the part of segment S->P inside the world-space box
+    [lo, hi] (Kay-Kajiya slab clipping in world coordinates)."""
+    d = P - S
+    t0, t1 = 0.0, 1.0
+    for a in range(3):
+        if d[a] == 0.0:
+            if not (lo[a] < S[a] < hi[a]):
+                return 0.0
+            continue
+        ta, tb = sorted(((lo[a] - S[a]) / d[a], (hi[a] - S[a]) / d[a]))
+        t0, t1 = max(t0, ta), min(t1, tb)
+    return max(0.0, t1 - t0) * float(np.linalg.norm(d))
+
+
+def voxel_box(geo: dict, i: int, j: int, k: int):
+    """World-space box of voxel (i, j, k): its centre +- half a voxel."""
+    n = np.array(geo["n_voxel"], dtype=float)
+    d = np.array(geo["d_voxel"])
+    o = np.array(geo["off_origin"])
+    c = (np.array([i, j, k], dtype=float) - (n - 1) / 2.0) * d + o
+    return c - d / 2.0, c + d / 2.0
+
+
+def volume_box(geo: dict):
+    """World-space box covered by all voxels."""
+    n = np.array(geo["n_voxel"], dtype=float)
+    d = np.array(geo["d_voxel"])
+    o = np.array(geo["off_origin"])
+    return o - n * d / 2.0, o + n * d / 2.0
