@@ -11,6 +11,8 @@ Operators (``oracle.c``, plain C, FP64, OpenMP over independent rays/voxels):
     siddon_forward, siddon_forward_rays, siddon_adjoint
                                    ray-voxel intersection (Siddon) projector
     tv_value, tv_grad, tv_steps    gradient-descent TV (Sec. 2.3)
+    ramp_kernel, fdk               FDK: cosine weights, Ram-Lak ramp filter
+                                   along detector rows, FDK-weighted backprojection
 Solvers (this file, numpy FP64, written as the textbook iterations):
     sirt, os_sart (with optional TV after each iteration), cgls.
 """
@@ -220,6 +222,63 @@ def adjoint_voxels(geo: dict, angles, proj, voxels) -> np.ndarray:
     return out
 
 
+def ramp_kernel(n: int) -> np.ndarray:
+    """Dimensionless Ram-Lak kernel h[k], k = -(n-1) .. n-1: the coefficients
+    of the ramp |w| band-limited to the Nyquist frequency (Kak & Slaney's
+    discrete ramp), h[0] = 1/4, h[odd k] = -1/(pi k)^2, h[even k] = 0.  With
+    sample spacing tau the kernel is h / tau^2."""
+    k = np.arange(-(n - 1), n, dtype=np.float64)
+    h = np.zeros_like(k)
+    h[k == 0] = 0.25
+    odd = (np.abs(k) % 2) == 1
+    h[odd] = -1.0 / (np.pi * k[odd]) ** 2
+    return h
+
+
+def fdk_angle_weights(angles) -> np.ndarray:
+    """Angular quadrature weight of each angle: half the angle between its
+    neighbours on the circle (2 pi / N for N uniform angles)."""
+    a = np.mod(_f64(angles), 2 * np.pi)
+    order = np.argsort(a)
+    srt = a[order]
+    nxt = np.roll(srt, -1)
+    prv = np.roll(srt, 1)
+    gap_n = np.mod(nxt - srt, 2 * np.pi)
+    gap_p = np.mod(srt - prv, 2 * np.pi)
+    if len(a) == 1:
+        gap_n = gap_p = np.array([2 * np.pi])
+    w = np.empty_like(a)
+    w[order] = 0.5 * (gap_n + gap_p)
+    return w
+
+
+def fdk(geo: dict, angles, proj) -> np.ndarray:
+    """Feldkamp-Davis-Kress reconstruction of a full circular scan:
+    each projection is weighted by DSD/sqrt(DSD^2 + u^2 + v^2), each detector
+    row is convolved (linearly, zero outside the detector) with the Ram-Lak
+    kernel of the detector pitch scaled to the isocentre (du DSO/DSD), and the
+    filtered projections are backprojected with the FDK distance weight
+    (DSO/(DSO-s))^2, each angle times half its angular weight."""
+    _, dshape = _shapes(geo)
+    ang = _f64(angles)
+    g = _f64(proj).reshape((len(ang),) + dshape)
+    nu, nv = geo["n_det"]
+    du, dv = geo["d_det"]
+    u = (np.arange(nu) - (nu - 1) / 2.0) * du + geo["off_det"][0]
+    v = (np.arange(nv) - (nv - 1) / 2.0) * dv + geo["off_det"][1]
+    dsd = geo["DSD"]
+    cosw = dsd / np.sqrt(dsd ** 2 + u[None, :] ** 2 + v[:, None] ** 2)
+    tau = du * geo["DSO"] / dsd
+    h = ramp_kernel(nu) / tau
+    q = np.empty_like(g)
+    for a in range(len(ang)):
+        gw = g[a] * cosw
+        for r in range(nv):
+            q[a, r] = np.convolve(gw[r], h)[nu - 1:2 * nu - 1]
+    q *= 0.5 * fdk_angle_weights(ang)[:, None, None]
+    return backward(geo, ang, q, BP_FDK)
+
+
 def tv_value(vol, eps: float) -> float:
     v = _f64(vol)
     nz, ny, nx = v.shape
@@ -315,24 +374,29 @@ def os_sart(geo, angles, b, n_iter, subset=20, lam=1.0, nonneg=False, x0=None,
     return x, np.array(resid)
 
 
-def cgls(geo, angles, b, n_iter, x0=None, bp="matched"):
+def cgls(geo, angles, b, n_iter, x0=None, bp="matched", projector="interpolated"):
     """CGLS (conjugate gradients on A^T A x = A^T b), FP64 scalars.
 
     bp = "matched" (voxel-driven pseudo-matched backprojector) or "adjoint"
-    (exact transpose).  Returns (x, resid) with resid[k] = ||r_k||_2 after
-    iteration k.
+    (exact transpose of the projector); projector = "interpolated" or
+    "siddon".  Returns (x, resid) with resid[k] = ||r_k||_2 after iteration k.
     """
     vshape, _ = _shapes(geo)
     b = _f64(b)
-    At = (lambda y: adjoint(geo, angles, y)) if bp == "adjoint" else \
-        (lambda y: backward(geo, angles, y, BP_MATCHED))
+    A = (lambda v: siddon_forward(geo, angles, v)) if projector == "siddon" else \
+        (lambda v: forward(geo, angles, v))
+    if bp == "adjoint":
+        At = (lambda y: siddon_adjoint(geo, angles, y)) if projector == "siddon" else \
+            (lambda y: adjoint(geo, angles, y))
+    else:
+        At = lambda y: backward(geo, angles, y, BP_MATCHED)  # noqa: E731
     x = np.zeros(vshape) if x0 is None else _f64(x0).reshape(vshape).copy()
-    r = b - forward(geo, angles, x) if x0 is not None else b.copy()
+    r = b - A(x) if x0 is not None else b.copy()
     p = At(r)
     gamma = float(np.sum(p * p))
     resid = []
     for _ in range(n_iter):
-        q = forward(geo, angles, p)
+        q = A(p)
         alpha = gamma / float(np.sum(q * q))
         x = x + alpha * p
         r = r - alpha * q
