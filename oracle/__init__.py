@@ -11,6 +11,8 @@ Operators (``oracle.c``, plain C, FP64, OpenMP over independent rays/voxels):
     siddon_forward, siddon_forward_rays, siddon_adjoint
                                    ray-voxel intersection (Siddon) projector
     tv_value, tv_grad, tv_steps    gradient-descent TV (Sec. 2.3)
+    rof_denoise (this file)        ROF-model TV minimisation (Sec. 2.3), first-order
+                                   primal-dual iteration
     ramp_kernel, fdk               FDK: cosine weights, Ram-Lak ramp filter
                                    along detector rows, FDK-weighted backprojection
 Solvers (this file, numpy FP64, written as the textbook iterations):
@@ -311,6 +313,62 @@ def tv_steps(vol, n_steps: int, alpha: float, eps: float) -> np.ndarray:
 
 
 # ------------------------------------------------------------------- solvers
+
+def rof_grad(u):
+    """Forward differences along x, y, z of u (nz, ny, nx); zero at the last
+    index of each axis (Neumann boundary).  Returns (gx, gy, gz)."""
+    u = _f64(u)
+    gx, gy, gz = np.zeros_like(u), np.zeros_like(u), np.zeros_like(u)
+    gx[:, :, :-1] = u[:, :, 1:] - u[:, :, :-1]
+    gy[:, :-1, :] = u[:, 1:, :] - u[:, :-1, :]
+    gz[:-1, :, :] = u[1:, :, :] - u[:-1, :, :]
+    return gx, gy, gz
+
+
+def rof_div(px, py, pz):
+    """Divergence, the negative adjoint of rof_grad: <grad u, p> = -<u, div p>."""
+    d = np.zeros_like(px)
+    for p_, ax in ((px, 2), (py, 1), (pz, 0)):
+        p_ = np.moveaxis(p_, ax, 0)
+        dd = np.moveaxis(d, ax, 0)
+        n = p_.shape[0]
+        if n == 1:
+            continue
+        dd[0] += p_[0]
+        dd[1:n - 1] += p_[1:n - 1] - p_[0:n - 2]
+        dd[n - 1] -= p_[n - 2]
+    return d
+
+
+def rof_denoise(f, lam: float, n_iter: int) -> np.ndarray:
+    """ROF model min_u ||grad u||_(2,1) + lam/2 ||u - f||^2 (isotropic TV),
+    solved with the first-order primal-dual iteration (over-relaxation 1,
+    step sizes tau = sigma = 1/sqrt(12), the bound ||grad||^2 <= 12 in 3-D):
+        p    <- (p + sigma grad(ubar)) / max(1, |p + sigma grad(ubar)|)
+        u'   <- (u + tau div p + tau lam f) / (1 + tau lam)
+        ubar <- 2 u' - u,  u <- u'
+    from u = ubar = f, p = 0."""
+    f = _f64(f)
+    tau = sigma = 1.0 / np.sqrt(12.0)
+    u = f.copy()
+    ubar = f.copy()
+    px, py, pz = np.zeros_like(f), np.zeros_like(f), np.zeros_like(f)
+    for _ in range(n_iter):
+        gx, gy, gz = rof_grad(ubar)
+        px, py, pz = px + sigma * gx, py + sigma * gy, pz + sigma * gz
+        nrm = np.maximum(1.0, np.sqrt(px * px + py * py + pz * pz))
+        px, py, pz = px / nrm, py / nrm, pz / nrm
+        un = (u + tau * rof_div(px, py, pz) + tau * lam * f) / (1.0 + tau * lam)
+        ubar = 2.0 * un - u
+        u = un
+    return u
+
+
+def rof_objective(u, f, lam: float) -> float:
+    gx, gy, gz = rof_grad(u)
+    return float(np.sum(np.sqrt(gx * gx + gy * gy + gz * gz)) +
+                 0.5 * lam * np.sum((_f64(u) - _f64(f)) ** 2))
+
 
 def _guarded_reciprocal(a: np.ndarray, floor: float = 1e-12) -> np.ndarray:
     out = np.zeros_like(a)

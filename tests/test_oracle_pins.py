@@ -548,3 +548,45 @@ def test_fdk_wide_fan_mid_plane_is_exact_fan_beam():
     rec = oracle.fdk(geo, ang, oracle.forward(geo, ang, vol))
     core = (np.abs(z) <= 0.5) & ((x - 13) ** 2 + y ** 2 <= 4 ** 2)
     assert abs(rec[core].mean() - 0.7) < 2.5e-3
+
+
+# --------------------------------------------------------------- ROF TV
+
+def test_rof_divergence_is_minus_gradient_transpose():
+    rng = np.random.default_rng(14)
+    u = rng.random((4, 5, 6))
+    p = [rng.random((4, 5, 6)) for _ in range(3)]
+    lhs = sum(np.sum(a * b) for a, b in zip(oracle.rof_grad(u), p))
+    assert lhs == pytest.approx(-np.sum(u * oracle.rof_div(*p)), rel=1e-12)
+    # one-voxel axes have no differences at all
+    flat = rng.random((1, 5, 6))
+    assert not oracle.rof_grad(flat)[2].any()
+
+
+def test_rof_leaves_constants_and_solves_a_step_exactly():
+    """A constant image is its own ROF solution; a two-level step (0 on a
+    voxels, h on b voxels, constant across y and z) has the closed-form
+    solution 1/(lam a) and h - 1/(lam b) (each level moves by the jump's
+    unit TV weight over its mass)."""
+    c = np.full((3, 4, 5), 0.42)
+    np.testing.assert_allclose(oracle.rof_denoise(c, 0.7, 50), c, rtol=0, atol=1e-15)
+    f = np.zeros((2, 3, 16))
+    f[:, :, 6:] = 1.0
+    lam = 1.0
+    u = oracle.rof_denoise(f, lam, 1500)
+    np.testing.assert_allclose(u[:, :, :6], 1.0 / (lam * 6), atol=1e-10)
+    np.testing.assert_allclose(u[:, :, 6:], 1.0 - 1.0 / (lam * 10), atol=1e-10)
+
+
+def test_rof_converged_point_is_a_minimum():
+    """After many iterations on a random image, small perturbations in random
+    directions do not lower the ROF objective."""
+    rng = np.random.default_rng(15)
+    f = rng.random((5, 6, 7))
+    lam = 4.0
+    u = oracle.rof_denoise(f, lam, 4000)
+    J = oracle.rof_objective(u, f, lam)
+    assert J < oracle.rof_objective(f, f, lam)
+    for _ in range(20):
+        d = rng.standard_normal(f.shape)
+        assert oracle.rof_objective(u + 1e-3 * d, f, lam) >= J - 1e-9
