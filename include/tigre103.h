@@ -253,13 +253,61 @@ TIGRE_API tigre_status tigre_cgls_iterate(tigre_cgls_t state, int n_iter);
 TIGRE_API tigre_status tigre_cgls_history(tigre_cgls_t state, double* resid_hist, int n);
 TIGRE_API tigre_status tigre_cgls_end(tigre_cgls_t state);
 
+/* ROF-model TV minimisation (Sec. 2.3, the second TV minimiser the paper
+ * uses): u = argmin ||grad u||_(2,1) + lambda/2 ||u - f||^2 (isotropic TV,
+ * forward differences, zero at the last index of each axis), by n_iter steps
+ * of the first-order primal-dual iteration (over-relaxation 1, step sizes
+ * 1/sqrt(12)) from u = f and zero dual.  f, u: DEVICE F32 (nz, ny, nx); u is
+ * overwritten and may be f itself.  lambda > 0.  Allocates four (five when u
+ * is f) volumes of workspace stream-ordered for the call; asynchronous on
+ * cuda_stream.  No counterpart of the voxel order's halo splitting is needed
+ * on one device. */
+TIGRE_API tigre_status tigre_rof_denoise(const int64_t n_voxel[3], const float* f, float* u,
+                                         double lambda, int n_iter, void* cuda_stream);
+
+/* FDK reconstruction of a circular scan over all the handle's angles (the
+ * paper's analytic reconstruction, Sec. 1 and Sec. 3.2, for comparison and as
+ * an initialiser): each projection is weighted by DSD/sqrt(DSD^2+u^2+v^2),
+ * each detector row convolved (linearly, zero outside) with the Ram-Lak
+ * kernel of pitch tau = du DSO/DSD (h0 = 1/(4 tau^2), h at odd k =
+ * -1/(pi k tau)^2, even k zero; times tau for the sum), and the result
+ * backprojected with the FDK weight (DSO/(DSO-s))^2, each angle times half
+ * its angular weight (half the angle between its neighbours on the circle).
+ * proj: DEVICE (n_angles, nv, nu) in proj_dtype; vol: DEVICE (nz, ny, nx) in
+ * vol_dtype, overwritten.  Allocates the filtered projections (F32)
+ * stream-ordered for the call.  Asynchronous on cuda_stream except for one
+ * small table upload. */
+TIGRE_API tigre_status tigre_fdk(tigre_geometry_t geo, const void* proj, tigre_dtype proj_dtype,
+                                 void* vol, tigre_dtype vol_dtype, void* cuda_stream);
+
+/* Projector of this handle (Sec. 2.1 offers both; Sec. 3.1 reconstructs with
+ * each): INTERPOLATED (default) samples the trilinear interpolant at the
+ * midpoints of K equal steps; SIDDON integrates the piecewise-constant volume
+ * exactly, voxel (i,j,k) filling [i-1/2, i+1/2] x ... in index space, as the
+ * sum of its intersection lengths (mm) with the ray times the voxel values.
+ * The choice applies to tigre_forward, to TIGRE_BP_EXACT_ADJOINT (the
+ * transpose of the chosen projector) and to the solvers; the voxel-driven
+ * MATCHED and FDK backprojectors are the same for both.  Out-of-core
+ * projection supports INTERPOLATED only (TIGRE_ERR_UNSUPPORTED otherwise). */
+typedef enum { TIGRE_PROJ_INTERPOLATED = 0, TIGRE_PROJ_SIDDON = 1 } tigre_projector;
+TIGRE_API tigre_status tigre_geometry_set_projector(tigre_geometry_t geo, int projector);
+
+/* Edge (voxels) of the x-y bricks into which out-of-core projections cut
+ * each z-slab (0 = default 512).  Rays resident on the GPU at one time then
+ * read one brick's planes, which stay in L2; at 3072^2 a single quad plane
+ * of the slab is larger than L2.  Only the partial sums' order changes. */
+TIGRE_API tigre_status tigre_geometry_set_brick(tigre_geometry_t geo, int64_t edge);
+
 /* Forward-projector kernel choice for this handle: 0 = automatic (the quad
  * gather kernel), 1 = scalar L1 gather kernel, 2 = shared-memory slab kernel
  * (TMA-staged; only for geometries whose ray bundles fit its staging box,
  * otherwise it reports error bit 2 and NaN), 3 = quad gather kernel (two
  * 16-byte loads per sample from a layout holding the four taps of a cell's
- * plane; four times the volume in workspace).  All compute the same sums in
- * the same order and give identical results. */
+ * plane; four times the volume in workspace), 4 = quad gather kernel taking a
+ * ray's samples two at a time (both samples' loads issued together).  All
+ * compute the same sums in the same order and give identical results.
+ * Out-of-core slab projections use the quad kernel, two samples at a time for
+ * path 4. */
 TIGRE_API tigre_status tigre_geometry_set_forward_path(tigre_geometry_t geo, int path);
 
 /* Error bits raised by kernels of this handle (1 = a bounded wait timed out,

@@ -442,13 +442,17 @@ static tigre_status launch_adjoint(tigre_geometry* g, const TP* proj, TV* vol, i
     float* axy = need[0] ? (float*)g->adj_xy.ptr : nullptr;
     float* ayx = need[1] ? (float*)g->adj_yx.ptr : nullptr;
     ProfScope prof(kProfAdjoint, st);
-    for (int64_t s = 0; s < na; s += 65535) {
-        const int64_t cnt = std::min<int64_t>(65535, na - s);
-        dim3 grid((unsigned)((c.nu + 31) / 32), (unsigned)cnt, (unsigned)((c.nv + 7) / 8));
-        adj_scatter_kernel<TP><<<grid, dim3(32, 8), 0, st>>>(
-            proj + s * (int64_t)c.nu * c.nv, axy, ayx, (const FwdAngle*)g->fwd_params.ptr, c,
-            (int)(a0 + s));
-        TIGRE_LAUNCHED("adj_scatter_kernel");
+    if (g->projector == TIGRE_PROJ_SIDDON) {
+        TIGRE_TRY(launch_siddon_scatter<TP>(g, proj, axy, ayx, a0, na, st));
+    } else {
+        for (int64_t s = 0; s < na; s += 65535) {
+            const int64_t cnt = std::min<int64_t>(65535, na - s);
+            dim3 grid((unsigned)((c.nu + 31) / 32), (unsigned)cnt, (unsigned)((c.nv + 7) / 8));
+            adj_scatter_kernel<TP><<<grid, dim3(32, 8), 0, st>>>(
+                proj + s * (int64_t)c.nu * c.nv, axy, ayx, (const FwdAngle*)g->fwd_params.ptr, c,
+                (int)(a0 + s));
+            TIGRE_LAUNCHED("adj_scatter_kernel");
+        }
     }
     dim3 grid((unsigned)((c.nx + 31) / 32), (unsigned)((c.ny + 31) / 32), (unsigned)c.nz);
     adj_finish_kernel<TV><<<grid, dim3(32, 8), 0, st>>>(axy, ayx, vol, c.nx, c.ny, c.nz,

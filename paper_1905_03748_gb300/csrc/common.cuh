@@ -96,6 +96,8 @@ struct DeviceBuffer {
     void release();
 };
 
+constexpr int64_t kBrickDefault = 512;  // x-y brick edge of out-of-core slab projections
+
 // Per-angle parameters of the forward projector, expressed in the index
 // coordinates of the padded volume layout the angle uses.  "f", "m", "s" are
 // the fastest, middle and slowest memory axes of that layout.
@@ -136,8 +138,11 @@ struct tigre_geometry {
     tigre::DeviceBuffer scratch_vol;  // FP32 volume-sized scratch
     tigre::DeviceBuffer scratch_red;  // reduction partials / device scalars
     std::vector<int> layout;          // forward-projector layout per angle (host copy)
-    int fwd_path = 0;                 // 0 auto, 1 L1 scalar, 2 TMA slab, 3 L1 quad
+    int fwd_path = 0;                 // 0 auto, 1 L1 scalar, 2 TMA slab, 3 quad, 4 quad pairs
+    int projector = 0;                // TIGRE_PROJ_INTERPOLATED or TIGRE_PROJ_SIDDON
     tigre::DeviceBuffer err_flag;     // int: error bits set by kernels (bounds, timeouts)
+    tigre::DeviceBuffer brick_prange; // int2 per (x-y brick, angle): detector columns reaching it
+    int64_t brick = tigre::kBrickDefault;  // x-y brick edge (voxels) of slab projections
 };
 
 namespace tigre {
@@ -168,6 +173,15 @@ tigre_status backward_slab_impl(tigre_geometry* g, const float* proj, float* vol
 // CGLS with host-resident volume vectors (ooc.cu).
 tigre_status cgls_ooc_impl(tigre_geometry* g, const float* b_host, float* x_host,
                            const tigre_solver_opts* o, double* h_hist);
+
+// Siddon projector and its transpose (siddon.cu); volumes in the padded
+// layouts, accumulators as for the exact adjoint.
+template <typename TV, typename TP>
+tigre_status launch_siddon_forward(tigre_geometry* g, const TV* vxy, const TV* vyx, TP* proj,
+                                   int64_t a0, int64_t na, const int* order, cudaStream_t st);
+template <typename TP>
+tigre_status launch_siddon_scatter(tigre_geometry* g, const TP* proj, float* acc_xy, float* acc_yx,
+                                   int64_t a0, int64_t na, cudaStream_t st);
 
 // Shared-memory slab forward projector (forward_tma.cu).
 bool tma_forward_fits(const tigre_geometry_desc& d, size_t elem);

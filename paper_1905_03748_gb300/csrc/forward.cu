@@ -21,6 +21,7 @@
 //  * floor() without conversion instructions (split_floor).
 #include <algorithm>
 #include <cmath>
+#include <vector>
 
 #include "ray.cuh"
 
@@ -243,6 +244,52 @@ __device__ __forceinline__ float tri_sample_quad(const typename QuadOf<TV>::type
     return fmaf(as, c1 - c0, c0);
 }
 
+// Samples k and k + 1 of a ray (kf = k), added to acc in that order when t0
+// (resp. t1) holds.  Both samples' loads are issued before either
+// interpolation, so four gathers are in flight per thread; a sample not taken
+// reads the volume's first element and adds nothing, so the sum is bitwise
+// the one-sample-at-a-time sum.
+template <typename TV>
+__device__ __forceinline__ void tri_pair_quad(const typename QuadOf<TV>::type* __restrict__ qv,
+                                              const Ray& R, float kf, int PF, int PFM, int s_off,
+                                              bool t0, bool t1, float& acc)
+{
+    using Q = typename QuadOf<TV>::type;
+    int f0, m0, z0, f1, m1, z1;
+    float af0, am0, as0, af1, am1, as1;
+    const float kf1 = kf + 1.0f;
+    split_floor(fmaf(kf, R.d[0], R.x0[0]), f0, af0);
+    split_floor(fmaf(kf, R.d[1], R.x0[1]), m0, am0);
+    split_floor(fmaf(kf, R.d[2], R.x0[2]), z0, as0);
+    split_floor(fmaf(kf1, R.d[0], R.x0[0]), f1, af1);
+    split_floor(fmaf(kf1, R.d[1], R.x0[1]), m1, am1);
+    split_floor(fmaf(kf1, R.d[2], R.x0[2]), z1, as1);
+    const Q* b0 = t0 ? qv + ((z0 - s_off) * PFM + m0 * PF + f0) : qv;
+    const Q* b1 = t1 ? qv + ((z1 - s_off) * PFM + m1 * PF + f1) : qv;
+    const float4 lo0 = load_quad(b0, (TV*)nullptr);
+    const float4 hi0 = load_quad(b0 + PFM, (TV*)nullptr);
+    const float4 lo1 = load_quad(b1, (TV*)nullptr);
+    const float4 hi1 = load_quad(b1 + PFM, (TV*)nullptr);
+    {
+        const float c00 = fmaf(af0, lo0.y - lo0.x, lo0.x);
+        const float c10 = fmaf(af0, lo0.w - lo0.z, lo0.z);
+        const float c01 = fmaf(af0, hi0.y - hi0.x, hi0.x);
+        const float c11 = fmaf(af0, hi0.w - hi0.z, hi0.z);
+        const float c0 = fmaf(am0, c10 - c00, c00);
+        const float c1 = fmaf(am0, c11 - c01, c01);
+        if (t0) acc += fmaf(as0, c1 - c0, c0);
+    }
+    {
+        const float c00 = fmaf(af1, lo1.y - lo1.x, lo1.x);
+        const float c10 = fmaf(af1, lo1.w - lo1.z, lo1.z);
+        const float c01 = fmaf(af1, hi1.y - hi1.x, hi1.x);
+        const float c11 = fmaf(af1, hi1.w - hi1.z, hi1.z);
+        const float c0 = fmaf(am1, c10 - c00, c00);
+        const float c1 = fmaf(am1, c11 - c01, c01);
+        if (t1) acc += fmaf(as1, c1 - c0, c0);
+    }
+}
+
 // Restriction of a projection to one axial slab (out-of-core mode): only the
 // samples whose z cell (padded index) lies in [cell_lo, cell_hi) count, the
 // volume buffer's plane 0 is padded plane plane0, results add into the
@@ -250,6 +297,11 @@ __device__ __forceinline__ float tri_sample_quad(const typename QuadOf<TV>::type
 // reach).
 struct SlabRange {
     int cell_lo, cell_hi, plane0, q0;
+    // x-y brick of the slab (padded cell ranges; +-1000000 = unbounded) and,
+    // when not null, the detector columns [x, y] per angle whose rays can
+    // reach the brick (blocks wholly outside return at once).
+    int bx_lo, bx_hi, by_lo, by_hi;
+    const int2* prange;
 };
 
 // First k in [0, K] whose z cell satisfies pred (pred monotone along the ray).
@@ -267,28 +319,53 @@ __device__ __forceinline__ int first_k(int K, P pred)
     return lo;
 }
 
-__device__ __forceinline__ int z_cell(const Ray& R, int k)
+__device__ __forceinline__ int axis_cell(const Ray& R, int ax, int k)
 {
     int i;
     float f;
-    split_floor(fmaf((float)k, R.d[2], R.x0[2]), i, f);
+    split_floor(fmaf((float)k, R.d[ax], R.x0[ax]), i, f);
     return i;
 }
 
+// Narrow [kb, ke) to the samples whose cell along axis ax lies in [lo, hi)
+// (monotone along the ray, so the samples in range form one interval).
+__device__ __forceinline__ void cut_axis(const Ray& R, int ax, int lo, int hi, int& kb, int& ke)
+{
+    if (lo <= -1000000 && hi >= 1000000) return;
+    const float dd = R.d[ax];
+    if (dd > 0.0f) {
+        kb = max(kb, first_k(R.K, [&](int k) { return axis_cell(R, ax, k) >= lo; }));
+        ke = min(ke, first_k(R.K, [&](int k) { return axis_cell(R, ax, k) >= hi; }));
+    } else if (dd < 0.0f) {
+        kb = max(kb, first_k(R.K, [&](int k) { return axis_cell(R, ax, k) < hi; }));
+        ke = min(ke, first_k(R.K, [&](int k) { return axis_cell(R, ax, k) < lo; }));
+    } else {
+        const int c0 = axis_cell(R, ax, 0);
+        if (!(c0 >= lo && c0 < hi)) ke = kb;
+    }
+}
+
 // The L1 kernel's depth-ordered march, gathering from quad volumes.  With
-// SLAB, each ray processes only its samples [kb, ke) inside the slab.
-template <typename TV, typename TP, bool SLAB = false>
+// SLAB, each ray processes only its samples [kb, ke) inside the slab (and
+// brick).  With PAIR, the march advances two depth steps at a time and each
+// lane takes up to two samples per step (tri_pair_quad).
+template <typename TV, typename TP, bool SLAB = false, bool PAIR = false>
 __global__ void __launch_bounds__(256) fwd_quad_kernel(
     const typename QuadOf<TV>::type* __restrict__ qxy,
     const typename QuadOf<TV>::type* __restrict__ qyx, TP* __restrict__ proj,
     const FwdAngle* __restrict__ params, FwdConst c, int a_first, const int* __restrict__ order,
-    SlabRange sr = SlabRange{0, 0, 0, 0})
+    SlabRange sr)
 {
     using Q = typename QuadOf<TV>::type;
     const unsigned full = 0xffffffffu;
     const int p = blockIdx.x * 32 + threadIdx.x;
     const int q = (SLAB ? sr.q0 : 0) + (int)(blockIdx.z * blockDim.y + threadIdx.y);
     const int a = order ? order[blockIdx.y] : (int)blockIdx.y;
+    if (SLAB && sr.prange) {  // uniform per block: all its rays miss the brick
+        const int2 pr = sr.prange[a_first + a];
+        const int p0 = (int)blockIdx.x * 32;
+        if (p0 + 31 < pr.x || p0 > pr.y) return;
+    }
     const bool inside = p < c.nu && q < c.nv;
 
     Ray R;
@@ -297,16 +374,10 @@ __global__ void __launch_bounds__(256) fwd_quad_kernel(
     if (inside) setup_ray(params + a_first + a, c, p, q, R);
     int kb = 0, ke = R.K;
     if (SLAB && inside && R.ok && R.K > 0) {
-        if (R.d[2] > 0.0f) {
-            kb = first_k(R.K, [&](int k) { return z_cell(R, k) >= sr.cell_lo; });
-            ke = first_k(R.K, [&](int k) { return z_cell(R, k) >= sr.cell_hi; });
-        } else if (R.d[2] < 0.0f) {
-            kb = first_k(R.K, [&](int k) { return z_cell(R, k) < sr.cell_hi; });
-            ke = first_k(R.K, [&](int k) { return z_cell(R, k) < sr.cell_lo; });
-        } else {
-            const int cz = z_cell(R, 0);
-            ke = (cz >= sr.cell_lo && cz < sr.cell_hi) ? R.K : 0;
-        }
+        cut_axis(R, 2, sr.cell_lo, sr.cell_hi, kb, ke);
+        // the brick's x-y ranges, on the layout's (f, m) axes
+        cut_axis(R, 0, R.layout ? sr.by_lo : sr.bx_lo, R.layout ? sr.by_hi : sr.bx_hi, kb, ke);
+        cut_axis(R, 1, R.layout ? sr.bx_lo : sr.by_lo, R.layout ? sr.bx_hi : sr.by_hi, kb, ke);
     }
     const bool active = inside && R.ok && ke > kb;
     const unsigned act = __ballot_sync(full, active);
@@ -338,12 +409,25 @@ __global__ void __launch_bounds__(256) fwd_quad_kernel(
             }
             const float ns = (Y1 - Y0) / D;
             const int nslab = ns < (float)(2 * kmax + 64) ? (int)ns + 1 : 0;
-            for (int j = 1; j <= nslab; ++j) {
-                const float bound = fmaf((float)j, D, Y0);
-                if (k < ke && fmaf(kf, dy, y0) < bound) {
-                    acc += tri_sample_quad<TV>(vol, R, kf, PF, PFM, s_off);
-                    ++k;
-                    kf += 1.0f;
+            if (PAIR) {
+                const float D2 = 2.0f * D;
+                for (int j = 1; j <= (nslab + 1) / 2; ++j) {
+                    const float bound = fmaf((float)j, D2, Y0);
+                    const bool t0 = k < ke && fmaf(kf, dy, y0) < bound;
+                    const bool t1 = t0 && k + 1 < ke && fmaf(kf + 1.0f, dy, y0) < bound;
+                    if (__any_sync(full, t0)) tri_pair_quad<TV>(vol, R, kf, PF, PFM, s_off, t0, t1, acc);
+                    const int took = (int)t0 + (int)t1;
+                    k += took;
+                    kf += (float)took;
+                }
+            } else {
+                for (int j = 1; j <= nslab; ++j) {
+                    const float bound = fmaf((float)j, D, Y0);
+                    if (k < ke && fmaf(kf, dy, y0) < bound) {
+                        acc += tri_sample_quad<TV>(vol, R, kf, PF, PFM, s_off);
+                        ++k;
+                        kf += 1.0f;
+                    }
                 }
             }
         }
@@ -464,8 +548,10 @@ tigre_status forward_impl(tigre_geometry* g, const void* vol, tigre_dtype vt, vo
     const FwdConst c = make_fwd_const(d);
     bool need[2] = {false, false};
     for (int64_t a = a0; a < a0 + na; ++a) need[g->layout[(size_t)a]] = true;
-    const bool use_tma = g->fwd_path == 2;
-    const bool use_quad = g->fwd_path == 0 || g->fwd_path == 3;
+    const bool siddon = g->projector == TIGRE_PROJ_SIDDON;
+    const bool use_tma = !siddon && g->fwd_path == 2;
+    const bool use_quad = !siddon && (g->fwd_path == 0 || g->fwd_path >= 3);
+    const bool pair = g->fwd_path == 4;
     // Full-range launches visit the angles grouped by memory layout, so the
     // blocks resident at one time read one layout's z-slab (half the L2
     // working set of an interleaved order).
@@ -508,16 +594,22 @@ tigre_status forward_impl(tigre_geometry* g, const void* vol, tigre_dtype vt, vo
         }
         return dispatch_dtype(pt, [&](auto ptag) -> tigre_status {
             using TP = decltype(ptag);
+            if (siddon)
+                return launch_siddon_forward<TV, TP>(g, (const TV*)g->vol_xy.ptr,
+                                                     (const TV*)g->vol_yx.ptr, (TP*)proj, a0, na,
+                                                     order, st);
             ProfScope prof(kProfForward, st);
             if (use_quad) {
                 for (int64_t s = 0; s < na; s += 65535) {
                     const int64_t cnt = std::min<int64_t>(65535, na - s);
                     dim3 grid((unsigned)((c.nu + 31) / 32), (unsigned)cnt,
                               (unsigned)((c.nv + 7) / 8));
-                    fwd_quad_kernel<TV, TP><<<grid, dim3(32, 8), 0, st>>>(
+                    auto kern = pair ? fwd_quad_kernel<TV, TP, false, true>
+                                     : fwd_quad_kernel<TV, TP, false, false>;
+                    kern<<<grid, dim3(32, 8), 0, st>>>(
                         (const Q*)g->vol_qxy.ptr, (const Q*)g->vol_qyx.ptr,
                         (TP*)proj + s * (int64_t)c.nu * c.nv, (const FwdAngle*)g->fwd_params.ptr,
-                        c, (int)(a0 + s), order);
+                        c, (int)(a0 + s), order, SlabRange{0, 0, 0, 0, 0, 0, 0, 0, nullptr});
                     TIGRE_LAUNCHED("fwd_quad_kernel");
                 }
                 return TIGRE_OK;
@@ -537,6 +629,61 @@ tigre_status forward_impl(tigre_geometry* g, const void* vol, tigre_dtype vt, vo
     });
 }
 
+// Detector columns [lo, hi] per (brick, angle) whose rays can reach the x-y
+// brick (its voxels extended by 1.5 voxels, the interpolation support),
+// from the perspective image of the brick's corners on the detector, with
+// two columns of margin; computed in FP64 once per geometry and kept on the
+// device.  A brick the source could be inside of gets the whole detector.
+static tigre_status brick_pixel_ranges(tigre_geometry* g, const int2** out)
+{
+    const tigre_geometry_desc& d = g->desc;
+    const int64_t edge = g->brick;
+    const int64_t nbx = (d.n_voxel[0] + edge - 1) / edge;
+    const int64_t nby = (d.n_voxel[1] + edge - 1) / edge;
+    const int64_t na = (int64_t)g->angles.size();
+    const size_t bytes = sizeof(int2) * (size_t)(nbx * nby * na);
+    const uint64_t tag = 1 + (uint64_t)edge;
+    if (g->brick_prange.tag != tag || g->brick_prange.bytes < bytes) {
+        const int nu = (int)d.n_det[0];
+        const double u0 = -0.5 * (double)(nu - 1) * d.d_det[0] + d.off_det[0];
+        std::vector<int2> h((size_t)(nbx * nby * na));
+        auto world = [&](int ax, double idx) {
+            return (idx - 0.5 * (double)(d.n_voxel[ax] - 1)) * d.d_voxel[ax] + d.off_origin[ax];
+        };
+        for (int64_t by = 0; by < nby; ++by)
+            for (int64_t bx = 0; bx < nbx; ++bx) {
+                const double xs[2] = {world(0, (double)(bx * edge) - 1.5),
+                                      world(0, (double)std::min<int64_t>((bx + 1) * edge, d.n_voxel[0]) - 1.0 + 1.5)};
+                const double ys[2] = {world(1, (double)(by * edge) - 1.5),
+                                      world(1, (double)std::min<int64_t>((by + 1) * edge, d.n_voxel[1]) - 1.0 + 1.5)};
+                for (int64_t a = 0; a < na; ++a) {
+                    const double cs = std::cos(g->angles[(size_t)a]), sn = std::sin(g->angles[(size_t)a]);
+                    double lo = 1e300, hi = -1e300;
+                    bool ok = true;
+                    for (double X : xs)
+                        for (double Y : ys) {
+                            const double depth = d.DSO - (X * cs + Y * sn);
+                            if (!(depth > 0.0)) ok = false;
+                            const double u = (-X * sn + Y * cs) * d.DSD / depth;
+                            lo = std::min(lo, u);
+                            hi = std::max(hi, u);
+                        }
+                    int plo = 0, phi = nu - 1;
+                    if (ok) {
+                        plo = (int)std::max(0.0, std::floor((lo - u0) / d.d_det[0]) - 2.0);
+                        phi = (int)std::min((double)(nu - 1), std::ceil((hi - u0) / d.d_det[0]) + 2.0);
+                    }
+                    h[(size_t)((by * nbx + bx) * na + a)] = make_int2(plo, phi);
+                }
+            }
+        TIGRE_TRY(g->brick_prange.ensure(bytes));
+        TIGRE_CUDA(cudaMemcpy(g->brick_prange.ptr, h.data(), bytes, cudaMemcpyHostToDevice));
+        g->brick_prange.tag = tag;
+    }
+    *out = (const int2*)g->brick_prange.ptr;
+    return TIGRE_OK;
+}
+
 // One axial slab of an out-of-core projection: pad[l] hold the slab's
 // zero-padded F32 layouts (planes of padded index plane0 .. for the
 // sub-volume description sd), quad[l] receive their quad volumes, and the
@@ -546,6 +693,8 @@ tigre_status forward_slab_impl(tigre_geometry* g, const tigre_geometry_desc& sd,
                                int cell_lo, int cell_hi, int plane0, cudaStream_t st)
 {
     const tigre_geometry_desc& d = g->desc;
+    if (g->projector != TIGRE_PROJ_INTERPOLATED)
+        return fail(TIGRE_ERR_UNSUPPORTED, "out-of-core projection is interpolated only");
     const FwdConst c = make_fwd_const(d);
     for (int l = 0; l < 2; ++l) {
         if (!pad[l]) continue;
@@ -568,16 +717,37 @@ tigre_status forward_slab_impl(tigre_geometry* g, const tigre_geometry_desc& sd,
         }
     }
     if (q_hi <= q_lo) return TIGRE_OK;
-    const SlabRange sr{cell_lo, cell_hi, plane0, q_lo};
+    // x-y bricks of at most brick^2 voxels: the rays resident at one time
+    // then read one brick's planes, which stay in L2 (a quad plane of a
+    // 3072^2 slab alone is larger than L2).
+    const int64_t edge = g->brick;
+    const int64_t nbx = (d.n_voxel[0] + edge - 1) / edge;
+    const int64_t nby = (d.n_voxel[1] + edge - 1) / edge;
+    const int2* pr = nullptr;
+    if (nbx * nby > 1) TIGRE_TRY(brick_pixel_ranges(g, &pr));
+    const int64_t na_all = (int64_t)g->angles.size();
+    auto kern = g->fwd_path == 4 ? fwd_quad_kernel<float, float, true, true>
+                                 : fwd_quad_kernel<float, float, true, false>;
     ProfScope prof(kProfForward, st);
-    for (int64_t s = 0; s < na; s += 65535) {
-        const int64_t cnt = std::min<int64_t>(65535, na - s);
-        dim3 grid((unsigned)((c.nu + 31) / 32), (unsigned)cnt, (unsigned)((q_hi - q_lo + 7) / 8));
-        fwd_quad_kernel<float, float, true><<<grid, dim3(32, 8), 0, st>>>(
-            quad[0], quad[1], proj + s * (int64_t)c.nu * c.nv, (const FwdAngle*)g->fwd_params.ptr,
-            c, (int)(a0 + s), nullptr, sr);
-        TIGRE_LAUNCHED("fwd_quad_kernel(slab)");
-    }
+    for (int64_t by = 0; by < nby; ++by)
+        for (int64_t bx = 0; bx < nbx; ++bx) {
+            // first / last bricks own the cells of the zero border too
+            const int bx_lo = bx == 0 ? -1000000 : (int)(bx * edge + kPad);
+            const int bx_hi = bx == nbx - 1 ? 1000000 : (int)((bx + 1) * edge + kPad);
+            const int by_lo = by == 0 ? -1000000 : (int)(by * edge + kPad);
+            const int by_hi = by == nby - 1 ? 1000000 : (int)((by + 1) * edge + kPad);
+            const int2* brick_pr = pr ? pr + (by * nbx + bx) * na_all : nullptr;
+            const SlabRange sr{cell_lo, cell_hi, plane0, q_lo, bx_lo, bx_hi, by_lo, by_hi, brick_pr};
+            for (int64_t s = 0; s < na; s += 65535) {
+                const int64_t cnt = std::min<int64_t>(65535, na - s);
+                dim3 grid((unsigned)((c.nu + 31) / 32), (unsigned)cnt,
+                          (unsigned)((q_hi - q_lo + 7) / 8));
+                kern<<<grid, dim3(32, 8), 0, st>>>(
+                    quad[0], quad[1], proj + s * (int64_t)c.nu * c.nv,
+                    (const FwdAngle*)g->fwd_params.ptr, c, (int)(a0 + s), nullptr, sr);
+                TIGRE_LAUNCHED("fwd_quad_kernel(slab)");
+            }
+        }
     return TIGRE_OK;
 }
 
@@ -601,9 +771,16 @@ __global__ void __launch_bounds__(256) sample_count_kernel(const FwdAngle* __res
 
 }  // namespace tigre
 
+extern "C" tigre_status tigre_geometry_set_brick(tigre_geometry_t g, int64_t edge)
+{
+    if (!g || edge < 0) return tigre::fail(TIGRE_ERR_INVALID_ARG, "brick edge must be >= 0");
+    g->brick = edge == 0 ? tigre::kBrickDefault : edge;
+    return TIGRE_OK;
+}
+
 extern "C" tigre_status tigre_geometry_set_forward_path(tigre_geometry_t g, int path)
 {
-    if (!g || path < 0 || path > 3) return tigre::fail(TIGRE_ERR_INVALID_ARG, "path must be 0..3");
+    if (!g || path < 0 || path > 4) return tigre::fail(TIGRE_ERR_INVALID_ARG, "path must be 0..4");
     g->fwd_path = path;
     return TIGRE_OK;
 }

@@ -243,6 +243,7 @@ tigre_status tigre_geometry_destroy(tigre_geometry_t g)
     g->adj_xy.release();
     g->adj_yx.release();
     g->err_flag.release();
+    g->brick_prange.release();
     g->scratch_vol.release();
     g->scratch_red.release();
     delete g;

@@ -23,7 +23,10 @@
 // page-locked for the duration of the call (cudaHostRegister), the paper's
 // page-locking step (Alg. 1/2, "page-lock image memory").
 #include <algorithm>
+#include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <thread>
 
 #include "ray.cuh"
@@ -37,11 +40,14 @@ namespace {
 struct HostPin {
     void* ptr = nullptr;
     bool registered = false;
+    bool pinned = false;  // page-locked, by this object or already
     tigre_status pin(const void* p, size_t bytes)
     {
         cudaPointerAttributes at;
-        if (cudaPointerGetAttributes(&at, p) == cudaSuccess && at.type == cudaMemoryTypeHost)
-            return TIGRE_OK;  // already pinned
+        if (cudaPointerGetAttributes(&at, p) == cudaSuccess && at.type == cudaMemoryTypeHost) {
+            pinned = true;  // already page-locked
+            return TIGRE_OK;
+        }
         cudaGetLastError();
         cudaError_t e = cudaHostRegister(const_cast<void*>(p), bytes, cudaHostRegisterDefault);
         if (e != cudaSuccess) {
@@ -50,6 +56,7 @@ struct HostPin {
         }
         ptr = const_cast<void*>(p);
         registered = true;
+        pinned = true;
         return TIGRE_OK;
     }
     ~HostPin()
@@ -388,6 +395,28 @@ tigre_status set_dscalar(double* dst, double v, cudaStream_t st)
     return TIGRE_OK;
 }
 
+// Progress lines on stderr (pass, slab count, seconds since the call began)
+// when the environment variable TIGRE_PROGRESS is set; for runs long enough
+// that a caller wants to see where time goes before they finish.
+struct Progress {
+    bool on = std::getenv("TIGRE_PROGRESS") != nullptr;
+    std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+    void flag(const char* what, bool v)
+    {
+        if (!on) return;
+        std::fprintf(stderr, "tigre cgls(out-of-core): %s: %s\n", what, v ? "yes" : "no");
+        std::fflush(stderr);
+    }
+    void note(const char* what, int it)
+    {
+        if (!on) return;
+        const double s =
+            std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        std::fprintf(stderr, "tigre cgls(out-of-core): %s iteration %d done at %.1f s\n", what, it, s);
+        std::fflush(stderr);
+    }
+};
+
 constexpr int64_t kMaxSlabPlanes = 256;
 constexpr int kScalarSlots = 16;
 
@@ -645,9 +674,14 @@ static tigre_status cgls_streamed_direction(tigre_geometry* g, const float* b_ho
     };
 
     // p = A^T r (into the host buffer), gamma = ||p||^2, q = A p
+    Progress prog;
+    prog.flag("volume buffer page-locked", pin_x.pinned);
+    prog.flag("projection buffer page-locked", pin_b.pinned);
+    prog.note("setup", -1);
     TIGRE_CUDA(cudaMemsetAsync(q, 0, sizeof(float) * (size_t)m, st));
     double gamma = 0.0;
     TIGRE_TRY(sweep(kInit, &gamma));
+    prog.note("first direction (A^T r, A p)", -1);
     TIGRE_TRY(set_dscalar(gam, gamma, st));
     for (int it = 0; it < o->n_iter; ++it) {
         // alpha = gamma / ||q||^2: r -= alpha q here, x += alpha p in the sweep
@@ -659,13 +693,16 @@ static tigre_status cgls_streamed_direction(tigre_geometry* g, const float* b_ho
         }
         if (it == o->n_iter - 1) {
             TIGRE_TRY(sweep(kXOnly, nullptr));
+            prog.note("x update", it);
             break;
         }
         double gamma_new = 0.0;
         TIGRE_TRY(sweep(kNorm, &gamma_new));
+        prog.note("norm pass (A^T r)", it);
         TIGRE_TRY(set_dscalar(gnew, gamma_new, st));
         TIGRE_CUDA(cudaMemsetAsync(q, 0, sizeof(float) * (size_t)m, st));
         TIGRE_TRY(sweep(kUpdate, nullptr));
+        prog.note("update pass (A^T r, x, p, A p)", it);
         TIGRE_TRY(set_dscalar(gam, gamma_new, st));
     }
     TIGRE_CUDA(cudaMemcpyAsync(x_host, xd, sizeof(float) * (size_t)nvox, cudaMemcpyDeviceToHost, st));

@@ -22,6 +22,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import sys
 import time
 
 import torch
@@ -53,6 +54,11 @@ def host_available_bytes() -> int:
     return min(limits) if limits else 0
 
 
+def stage(msg: str) -> None:
+    """Progress line on stderr (kept when a long run is cut short)."""
+    print(f"[ooc_cgls_bench {time.strftime('%H:%M:%S')}] {msg}", file=sys.stderr, flush=True)
+
+
 def main(argv=None) -> dict:
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
     ap.add_argument("--workload", default=None, help="named workload (e.g. ooc_3072)")
@@ -66,6 +72,9 @@ def main(argv=None) -> dict:
     ap.add_argument("--host-margin", type=float, default=0.9,
                     help="fraction of available host memory the run may take")
     ap.add_argument("--no-error", action="store_true", help="skip the error pass")
+    ap.add_argument("--brick", type=int, default=0,
+                    help="x-y brick edge of the slab projections (0 = default)")
+    ap.add_argument("--path", type=int, default=0, help="forward kernel path (0 = automatic)")
     ap.add_argument("--out", default=None, help="write the JSON result here too")
     a = ap.parse_args(argv)
 
@@ -91,8 +100,11 @@ def main(argv=None) -> dict:
     budget = int(a.budget_gb * (1 << 30))
     dev = torch.device("cuda")
     with T.Geometry(geo, ang) as G:
+        T.tigre_geometry_set_brick(G.handle, a.brick)
+        T.tigre_geometry_set_forward_path(G.handle, a.path)
         placement, slab = T.tigre_cgls_ooc_plan(G.handle, budget)
-        res.update(placement=placement, slab_planes=slab, device_budget_bytes=budget)
+        res.update(placement=placement, slab_planes=slab, device_budget_bytes=budget,
+                   brick=a.brick, path=a.path)
         free_b, total_b = torch.cuda.mem_get_info()
         res["device_bytes_total"] = int(total_b)
 
@@ -106,6 +118,7 @@ def main(argv=None) -> dict:
             x[z0:z1].copy_(synth.voxelize_torch(ells, (nx, ny, nz), geo["d_voxel"], (z0, z1), dev))
         torch.cuda.synchronize()
         res["t_phantom_s"] = time.perf_counter() - t0
+        stage(f"phantom {res['t_phantom_s']:.1f} s; placement {placement}, slab {slab}")
 
         # 2. b = A x_true, streamed from host memory (Alg. 1)
         torch.cuda.empty_cache()
@@ -118,6 +131,7 @@ def main(argv=None) -> dict:
         res["t_forward_ooc_s"] = time.perf_counter() - t0
         res["forward_ooc_kernel_s"] = T.tigre_profile_read(T.PROF_FORWARD)[1] / 1e3
         res["forward_ooc_gvox_ang_per_s"] = nvox * na / res["t_forward_ooc_s"] / 1e9
+        stage(f"b = A x_true out of core: {res['t_forward_ooc_s']:.1f} s")
         b = torch.empty((na, nv, nu), dtype=torch.float32)
         b.copy_(bd)
         del bd
@@ -137,6 +151,7 @@ def main(argv=None) -> dict:
         res["cgls_backproject_kernel_s"] = T.tigre_profile_read(T.PROF_BACKPROJECT)[1] / 1e3
         T.tigre_profile_enable(False)
         res["residual_history"] = [float(v) for v in hist]
+        stage(f"cgls {a.iters} iterations: {res['t_cgls_s']:.1f} s")
 
         # 4. relative error against the phantom
         if not a.no_error:

@@ -12,6 +12,8 @@ from __future__ import annotations
 
 import argparse
 import json
+import os
+import tempfile
 
 import numpy as np
 import torch
@@ -19,10 +21,22 @@ import torch
 from . import synth, tigre
 
 
+def cached_phantom(n: int) -> np.ndarray:
+    """The 50-ellipsoid phantom, kept in the temp directory between runs (its
+    numpy voxelisation takes seconds at 512^3)."""
+    path = os.path.join(tempfile.gettempdir(), f"tigre103_ellipsoids50_{n}.npy")
+    if os.path.exists(path):
+        return np.load(path)
+    vol = synth.phantom("ellipsoids50", n, 256.0 / n)
+    np.save(path + ".tmp.npy", vol)
+    os.replace(path + ".tmp.npy", path)
+    return vol
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--op", choices=["forward", "backward", "adjoint", "tv", "forward_ooc",
-                                     "backward_ooc"], default="forward")
+                                     "backward_ooc", "fdk", "rof"], default="forward")
     ap.add_argument("--slab", type=int, default=0, help="out-of-core slab planes (0 = auto)")
     ap.add_argument("--weight", choices=["matched", "fdk"], default="matched")
     ap.add_argument("--n", type=int, default=512)
@@ -30,15 +44,18 @@ def main():
     ap.add_argument("--dtype", choices=["f32", "bf16", "f16"], default="f32")
     ap.add_argument("--repeat", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=1)
-    ap.add_argument("--path", choices=["auto", "l1", "tma", "quad"], default="auto",
+    ap.add_argument("--path", choices=["auto", "l1", "tma", "quad", "pair"], default="auto",
                     help="forward-projector kernel")
+    ap.add_argument("--projector", choices=["interpolated", "siddon"], default="interpolated")
     a = ap.parse_args()
     dt = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}[a.dtype]
     geo = synth.cube_geometry(a.n, a.n)
     ang = synth.angles(a.angles)
     G = tigre.Geometry(geo, ang)
-    tigre.tigre_geometry_set_forward_path(G.handle, {"auto": 0, "l1": 1, "tma": 2, "quad": 3}[a.path])
-    vol = torch.from_numpy(synth.phantom("ellipsoids50", a.n, 256.0 / a.n)).cuda().to(dt)
+    tigre.tigre_geometry_set_forward_path(G.handle, {"auto": 0, "l1": 1, "tma": 2, "quad": 3,
+                                                     "pair": 4}[a.path])
+    tigre.tigre_geometry_set_projector(G.handle, a.projector)
+    vol = torch.from_numpy(cached_phantom(a.n)).cuda().to(dt)
     proj = torch.empty(G.proj_shape, device="cuda", dtype=dt)
     out = torch.empty(G.vol_shape, device="cuda", dtype=dt)
     if a.op in ("backward", "adjoint", "backward_ooc"):
@@ -58,6 +75,13 @@ def main():
         fn = lambda: G.backward(proj, out=out, weight=a.weight)  # noqa: E731
     elif a.op == "adjoint":
         fn = lambda: G.backward(proj, out=out, weight="adjoint")  # noqa: E731
+    elif a.op == "fdk":
+        G.forward(vol, out=proj)
+        fn = lambda: G.fdk(proj, out=out)  # noqa: E731
+    elif a.op == "rof":
+        volf = vol.float()
+        out = torch.empty_like(volf)
+        fn = lambda: tigre.tigre_rof_denoise(volf, 20.0, 10, out=out)  # noqa: E731
     else:
         fn = lambda: tigre.tigre_tv_step(vol, 1, 0.002, 1e-8)  # noqa: E731
     for _ in range(a.warmup):
@@ -72,7 +96,7 @@ def main():
     ms = e0.elapsed_time(e1) / max(a.repeat, 1)
     va = float(a.n) ** 3 * a.angles
     print(json.dumps({"op": a.op, "weight": a.weight, "n": a.n, "angles": a.angles,
-                      "dtype": a.dtype, "path": a.path, "ms": ms, "gvox_ang_s": va / ms / 1e6,
+                      "dtype": a.dtype, "path": a.path, "projector": a.projector, "ms": ms, "gvox_ang_s": va / ms / 1e6,
                       "error_flags": tigre.tigre_geometry_error_flags(G.handle),
                       "checksum": float(out.float().sum() if a.op != "forward" else
                                         proj.float().sum())}))

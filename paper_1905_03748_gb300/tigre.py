@@ -36,6 +36,8 @@ EXPORTED = ["tigre_geometry_create", "tigre_geometry_destroy", "tigre_forward", 
             "tigre_cgls", "tigre_cgls_begin", "tigre_cgls_iterate", "tigre_cgls_history",
             "tigre_cgls_end", "tigre_forward_samples", "tigre_forward_ooc", "tigre_backward_ooc",
             "tigre_cgls_ooc_plan", "tigre_geometry_set_forward_path",
+            "tigre_geometry_set_projector", "tigre_fdk", "tigre_rof_denoise",
+            "tigre_geometry_set_brick",
             "tigre_geometry_error_flags", "tigre_profile_enable",
             "tigre_profile_read", "tigre_launch_count", "tigre_last_error"]
 
@@ -84,6 +86,10 @@ _sigs = {
     "tigre_backward_ooc": [_P, _P, ctypes.c_int, _P, _I64, _I64, ctypes.c_int, _I64, _I64, _P],
     "tigre_cgls_ooc_plan": [_P, _I64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_I64)],
     "tigre_geometry_set_forward_path": [_P, ctypes.c_int],
+    "tigre_geometry_set_projector": [_P, ctypes.c_int],
+    "tigre_geometry_set_brick": [_P, _I64],
+    "tigre_fdk": [_P, _P, ctypes.c_int, _P, ctypes.c_int, _P],
+    "tigre_rof_denoise": [_P, _P, _P, ctypes.c_double, ctypes.c_int, _P],
     "tigre_geometry_error_flags": [_P, ctypes.POINTER(ctypes.c_int), ctypes.c_int],
     "tigre_profile_enable": [ctypes.c_int],
     "tigre_profile_read": [ctypes.c_int, ctypes.POINTER(_I64), ctypes.POINTER(ctypes.c_double)],
@@ -351,7 +357,45 @@ def tigre_backward_ooc(handle, proj: torch.Tensor, vol_host: torch.Tensor, angle
                                    int(angle_chunk), _stream(stream)))
 
 
-FWD_AUTO, FWD_L1, FWD_TMA, FWD_QUAD = 0, 1, 2, 3
+FWD_AUTO, FWD_L1, FWD_TMA, FWD_QUAD, FWD_QUAD_PAIR = 0, 1, 2, 3, 4
+
+
+def tigre_fdk(handle, proj: torch.Tensor, vol: torch.Tensor, stream=None) -> None:
+    """FDK reconstruction of all the handle's angles into vol (device)."""
+    pp, pt = _dev(proj, "proj")
+    vp, vt = _dev(vol, "vol")
+    _check(_lib.tigre_fdk(handle, pp, pt, vp, vt, _stream(stream)))
+
+
+def tigre_rof_denoise(f: torch.Tensor, lam: float, n_iter: int, out: torch.Tensor = None,
+                      stream=None) -> torch.Tensor:
+    """ROF-model TV minimisation of a device F32 volume (out may be f)."""
+    fp, ft = _dev(f, "f")
+    if ft != TIGRE_F32:
+        raise TypeError("f must be float32")
+    if out is None:
+        out = torch.empty_like(f)
+    op, ot = _dev(out, "out")
+    if ot != TIGRE_F32 or out.shape != f.shape:
+        raise TypeError("out must be a float32 tensor of f's shape")
+    n = (ctypes.c_int64 * 3)(f.shape[2], f.shape[1], f.shape[0])
+    _check(_lib.tigre_rof_denoise(n, fp, op, float(lam), int(n_iter), _stream(stream)))
+    return out
+
+
+PROJ_INTERPOLATED, PROJ_SIDDON = 0, 1
+
+
+def tigre_geometry_set_projector(handle, projector) -> None:
+    """'interpolated' (default) or 'siddon' (or the PROJ_* value)."""
+    if isinstance(projector, str):
+        projector = {"interpolated": PROJ_INTERPOLATED, "siddon": PROJ_SIDDON}[projector]
+    _check(_lib.tigre_geometry_set_projector(handle, int(projector)))
+
+
+def tigre_geometry_set_brick(handle, edge: int) -> None:
+    """x-y brick edge (voxels) of out-of-core slab projections; 0 = default."""
+    _check(_lib.tigre_geometry_set_brick(handle, int(edge)))
 
 
 def tigre_geometry_set_forward_path(handle, path: int) -> None:
@@ -416,6 +460,12 @@ class Geometry:
             out = torch.empty((na,) + self.proj_shape[1:], device=vol.device,
                               dtype=dtype or vol.dtype)
         tigre_forward(self.handle, vol, out, angle_begin, na, stream)
+        return out
+
+    def fdk(self, proj, out=None, dtype=None, stream=None):
+        if out is None:
+            out = torch.empty(self.vol_shape, device=proj.device, dtype=dtype or proj.dtype)
+        tigre_fdk(self.handle, proj, out, stream)
         return out
 
     def backward(self, proj, out=None, angle_begin=0, weight="matched", dtype=None, stream=None):

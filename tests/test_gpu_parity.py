@@ -223,19 +223,21 @@ def test_cgls_host_resident_equals_device(tigre):
 
 # ----------------------------------------------- forward kernel paths
 
-@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16, torch.float16])
 def test_forward_paths_are_bitwise_identical(tigre, case, dtype):
-    """The scalar and quad L1 gather kernels and the shared-memory slab kernel
-    add the same samples in the same order: identical bits, no error flags."""
+    """The scalar and quad (one or two samples at a time) gather kernels and
+    the shared-memory slab kernel add the same samples in the same order:
+    identical bits, no error flags."""
     geo, ang, vol = case
     with tigre.Geometry(geo, ang) as G:
         v = torch.from_numpy(vol).cuda().to(dtype)
         out = {}
-        for path in (tigre.FWD_L1, tigre.FWD_TMA, tigre.FWD_QUAD, tigre.FWD_AUTO):
+        for path in (tigre.FWD_L1, tigre.FWD_TMA, tigre.FWD_QUAD, tigre.FWD_QUAD_PAIR,
+                     tigre.FWD_AUTO):
             tigre.tigre_geometry_set_forward_path(G.handle, path)
             out[path] = G.forward(v, dtype=torch.float32)
         assert tigre.tigre_geometry_error_flags(G.handle) == 0
-    for path in (tigre.FWD_TMA, tigre.FWD_QUAD, tigre.FWD_AUTO):
+    for path in (tigre.FWD_TMA, tigre.FWD_QUAD, tigre.FWD_QUAD_PAIR, tigre.FWD_AUTO):
         assert torch.isfinite(out[path]).all()
         assert torch.equal(out[tigre.FWD_L1], out[path]), path
 
