@@ -11,6 +11,8 @@ Operators (``oracle.c``, plain C, FP64, OpenMP over independent rays/voxels):
     siddon_forward, siddon_forward_rays, siddon_adjoint
                                    ray-voxel intersection (Siddon) projector
     tv_value, tv_grad, tv_steps    gradient-descent TV (Sec. 2.3)
+    tv_steps_split (this file)     the same steps on z-slabs with halo buffers and
+                                   the per-slab norm approximation (Sec. 2.3)
     rof_denoise (this file)        ROF-model TV minimisation (Sec. 2.3), first-order
                                    primal-dual iteration
     ramp_kernel, fdk               FDK: cosine weights, Ram-Lak ramp filter
@@ -313,6 +315,40 @@ def tv_steps(vol, n_steps: int, alpha: float, eps: float) -> np.ndarray:
 
 
 # ------------------------------------------------------------------- solvers
+
+def tv_steps_split(vol, n_steps: int, alpha: float, eps: float, slab: int, depth: int,
+                   halo: int = None) -> np.ndarray:
+    """Gradient-descent TV on z-slabs, the paper's splitting of a regulariser
+    (Sec. 2.3): in rounds of k = min(depth, steps left) steps, every slab takes
+    its k steps on its own, from the previous round's values, with k planes of
+    those values on each side as a buffer (a buffer as deep as the number of
+    independent steps); the norm of the update is approximated from the
+    slab's own voxels as if uniformly distributed over the volume,
+    ||g|| ~ ||g_slab|| sqrt(N / N_slab); the slab's own planes are then
+    written back.  halo overrides the buffer depth (for tests)."""
+    f = _f64(vol).copy()
+    nz = f.shape[0]
+    N = f.size
+    plane = f.shape[1] * f.shape[2]
+    done = 0
+    while done < n_steps:
+        k = min(depth, n_steps - done)
+        h = k if halo is None else halo
+        old = f.copy()
+        for z0 in range(0, nz, slab):
+            z1 = min(nz, z0 + slab)
+            lo, hi = max(0, z0 - h), min(nz, z1 + h)
+            sub = old[lo:hi].copy()
+            scale = np.sqrt(N / ((z1 - z0) * plane))
+            for _ in range(k):
+                g = tv_grad(sub, eps)
+                nrm = np.sqrt(np.sum(g[z0 - lo:z1 - lo] ** 2)) * scale
+                if nrm > 0:
+                    sub = sub - alpha * g / nrm
+            f[z0:z1] = sub[z0 - lo:z1 - lo]
+        done += k
+    return f
+
 
 def rof_grad(u):
     """Forward differences along x, y, z of u (nz, ny, nx); zero at the last

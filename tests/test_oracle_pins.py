@@ -590,3 +590,38 @@ def test_rof_converged_point_is_a_minimum():
     for _ in range(20):
         d = rng.standard_normal(f.shape)
         assert oracle.rof_objective(u + 1e-3 * d, f, lam) >= J - 1e-9
+
+
+# ------------------------------------------------ split TV (halo buffers)
+
+def test_split_tv_with_one_slab_is_the_global_descent():
+    f = np.random.default_rng(18).random((9, 7, 8))
+    np.testing.assert_allclose(oracle.tv_steps_split(f, 5, 0.02, 1e-8, slab=9, depth=2),
+                               oracle.tv_steps(f, 5, 0.02, 1e-8), rtol=1e-12, atol=1e-14)
+
+
+def test_split_tv_single_step_moves_each_slab_along_the_exact_gradient():
+    """One step: inside each slab the update is the exact gradient there
+    (the one-plane buffer covers the stencil), scaled to length
+    alpha sqrt(N_slab / N) (the uniform-distribution norm approximation)."""
+    f = np.random.default_rng(19).random((10, 6, 7))
+    alpha = 0.05
+    out = oracle.tv_steps_split(f, 1, alpha, 1e-8, slab=3, depth=1)
+    g = oracle.tv_grad(f, 1e-8)
+    N = f.size
+    for z0 in range(0, 10, 3):
+        z1 = min(10, z0 + 3)
+        gi = g[z0:z1]
+        want = f[z0:z1] - alpha * np.sqrt(gi.size / N) * gi / np.linalg.norm(gi)
+        np.testing.assert_allclose(out[z0:z1], want, rtol=1e-12, atol=1e-14)
+
+
+def test_split_tv_buffer_as_deep_as_the_steps_is_enough():
+    """k independent steps need a k-plane buffer: a deeper buffer (the whole
+    volume) gives the same slab interiors; a shallower one does not."""
+    f = np.random.default_rng(20).random((12, 5, 6))
+    a = oracle.tv_steps_split(f, 3, 0.03, 1e-8, slab=4, depth=3)
+    b = oracle.tv_steps_split(f, 3, 0.03, 1e-8, slab=4, depth=3, halo=12)
+    c = oracle.tv_steps_split(f, 3, 0.03, 1e-8, slab=4, depth=3, halo=1)
+    np.testing.assert_allclose(a, b, rtol=1e-12, atol=1e-14)
+    assert np.abs(a - c).max() > 1e-6
