@@ -253,6 +253,22 @@ TIGRE_API tigre_status tigre_cgls_iterate(tigre_cgls_t state, int n_iter);
 TIGRE_API tigre_status tigre_cgls_history(tigre_cgls_t state, double* resid_hist, int n);
 TIGRE_API tigre_status tigre_cgls_end(tigre_cgls_t state);
 
+/* Out-of-core gradient-descent TV (Sec. 2.3's splitting of a regulariser,
+ * on one GPU): vol_host is a HOST F32 volume (nz, ny, nx), updated in place.
+ * In rounds of k = min(halo_depth, steps left) steps, each axial slab of
+ * slab_planes planes (0 = the whole volume) is copied to the device with k
+ * planes of buffer on each side holding the previous round's values, takes k
+ * steps x <- x - alpha g/||g|| on its own, and writes its own planes back.
+ * The buffer keeps each slab's interior exact for the k steps; ||g|| is
+ * approximated from the slab's own voxels as if uniformly distributed over
+ * the volume, ||g_slab|| sqrt(N / N_slab), as the paper does instead of a
+ * synchronisation per step.  With one slab this is tigre_tv_step.  Needs
+ * 1 <= halo_depth <= slab_planes (unless one slab).  Pageable memory is
+ * page-locked for the call.  Synchronous. */
+TIGRE_API tigre_status tigre_tv_step_ooc(const int64_t n_voxel[3], float* vol_host, int n_steps,
+                                         double alpha, double eps, int64_t slab_planes,
+                                         int64_t halo_depth, void* cuda_stream);
+
 /* ROF-model TV minimisation (Sec. 2.3, the second TV minimiser the paper
  * uses): u = argmin ||grad u||_(2,1) + lambda/2 ||u - f||^2 (isotropic TV,
  * forward differences, zero at the last index of each axis), by n_iter steps

@@ -211,6 +211,11 @@ tigre_status backward_impl(tigre_geometry* g, const void* proj, tigre_dtype pt, 
 tigre_status tv_impl(const int64_t n[3], void* vol, tigre_dtype t, int n_steps, double alpha,
                      double eps, const double* d_alpha_scale, void* scratch_g,
                      double* d_red, cudaStream_t st);
+// Same, with ||g|| summed over the planes [k_lo, k_hi) only (all planes are
+// updated): the out-of-core split's per-slab norm.
+tigre_status tv_impl_region(const int64_t n[3], void* vol, tigre_dtype t, int n_steps,
+                            double alpha, double eps, const double* d_alpha_scale,
+                            void* scratch_g, double* d_red, int k_lo, int k_hi, cudaStream_t st);
 
 // ------------------------------------------------------------ vector ops
 // All reductions are deterministic: a fixed grid writes per-block FP64

@@ -734,3 +734,83 @@ extern "C" tigre_status tigre_cgls_ooc_plan(tigre_geometry_t geo, int64_t device
     *slab_planes = plan.slab;
     return TIGRE_OK;
 }
+
+// ------------------------------------------------ out-of-core TV (halo buffers)
+//
+// The paper's splitting of a regulariser (Sec. 2.3) on one GPU whose volume
+// lives in host memory: in rounds of k = min(depth, steps left) steps, each
+// z-slab is copied to the device with k planes of buffer on each side (the
+// previous round's values: the slab below has already been written back,
+// so its old top planes are kept aside first), takes its k steps on its own,
+// and writes its own planes back.  A buffer as deep as the number of
+// independent steps keeps the slab's interior exact; the norm of the update
+// is approximated from the slab's own voxels as if uniformly distributed over
+// the volume, ||g|| ~ ||g_slab|| sqrt(N / N_slab).
+
+namespace tigre {
+
+tigre_status tv_ooc_impl(const int64_t n[3], float* vol_host, int n_steps, double alpha,
+                         double eps, int64_t slab, int64_t depth, cudaStream_t st)
+{
+    if (!n || !vol_host) return fail(TIGRE_ERR_INVALID_ARG, "null n_voxel or vol");
+    for (int a = 0; a < 3; ++a)
+        if (n[a] <= 0 || n[a] > (1 << 20)) return fail(TIGRE_ERR_INVALID_ARG, "n_voxel out of range");
+    if (n_steps < 0 || !std::isfinite(alpha) || !std::isfinite(eps) || eps < 0.0)
+        return fail(TIGRE_ERR_INVALID_ARG, "need n_steps >= 0, finite alpha, eps >= 0");
+    if (depth < 1) return fail(TIGRE_ERR_INVALID_ARG, "halo depth must be >= 1");
+    const int64_t nz = n[2], plane = n[0] * n[1], N = plane * nz;
+    if (slab <= 0) slab = nz;
+    slab = std::min(slab, nz);
+    if (depth > slab && slab < nz)
+        return fail(TIGRE_ERR_INVALID_ARG, "halo depth must not exceed the slab thickness");
+    if (n_steps == 0) return TIGRE_OK;
+    const int64_t sub_planes = std::min(nz, slab + 2 * depth);
+    if (plane * sub_planes > INT32_MAX) return fail(TIGRE_ERR_UNSUPPORTED, "slab too large");
+    HostPin pin;
+    TIGRE_TRY(pin.pin(vol_host, sizeof(float) * (size_t)N));
+    Bufs B;
+    float *dsub, *dg;
+    double* dred;
+    TIGRE_TRY(B.alloc(&dsub, (size_t)(plane * sub_planes)));
+    TIGRE_TRY(B.alloc(&dg, (size_t)(plane * sub_planes)));
+    TIGRE_TRY(B.alloc(&dred, (size_t)(kRedBlocks + 4)));
+    std::vector<float> saved((size_t)(plane * std::min(depth, nz)));
+    const size_t pb = sizeof(float) * (size_t)plane;
+    for (int done = 0; done < n_steps;) {
+        const int k = (int)std::min<int64_t>(depth, n_steps - done);
+        for (int64_t z0 = 0; z0 < nz; z0 += slab) {
+            const int64_t z1 = std::min(nz, z0 + slab);
+            const int64_t lo = std::min<int64_t>(k, z0), hi = std::min<int64_t>(k, nz - z1);
+            const int64_t own = z1 - z0, planes = lo + own + hi;
+            // buffer below: the previous slab's top planes as they were before
+            // its write-back; the slab and the buffer above are still old
+            if (lo > 0)
+                TIGRE_CUDA(cudaMemcpyAsync(dsub, saved.data() + (size_t)((k - lo) * plane), pb * lo,
+                                           cudaMemcpyHostToDevice, st));
+            TIGRE_CUDA(cudaMemcpyAsync(dsub + lo * plane, vol_host + z0 * plane, pb * (own + hi),
+                                       cudaMemcpyHostToDevice, st));
+            TIGRE_CUDA(cudaStreamSynchronize(st));
+            if (z1 < nz)  // keep this slab's old top k planes for the next slab
+                std::copy(vol_host + (z1 - k) * plane, vol_host + z1 * plane, saved.begin());
+            const int64_t sn[3] = {n[0], n[1], planes};
+            const double a = alpha * std::sqrt((double)(own * plane) / (double)N);
+            TIGRE_TRY(tv_impl_region(sn, dsub, TIGRE_F32, k, a, eps, nullptr, dg, dred, (int)lo,
+                                     (int)(lo + own), st));
+            TIGRE_CUDA(cudaMemcpyAsync(vol_host + z0 * plane, dsub + lo * plane, pb * own,
+                                       cudaMemcpyDeviceToHost, st));
+            TIGRE_CUDA(cudaStreamSynchronize(st));
+        }
+        done += k;
+    }
+    return TIGRE_OK;
+}
+
+}  // namespace tigre
+
+extern "C" tigre_status tigre_tv_step_ooc(const int64_t n_voxel[3], float* vol_host, int n_steps,
+                                          double alpha, double eps, int64_t slab_planes,
+                                          int64_t halo_depth, void* cuda_stream)
+{
+    return tigre::tv_ooc_impl(n_voxel, vol_host, n_steps, alpha, eps, slab_planes, halo_depth,
+                              (cudaStream_t)cuda_stream);
+}

@@ -29,7 +29,8 @@ template <typename T>
 __global__ void __launch_bounds__(kRedThreads) tv_grad_kernel(const T* __restrict__ f,
                                                               float* __restrict__ g, int nx,
                                                               int ny, int nz, float eps,
-                                                              double* __restrict__ partials)
+                                                              double* __restrict__ partials,
+                                                              int k_lo, int k_hi)
 {
     __shared__ double sh[kRedThreads];
     const int64_t sx = 1, sy = nx, sz = (int64_t)nx * ny;
@@ -67,7 +68,7 @@ __global__ void __launch_bounds__(kRedThreads) tv_grad_kernel(const T* __restric
                 gv -= az * rsqrtf(fmaf(ax, ax, fmaf(ay, ay, fmaf(az, az, eps))));
             }
             g[r * nx + i] = gv;
-            acc = fma((double)gv, (double)gv, acc);
+            if (k >= k_lo && k < k_hi) acc = fma((double)gv, (double)gv, acc);
         }
     }
     sh[threadIdx.x] = acc;
@@ -98,6 +99,14 @@ tigre_status tv_impl(const int64_t n[3], void* vol, tigre_dtype t, int n_steps, 
                      double eps, const double* d_alpha_scale, void* scratch_g, double* d_red,
                      cudaStream_t st)
 {
+    return tv_impl_region(n, vol, t, n_steps, alpha, eps, d_alpha_scale, scratch_g, d_red, 0,
+                          (int)n[2], st);
+}
+
+tigre_status tv_impl_region(const int64_t n[3], void* vol, tigre_dtype t, int n_steps,
+                            double alpha, double eps, const double* d_alpha_scale,
+                            void* scratch_g, double* d_red, int k_lo, int k_hi, cudaStream_t st)
+{
     const int64_t N = n[0] * n[1] * n[2];
     double* partials = d_red;
     double* norm = d_red + kRedBlocks;
@@ -107,7 +116,7 @@ tigre_status tv_impl(const int64_t n[3], void* vol, tigre_dtype t, int n_steps, 
         for (int s = 0; s < n_steps; ++s) {
             tv_grad_kernel<T><<<kRedBlocks, kRedThreads, 0, st>>>(
                 (const T*)vol, (float*)scratch_g, (int)n[0], (int)n[1], (int)n[2], (float)eps,
-                partials);
+                partials, k_lo, k_hi);
             TIGRE_LAUNCHED("tv_grad_kernel");
             TIGRE_TRY(reduce_partials(partials, norm, 1, st));
             const int64_t blocks = std::min<int64_t>((N + 255) / 256, 152 * 16);

@@ -37,7 +37,7 @@ EXPORTED = ["tigre_geometry_create", "tigre_geometry_destroy", "tigre_forward", 
             "tigre_cgls_end", "tigre_forward_samples", "tigre_forward_ooc", "tigre_backward_ooc",
             "tigre_cgls_ooc_plan", "tigre_geometry_set_forward_path",
             "tigre_geometry_set_projector", "tigre_fdk", "tigre_rof_denoise",
-            "tigre_geometry_set_brick",
+            "tigre_geometry_set_brick", "tigre_tv_step_ooc",
             "tigre_geometry_error_flags", "tigre_profile_enable",
             "tigre_profile_read", "tigre_launch_count", "tigre_last_error"]
 
@@ -88,6 +88,7 @@ _sigs = {
     "tigre_geometry_set_forward_path": [_P, ctypes.c_int],
     "tigre_geometry_set_projector": [_P, ctypes.c_int],
     "tigre_geometry_set_brick": [_P, _I64],
+    "tigre_tv_step_ooc": [_P, _P, ctypes.c_int, ctypes.c_double, ctypes.c_double, _I64, _I64, _P],
     "tigre_fdk": [_P, _P, ctypes.c_int, _P, ctypes.c_int, _P],
     "tigre_rof_denoise": [_P, _P, _P, ctypes.c_double, ctypes.c_int, _P],
     "tigre_geometry_error_flags": [_P, ctypes.POINTER(ctypes.c_int), ctypes.c_int],
@@ -381,6 +382,15 @@ def tigre_rof_denoise(f: torch.Tensor, lam: float, n_iter: int, out: torch.Tenso
     n = (ctypes.c_int64 * 3)(f.shape[2], f.shape[1], f.shape[0])
     _check(_lib.tigre_rof_denoise(n, fp, op, float(lam), int(n_iter), _stream(stream)))
     return out
+
+
+def tigre_tv_step_ooc(vol_host: torch.Tensor, n_steps: int, alpha: float, eps: float = 1e-8,
+                      slab_planes: int = 0, halo_depth: int = 1, stream=None) -> None:
+    """Out-of-core TV steps on a host F32 volume (in place): z-slabs with
+    halo buffers and the per-slab norm approximation."""
+    n = (ctypes.c_int64 * 3)(vol_host.shape[2], vol_host.shape[1], vol_host.shape[0])
+    _check(_lib.tigre_tv_step_ooc(n, _host_f32(vol_host, "vol_host"), int(n_steps), float(alpha),
+                                  float(eps), int(slab_planes), int(halo_depth), _stream(stream)))
 
 
 PROJ_INTERPOLATED, PROJ_SIDDON = 0, 1

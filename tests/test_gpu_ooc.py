@@ -186,3 +186,29 @@ def test_cgls_streamed_direction_short_runs(tigre, n_iter):
         assert not xh.any()
     else:
         assert rel(xh.numpy(), xd.cpu().numpy()) < 1e-5
+
+
+@pytest.mark.parametrize("slab,depth,steps", [(6, 2, 5), (4, 4, 4), (23, 3, 3), (1, 1, 2)])
+def test_tv_out_of_core_matches_split_oracle(tigre, slab, depth, steps):
+    """Split TV on a host volume: the same rounds, buffers and per-slab norms
+    as the oracle's split (short last slab, buffers at both ends)."""
+    vol = synth.random_volume((23, 29, 37), seed=22)
+    ref = oracle.tv_steps_split(vol, steps, 0.02, 1e-8, slab=slab, depth=depth)
+    h = torch.from_numpy(vol.copy())
+    tigre.tigre_tv_step_ooc(h, steps, 0.02, 1e-8, slab_planes=slab, halo_depth=depth)
+    assert rel(h.numpy(), ref) < 1e-5
+
+
+def test_tv_out_of_core_one_slab_is_the_in_core_step(tigre):
+    vol = synth.random_volume((11, 13, 17), seed=23)
+    d = torch.from_numpy(vol.copy()).cuda()
+    tigre.tigre_tv_step(d, 4, 0.03, 1e-8)
+    h = torch.from_numpy(vol.copy())
+    tigre.tigre_tv_step_ooc(h, 4, 0.03, 1e-8, slab_planes=0, halo_depth=2)
+    assert torch.equal(h, d.cpu())
+
+
+def test_tv_out_of_core_rejects_a_buffer_deeper_than_the_slab(tigre):
+    h = torch.zeros((8, 4, 4))
+    with pytest.raises(tigre.TigreError):
+        tigre.tigre_tv_step_ooc(h, 2, 0.1, slab_planes=2, halo_depth=3)
