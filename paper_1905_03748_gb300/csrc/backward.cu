@@ -56,8 +56,11 @@ __device__ __forceinline__ float ldp(const T* p)
 // projections (the normaliser V^-1 = A_w^T 1, from the same weights and
 // interpolation) and finish with vol += lambda * num / den (den > 1e-12),
 // clamped at zero when nonneg.
+// Occupancy: 5 blocks per SM (48 registers, no spills) measured 11 % faster
+// than the unconstrained 62-register build; 6 blocks (40 registers) gained
+// nothing more.  The SART form, with twice the accumulators, keeps 3.
 template <typename TP, typename TV, int NZ, int MODE, bool SART = false>
-__global__ void __launch_bounds__(256) bp_voxel_kernel(const TP* __restrict__ pp,
+__global__ void __launch_bounds__(256, SART ? 3 : 5) bp_voxel_kernel(const TP* __restrict__ pp,
                                                        TV* __restrict__ vol,
                                                        const BpAngle* __restrict__ params,
                                                        BpConst c, int a_first, int na,
