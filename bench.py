@@ -273,11 +273,13 @@ def run_ours(args):
     fp32_peak = 152 * 128 * 2 * sm_max_mhz * 1e6 / 1e12  # TFLOP/s, FMA = 2 flops
     achieved = samples * FLOPS_PER_SAMPLE / (fwd_avg / 1e3) / 1e12
     traffic = None
+    sol = None
     try:
         with open(TRAFFIC_FILE) as f:
             tr = json.load(f)
         if tr.get("source_hash") == source_hash():
             traffic = tr.get("dram_bytes_per_launch")
+            sol = tr.get("sol_16_angle_capture")
     except Exception:
         pass
 
@@ -297,7 +299,10 @@ def run_ours(args):
                         "per_unit": f"{FLOPS_PER_SAMPLE} FP32 flops per quadrature sample "
                                     f"x {samples} samples per launch",
                         "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock "
-                                       f"{sm_max_mhz:.0f} MHz (derived)"},
+                                       f"{sm_max_mhz:.0f} MHz (derived)",
+                        "binding_unit": "L1/TEX gathers (latency and throughput), not the "
+                                        "FP32 pipe and not DRAM",
+                        "binding_unit_sol_ncu": sol},
            "gpu_launches": launches, "clocks": clk.summary(),
            "paper_context": "CGLS 512^3, 15 it in 61 s (4.1 s/iter incl. host copies), "
                             "1x GTX 1080 Ti (Sec. 4); detector/angles not stated"}
