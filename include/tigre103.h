@@ -232,7 +232,14 @@ TIGRE_API tigre_status tigre_sart(tigre_geometry_t geo, const void* proj, void* 
                         const tigre_solver_opts* opts, double* resid_hist);
 
 /* CGLS with FP64 inner products computed on the device; x0 = vol on entry
- * (r0 = b - A x0).  resid_hist[k] = ||r|| after iteration k. */
+ * (r0 = b - A x0).  resid_hist[k] = ||r|| after iteration k.  proj, vol and
+ * the iterates are stored in opts->storage (F32, BF16 or F16): every ray and
+ * voxel sum and every vector update is computed in FP32 and rounded once to
+ * the storage type; inner products, norms and step lengths stay FP64 on the
+ * device.  Out-of-core (TIGRE_OUT_OF_CORE) stores F32 only.  F16 storage
+ * has a narrow range: A^T r and A p grow to ~||A||^2 ||b|| (about 1e6 for
+ * mm-unit ray sums of a 64^3 head), so the caller scales b (CGLS is linear
+ * in b) to keep them below 65504; BF16 has FP32's range. */
 TIGRE_API tigre_status tigre_cgls(tigre_geometry_t geo, const void* proj, void* vol,
                         const tigre_solver_opts* opts, double* resid_hist);
 

@@ -197,9 +197,10 @@ struct tigre_cgls_state {
     tigre_bp_weight bw = TIGRE_BP_MATCHED;
     cudaStream_t st = nullptr;
     int64_t nvox = 0, m = 0, na = 0;
-    const float* b = nullptr;
-    float* x = nullptr;
-    float *r = nullptr, *q = nullptr, *p = nullptr, *s = nullptr;
+    tigre_dtype dt = TIGRE_F32;  // storage of b, x and the iterates (FP32 arithmetic)
+    const void* b = nullptr;
+    void* x = nullptr;
+    void *r = nullptr, *q = nullptr, *p = nullptr, *s = nullptr;
     double* sc = nullptr;    // Scalars area
     double* hist = nullptr;  // residual norms, capacity hist_cap
     int* counter = nullptr;  // device: number of residuals recorded (graph-safe index)
@@ -238,10 +239,12 @@ tigre_status dalloc(T** out, size_t count, cudaStream_t st)
 
 tigre_status cgls_init(tigre_cgls_state* S, int hist_cap)
 {
-    TIGRE_TRY(dalloc(&S->r, (size_t)S->m, S->st));
-    TIGRE_TRY(dalloc(&S->q, (size_t)S->m, S->st));
-    TIGRE_TRY(dalloc(&S->p, (size_t)S->nvox, S->st));
-    TIGRE_TRY(dalloc(&S->s, (size_t)S->nvox, S->st));
+    // iterates in the storage type: allocate as 16-bit units (elements x size / 2)
+    const size_t u = dtype_size(S->dt) / 2;
+    TIGRE_TRY(dalloc((uint16_t**)&S->r, (size_t)S->m * u, S->st));
+    TIGRE_TRY(dalloc((uint16_t**)&S->q, (size_t)S->m * u, S->st));
+    TIGRE_TRY(dalloc((uint16_t**)&S->p, (size_t)S->nvox * u, S->st));
+    TIGRE_TRY(dalloc((uint16_t**)&S->s, (size_t)S->nvox * u, S->st));
     TIGRE_TRY(dalloc(&S->sc, Scalars::count(4), S->st));
     S->hist_cap = std::max(hist_cap, 16);
     TIGRE_TRY(dalloc(&S->hist, (size_t)S->hist_cap, S->st));
@@ -249,10 +252,11 @@ tigre_status cgls_init(tigre_cgls_state* S, int hist_cap)
     TIGRE_CUDA(cudaMemsetAsync(S->counter, 0, sizeof(int), S->st));
     Scalars sc{S->sc};
     // r = b - A x0; p = A^T r; gamma = ||p||^2
-    TIGRE_TRY(forward_impl(S->g, S->x, TIGRE_F32, S->q, TIGRE_F32, 0, S->na, S->st));
-    TIGRE_TRY(weighted_residual(S->b, S->q, nullptr, S->r, S->m, sc.partials(), sc.slot(3), S->st));
-    TIGRE_TRY(backward_impl(S->g, S->r, TIGRE_F32, S->p, TIGRE_F32, 0, S->na, S->bw, 0, S->st));
-    TIGRE_TRY(dot_f64(S->p, S->p, S->nvox, sc.partials(), sc.slot(0), S->st));
+    TIGRE_TRY(forward_impl(S->g, S->x, S->dt, S->q, S->dt, 0, S->na, S->st));
+    TIGRE_TRY(weighted_residual_dt(S->dt, S->b, S->q, nullptr, S->r, S->m, sc.partials(),
+                                   sc.slot(3), S->st));
+    TIGRE_TRY(backward_impl(S->g, S->r, S->dt, S->p, S->dt, 0, S->na, S->bw, 0, S->st));
+    TIGRE_TRY(dot_f64_dt(S->dt, S->p, S->p, S->nvox, sc.partials(), sc.slot(0), S->st));
     S->cur = 0;
     return TIGRE_OK;
 }
@@ -286,16 +290,17 @@ tigre_status cgls_step(tigre_cgls_state* S)
     double* qq = sc.slot(2);
     double* rr = sc.slot(3);
     const int c = S->cur;
-    TIGRE_TRY(forward_impl(S->g, S->p, TIGRE_F32, S->q, TIGRE_F32, 0, S->na, S->st));
-    TIGRE_TRY(dot_f64(S->q, S->q, S->m, sc.partials(), qq, S->st));
+    TIGRE_TRY(forward_impl(S->g, S->p, S->dt, S->q, S->dt, 0, S->na, S->st));
+    TIGRE_TRY(dot_f64_dt(S->dt, S->q, S->q, S->m, sc.partials(), qq, S->st));
     // alpha = gamma / ||q||^2: x += alpha p, r -= alpha q
-    TIGRE_TRY(axpy_ratio(S->x, S->p, S->nvox, gam[c], qq, 1.0f, S->st));
-    TIGRE_TRY(axpy_ratio_norm(S->r, S->q, S->m, gam[c], qq, -1.0f, sc.partials(), rr, S->st));
+    TIGRE_TRY(axpy_ratio_dt(S->dt, S->x, S->p, S->nvox, gam[c], qq, 1.0f, S->st));
+    TIGRE_TRY(axpy_ratio_norm_dt(S->dt, S->r, S->q, S->m, gam[c], qq, -1.0f, sc.partials(), rr,
+                                 S->st));
     TIGRE_TRY(record_dscalar(S->hist, S->hist_cap, S->counter, rr + 1, S->st));
-    TIGRE_TRY(backward_impl(S->g, S->r, TIGRE_F32, S->s, TIGRE_F32, 0, S->na, S->bw, 0, S->st));
-    TIGRE_TRY(dot_f64(S->s, S->s, S->nvox, sc.partials(), gam[1 - c], S->st));
+    TIGRE_TRY(backward_impl(S->g, S->r, S->dt, S->s, S->dt, 0, S->na, S->bw, 0, S->st));
+    TIGRE_TRY(dot_f64_dt(S->dt, S->s, S->s, S->nvox, sc.partials(), gam[1 - c], S->st));
     // p = s + (gamma_new / gamma) p
-    TIGRE_TRY(xpay_ratio(S->p, S->s, S->nvox, gam[1 - c], gam[c], S->st));
+    TIGRE_TRY(xpay_ratio_dt(S->dt, S->p, S->s, S->nvox, gam[1 - c], gam[c], S->st));
     S->cur = 1 - c;
     S->done += 1;
     return TIGRE_OK;
@@ -325,7 +330,7 @@ tigre_status cgls_capture(tigre_cgls_state* S, cudaGraphExec_t* out)
     return TIGRE_OK;
 }
 
-tigre_status cgls_begin_device(tigre_geometry* g, const float* b, float* x,
+tigre_status cgls_begin_device(tigre_geometry* g, const void* b, void* x,
                                const tigre_solver_opts* o, tigre_cgls_state** out)
 {
     tigre_cgls_state* S = new (std::nothrow) tigre_cgls_state();
@@ -338,6 +343,7 @@ tigre_status cgls_begin_device(tigre_geometry* g, const float* b, float* x,
     S->nvox = n_vox(g);
     S->na = (int64_t)g->angles.size();
     S->m = n_pix(g) * S->na;
+    S->dt = o->storage;
     S->b = b;
     S->x = x;
     tigre_status st = cgls_init(S, o->n_iter);
@@ -352,8 +358,7 @@ tigre_status cgls_begin_device(tigre_geometry* g, const float* b, float* x,
 tigre_status run_cgls(const Problem& P, double* h_hist)
 {
     tigre_cgls_state* S = nullptr;
-    if (P.dt != TIGRE_F32) return fail(TIGRE_ERR_UNSUPPORTED, "CGLS iterates are stored in F32");
-    TIGRE_TRY(cgls_begin_device(P.g, (const float*)P.b, (float*)P.x, P.o, &S));
+    TIGRE_TRY(cgls_begin_device(P.g, P.b, P.x, P.o, &S));
     tigre_status st = cgls_reserve(S, P.o->n_iter);
     for (int it = 0; it < P.o->n_iter && st == TIGRE_OK; ++it) st = cgls_step(S);
     if (st == TIGRE_OK) st = finish_history(S->hist, h_hist, P.o->n_iter, P.st);
@@ -408,9 +413,7 @@ tigre_status tigre_cgls_begin(tigre_geometry_t geo, const void* proj, void* vol,
     TIGRE_TRY(check_opts(geo, opts, proj, vol));
     if (opts->flags & TIGRE_HOST_RESIDENT)
         return fail(TIGRE_ERR_UNSUPPORTED, "stepwise CGLS takes device buffers");
-    if (opts->storage != TIGRE_F32)
-        return fail(TIGRE_ERR_UNSUPPORTED, "CGLS iterates are stored in F32");
-    return cgls_begin_device(geo, (const float*)proj, (float*)vol, opts, out);
+    return cgls_begin_device(geo, proj, vol, opts, out);
 }
 
 tigre_status tigre_cgls_iterate(tigre_cgls_t S, int n_iter)

@@ -24,8 +24,13 @@ __device__ __forceinline__ double block_sum(double v, double* sh)
     return r;
 }
 
-__global__ void __launch_bounds__(kRedThreads) dot_partials_kernel(const float* __restrict__ a,
-                                                                   const float* __restrict__ b,
+// The element-wise kernels below are templates on the storage type T of the
+// vectors (F32, BF16 or F16): values are widened to FP32 for the arithmetic,
+// sums are FP64, results are rounded once to T.  For T = float they are the
+// plain FP32 kernels.
+template <typename T>
+__global__ void __launch_bounds__(kRedThreads) dot_partials_kernel(const T* __restrict__ a,
+                                                                   const T* __restrict__ b,
                                                                    int64_t n,
                                                                    double* __restrict__ partials)
 {
@@ -33,7 +38,7 @@ __global__ void __launch_bounds__(kRedThreads) dot_partials_kernel(const float* 
     double acc = 0.0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
-        acc = fma((double)a[i], (double)b[i], acc);
+        acc = fma((double)to_f32<T>(a[i]), (double)to_f32<T>(b[i]), acc);
     const double s = block_sum(acc, sh);
     if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
@@ -62,7 +67,7 @@ tigre_status reduce_partials(const double* partials, double* out, int sqrt_out, 
 tigre_status dot_f64(const float* a, const float* b, int64_t n, double* d_partials, double* d_out,
                      cudaStream_t st)
 {
-    dot_partials_kernel<<<kRedBlocks, kRedThreads, 0, st>>>(a, b, n, d_partials);
+    dot_partials_kernel<float><<<kRedBlocks, kRedThreads, 0, st>>>(a, b, n, d_partials);
     TIGRE_LAUNCHED("dot_partials_kernel");
     return reduce_partials(d_partials, d_out, 0, st);
 }
@@ -76,18 +81,20 @@ __device__ __forceinline__ double dev_ratio(const double* num, const double* den
 }
 
 // y += sign * (num/den) * x
-__global__ void axpy_ratio_kernel(float* __restrict__ y, const float* __restrict__ x, int64_t n,
+template <typename T>
+__global__ void axpy_ratio_kernel(T* __restrict__ y, const T* __restrict__ x, int64_t n,
                                   const double* num, const double* den, float sign)
 {
     const float s = sign * (float)dev_ratio(num, den);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
-        y[i] = fmaf(s, x[i], y[i]);
+        y[i] = from_f32<T>(fmaf(s, to_f32<T>(x[i]), to_f32<T>(y[i])));
 }
 
 // y += sign * (num/den) * x, and per-block partial sums of y_new^2.
+template <typename T>
 __global__ void __launch_bounds__(kRedThreads) axpy_ratio_norm_kernel(
-    float* __restrict__ y, const float* __restrict__ x, int64_t n, const double* num,
+    T* __restrict__ y, const T* __restrict__ x, int64_t n, const double* num,
     const double* den, float sign, double* __restrict__ partials)
 {
     __shared__ double sh[kRedThreads];
@@ -95,22 +102,24 @@ __global__ void __launch_bounds__(kRedThreads) axpy_ratio_norm_kernel(
     double acc = 0.0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        const float v = fmaf(s, x[i], y[i]);
+        const T v = from_f32<T>(fmaf(s, to_f32<T>(x[i]), to_f32<T>(y[i])));
         y[i] = v;
-        acc = fma((double)v, (double)v, acc);
+        const double vd = (double)to_f32<T>(v);  // the norm of the stored vector
+        acc = fma(vd, vd, acc);
     }
     const double t = block_sum(acc, sh);
     if (threadIdx.x == 0) partials[blockIdx.x] = t;
 }
 
 // y = x + (num/den) * y
-__global__ void xpay_ratio_kernel(float* __restrict__ y, const float* __restrict__ x, int64_t n,
+template <typename T>
+__global__ void xpay_ratio_kernel(T* __restrict__ y, const T* __restrict__ x, int64_t n,
                                   const double* num, const double* den)
 {
     const float s = (float)dev_ratio(num, den);
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
-        y[i] = fmaf(s, y[i], x[i]);
+        y[i] = from_f32<T>(fmaf(s, to_f32<T>(y[i]), to_f32<T>(x[i])));
 }
 
 // r = W * (b - q), partial sums of (b - q)^2.
@@ -264,7 +273,7 @@ static inline unsigned ew_blocks(int64_t n)
 tigre_status axpy_ratio(float* y, const float* x, int64_t n, const double* num, const double* den,
                         float sign, cudaStream_t st)
 {
-    axpy_ratio_kernel<<<ew_blocks(n), 256, 0, st>>>(y, x, n, num, den, sign);
+    axpy_ratio_kernel<float><<<ew_blocks(n), 256, 0, st>>>(y, x, n, num, den, sign);
     TIGRE_LAUNCHED("axpy_ratio_kernel");
     return TIGRE_OK;
 }
@@ -273,7 +282,8 @@ tigre_status axpy_ratio_norm(float* y, const float* x, int64_t n, const double* 
                              const double* den, float sign, double* partials, double* out,
                              cudaStream_t st)
 {
-    axpy_ratio_norm_kernel<<<kRedBlocks, kRedThreads, 0, st>>>(y, x, n, num, den, sign, partials);
+    axpy_ratio_norm_kernel<float><<<kRedBlocks, kRedThreads, 0, st>>>(y, x, n, num, den, sign,
+                                                                      partials);
     TIGRE_LAUNCHED("axpy_ratio_norm_kernel");
     return reduce_partials(partials, out, 1, st);
 }
@@ -281,7 +291,7 @@ tigre_status axpy_ratio_norm(float* y, const float* x, int64_t n, const double* 
 tigre_status xpay_ratio(float* y, const float* x, int64_t n, const double* num, const double* den,
                         cudaStream_t st)
 {
-    xpay_ratio_kernel<<<ew_blocks(n), 256, 0, st>>>(y, x, n, num, den);
+    xpay_ratio_kernel<float><<<ew_blocks(n), 256, 0, st>>>(y, x, n, num, den);
     TIGRE_LAUNCHED("xpay_ratio_kernel");
     return TIGRE_OK;
 }
@@ -335,6 +345,53 @@ tigre_status scale_dscalar(double* dst, const double* src, double factor, cudaSt
     scale_dscalar_kernel<<<1, 1, 0, st>>>(dst, src, factor);
     TIGRE_LAUNCHED("scale_dscalar_kernel");
     return TIGRE_OK;
+}
+
+tigre_status dot_f64_dt(tigre_dtype t, const void* a, const void* b, int64_t n, double* d_partials,
+                        double* d_out, cudaStream_t st)
+{
+    return dispatch_dtype(t, [&](auto tag) -> tigre_status {
+        using T = decltype(tag);
+        dot_partials_kernel<T><<<kRedBlocks, kRedThreads, 0, st>>>((const T*)a, (const T*)b, n,
+                                                                   d_partials);
+        TIGRE_LAUNCHED("dot_partials_kernel");
+        return reduce_partials(d_partials, d_out, 0, st);
+    });
+}
+
+tigre_status axpy_ratio_dt(tigre_dtype t, void* y, const void* x, int64_t n, const double* num,
+                           const double* den, float sign, cudaStream_t st)
+{
+    return dispatch_dtype(t, [&](auto tag) -> tigre_status {
+        using T = decltype(tag);
+        axpy_ratio_kernel<T><<<ew_blocks(n), 256, 0, st>>>((T*)y, (const T*)x, n, num, den, sign);
+        TIGRE_LAUNCHED("axpy_ratio_kernel");
+        return TIGRE_OK;
+    });
+}
+
+tigre_status axpy_ratio_norm_dt(tigre_dtype t, void* y, const void* x, int64_t n,
+                                const double* num, const double* den, float sign,
+                                double* partials, double* out, cudaStream_t st)
+{
+    return dispatch_dtype(t, [&](auto tag) -> tigre_status {
+        using T = decltype(tag);
+        axpy_ratio_norm_kernel<T><<<kRedBlocks, kRedThreads, 0, st>>>(
+            (T*)y, (const T*)x, n, num, den, sign, partials);
+        TIGRE_LAUNCHED("axpy_ratio_norm_kernel");
+        return reduce_partials(partials, out, 1, st);
+    });
+}
+
+tigre_status xpay_ratio_dt(tigre_dtype t, void* y, const void* x, int64_t n, const double* num,
+                           const double* den, cudaStream_t st)
+{
+    return dispatch_dtype(t, [&](auto tag) -> tigre_status {
+        using T = decltype(tag);
+        xpay_ratio_kernel<T><<<ew_blocks(n), 256, 0, st>>>((T*)y, (const T*)x, n, num, den);
+        TIGRE_LAUNCHED("xpay_ratio_kernel");
+        return TIGRE_OK;
+    });
 }
 
 }  // namespace tigre

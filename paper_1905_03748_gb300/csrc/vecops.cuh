@@ -37,6 +37,18 @@ tigre_status record_dscalar(double* hist, int cap, int* counter, const double* v
 // mode 0: dst = src; 1: dst += src; 2: dst = sqrt(src)
 tigre_status combine_dscalar(double* dst, const double* src, int mode, cudaStream_t st);
 tigre_status fill_f32(float* p, float v, int64_t n, cudaStream_t st);
+// Storage-typed forms of dot_f64, axpy_ratio, axpy_ratio_norm, xpay_ratio
+// (vectors in dtype t, FP32 arithmetic, FP64 sums; the norm is that of the
+// stored, rounded vector).
+tigre_status dot_f64_dt(tigre_dtype t, const void* a, const void* b, int64_t n, double* d_partials,
+                        double* d_out, cudaStream_t st);
+tigre_status axpy_ratio_dt(tigre_dtype t, void* y, const void* x, int64_t n, const double* num,
+                           const double* den, float sign, cudaStream_t st);
+tigre_status axpy_ratio_norm_dt(tigre_dtype t, void* y, const void* x, int64_t n,
+                                const double* num, const double* den, float sign,
+                                double* partials, double* out, cudaStream_t st);
+tigre_status xpay_ratio_dt(tigre_dtype t, void* y, const void* x, int64_t n, const double* num,
+                           const double* den, cudaStream_t st);
 tigre_status scale_dscalar(double* dst, const double* src, double factor, cudaStream_t st);
 
 }  // namespace tigre

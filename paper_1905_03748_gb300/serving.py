@@ -32,7 +32,8 @@ class Request:
     rid: int
     geo: dict
     angles: np.ndarray
-    proj: torch.Tensor            # host (pinned preferred) projections, F32 or BF16
+    proj: torch.Tensor            # host (pinned preferred) projections, F32, BF16 or F16:
+                                  # the reconstruction stores its iterates in this type
     n_iter: int = 15
     arrival: float = 0.0          # seconds after the start of the run
 
@@ -40,7 +41,7 @@ class Request:
 @dataclass
 class Result:
     rid: int
-    x: torch.Tensor               # host F32 volume
+    x: torch.Tensor               # host F32 volume (widened from the storage type)
     resid: np.ndarray
     arrival: float
     admitted: float
@@ -51,17 +52,28 @@ class Result:
         return self.finished - self.arrival
 
 
-def footprint_bytes(geo: dict, n_angles: int) -> int:
-    """HBM needed by one resident CGLS reconstruction: x, p, s (volume-sized),
-    b, r, q (projection-sized), the forward projector's two padded layouts
-    and their quad copies (5 padded volumes each), the backprojector's padded
-    projections, plus 64 MiB of slack."""
+def footprint_bytes(geo: dict, n_angles: int, elem: int = 4) -> int:
+    """HBM needed by one resident CGLS reconstruction stored in elem-byte
+    values: x, p, s (volume-sized), b, r, q (projection-sized), the forward
+    projector's two padded layouts and their quad copies (5 padded volumes
+    each), the backprojector's padded projections, plus 64 MiB of slack."""
     nx, ny, nz = geo["n_voxel"]
     nu, nv = geo["n_det"]
-    vol = 4 * nx * ny * nz
-    padded = 4 * (nx + 4) * (ny + 4) * (nz + 4)
-    proj = 4 * nu * nv * n_angles
+    vol = elem * nx * ny * nz
+    padded = elem * (nx + 4) * (ny + 4) * (nz + 4)
+    proj = elem * nu * nv * n_angles
     return 3 * vol + 4 * proj + 10 * padded + (64 << 20)
+
+
+_STORAGE = (torch.float32, torch.bfloat16, torch.float16)
+
+
+def storage_dtype(req: Request) -> torch.dtype:
+    return req.proj.dtype if req.proj.dtype in _STORAGE else torch.float32
+
+
+def request_bytes(req: Request) -> int:
+    return footprint_bytes(req.geo, len(req.angles), storage_dtype(req).itemsize)
 
 
 def work_estimate(req: Request) -> float:
@@ -106,16 +118,16 @@ class Server:
         stream = torch.cuda.Stream(device=self.device)
         with torch.cuda.stream(stream):
             G = tigre.Geometry(req.geo, req.angles)
-            b = req.proj.to(self.device, non_blocking=True).float()
-            x = torch.zeros(G.vol_shape, device=self.device)
+            dt = storage_dtype(req)
+            b = req.proj.to(self.device, dtype=dt, non_blocking=True)
+            x = torch.zeros(G.vol_shape, device=self.device, dtype=dt)
             state = tigre.tigre_cgls_begin(G.handle, b, x, n_iter_hint=req.n_iter,
                                            stream=stream, graph=self.graph)
-        return _Slot(req, G, stream, b, x, state, 0, now,
-                     bytes=footprint_bytes(req.geo, len(req.angles)))
+        return _Slot(req, G, stream, b, x, state, 0, now, bytes=request_bytes(req))
 
     def _finish(self, s: _Slot, now: float) -> Result:
         resid = tigre.tigre_cgls_history(s.state, s.req.n_iter)  # syncs the slot's stream
-        x = s.x.cpu()
+        x = s.x.float().cpu()
         tigre.tigre_cgls_end(s.state)
         s.G.close()
         return Result(s.req.rid, x, resid, s.req.arrival, s.admitted, now)
@@ -138,7 +150,7 @@ class Server:
             if self.policy == "sjf":
                 queue.sort(key=lambda r: (work_estimate(r), r.arrival))
             while queue and len(active) < self.max_slots:
-                need = footprint_bytes(queue[0].geo, len(queue[0].angles))
+                need = request_bytes(queue[0])
                 if used + need > self.hbm_budget and active:
                     break
                 req = queue.pop(0)
@@ -182,10 +194,11 @@ def run_plain(requests: list[Request], realtime: bool = True,
             time.sleep(req.arrival - now)
         admitted = time.perf_counter() - t0
         with tigre.Geometry(req.geo, req.angles) as G:
-            b = req.proj.to(dev).float()
-            x = torch.zeros(G.vol_shape, device=dev)
+            dt = storage_dtype(req)
+            b = req.proj.to(dev, dtype=dt)
+            x = torch.zeros(G.vol_shape, device=dev, dtype=dt)
             resid = tigre.tigre_cgls(G.handle, b, x, req.n_iter)
-            xh = x.cpu()
+            xh = x.float().cpu()
         results.append(Result(req.rid, xh, resid, req.arrival, admitted,
                               time.perf_counter() - t0))
     return results

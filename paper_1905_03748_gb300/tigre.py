@@ -299,12 +299,16 @@ def tigre_cgls_ooc_plan(handle, device_budget_bytes: int = 0) -> tuple:
 def tigre_cgls_begin(handle, proj, vol, n_iter_hint=16, bp_weight="matched", stream=None,
                      graph=False):
     """Stepwise CGLS; graph=True replays captured iteration pairs as CUDA
-    graphs (needs a non-default stream)."""
+    graphs (needs a non-default stream).  proj and vol share one storage
+    dtype (float32, bfloat16 or float16); arithmetic is FP32, scalars FP64."""
     o = _opts(n_iter_hint, stream, bp_weight=bp_weight)
     if graph:
         o.flags |= TIGRE_GRAPH
-    pp, _ = _dev(proj, "proj")
-    vp, _ = _dev(vol, "vol")
+    pp, pt = _dev(proj, "proj")
+    vp, vt = _dev(vol, "vol")
+    if pt != vt:
+        raise TypeError("proj and vol must share one storage dtype")
+    o.storage = vt
     s = ctypes.c_void_p()
     _check(_lib.tigre_cgls_begin(handle, pp, vp, ctypes.byref(o), ctypes.byref(s)))
     return s

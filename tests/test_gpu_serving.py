@@ -25,22 +25,23 @@ def projections(tigre, geo, ang, vol):
         return G.forward(torch.from_numpy(vol).cuda()).cpu()
 
 
-def test_graph_replay_equals_eager_iterations(tigre):
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
+def test_graph_replay_equals_eager_iterations(tigre, dtype):
     rng = np.random.default_rng(0)
     geo, ang, vol = make_request(0, rng, n=32)
-    b = projections(tigre, geo, ang, vol).cuda()
+    b = projections(tigre, geo, ang, vol).cuda().to(dtype)
     out = {}
     for graph in (False, True):
         s = torch.cuda.Stream()
         with torch.cuda.stream(s), tigre.Geometry(geo, ang) as G:
-            x = torch.zeros(G.vol_shape, device="cuda")
+            x = torch.zeros(G.vol_shape, device="cuda", dtype=dtype)
             st = tigre.tigre_cgls_begin(G.handle, b, x, n_iter_hint=4, stream=s, graph=graph)
             tigre.tigre_cgls_iterate(st, 1)   # odd first: exercises both graph parities
             tigre.tigre_cgls_iterate(st, 6)
             h = tigre.tigre_cgls_history(st, 7)
             tigre.tigre_cgls_end(st)
             torch.cuda.synchronize()
-            out[graph] = (x.cpu(), h)
+            out[graph] = (x.float().cpu(), h)
     assert torch.equal(out[False][0], out[True][0])
     np.testing.assert_array_equal(out[False][1], out[True][1])
     assert np.all(np.diff(out[True][1]) < 0)
@@ -53,8 +54,11 @@ def test_each_request_same_alone_and_in_the_mix(tigre, budget_mb):
     reqs = []
     for i in range(6):
         geo, ang, vol = make_request(i, rng)
-        b = projections(tigre, geo, ang, vol).pin_memory()
-        reqs.append(serving.Request(i, geo, ang, b, n_iter=5 + (i % 3), arrival=0.002 * i))
+        b = projections(tigre, geo, ang, vol)
+        if i % 2:  # every other request is served with BF16 storage
+            b = b.to(torch.bfloat16)
+        reqs.append(serving.Request(i, geo, ang, b.pin_memory(), n_iter=5 + (i % 3),
+                                    arrival=0.002 * i))
     alone = {r.rid: r for r in serving.run_plain(reqs, realtime=False)}
     budget = None if budget_mb is None else budget_mb << 20
     server = serving.Server(max_slots=4, hbm_budget=budget, graph=True, iters_per_tick=2)
