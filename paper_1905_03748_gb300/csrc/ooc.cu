@@ -451,6 +451,15 @@ size_t placement1_workspace(const tigre_geometry* g, int64_t slab, const bool ne
     return std::max(fwd, bwd) + sizeof(double) * (size_t)(kRedBlocks + kScalarSlots);
 }
 
+// Slab thicknesses the backprojector fills without waste: it computes z in
+// chunks of 16 voxels per thread, so a slab of 100 planes costs 112.  Thin
+// slabs (under 16 planes) and the whole volume are always allowed.
+bool whole_chunks(int64_t slab, int64_t nz)
+{
+    constexpr int64_t kChunk = 16;
+    return slab < kChunk || slab % kChunk == 0 || slab >= nz;
+}
+
 // The placement and slab thickness for a device budget (0: the free device
 // memory less 1 GiB): placement 2 with the thickest slab (at most
 // kMaxSlabPlanes) that fits, else placement 1 likewise, else OOM.
@@ -468,13 +477,13 @@ tigre_status plan_ooc(const tigre_geometry* g, int64_t budget, OocPlan* out)
     const int64_t top = std::min(std::min(nz, kMaxSlabPlanes), max_slab_planes(g->desc));
     const int64_t base2 = (int64_t)sizeof(float) * (nvox + 2 * m);
     for (int64_t slab = top; slab >= 1; --slab)
-        if (base2 + (int64_t)placement2_workspace(g, slab, need) <= budget) {
+        if (whole_chunks(slab, nz) && base2 + (int64_t)placement2_workspace(g, slab, need) <= budget) {
             *out = OocPlan{2, slab};
             return TIGRE_OK;
         }
     const int64_t base1 = (int64_t)sizeof(float) * 3 * m;
     for (int64_t slab = top; slab >= 1; --slab)
-        if (base1 + (int64_t)placement1_workspace(g, slab, need) <= budget) {
+        if (whole_chunks(slab, nz) && base1 + (int64_t)placement1_workspace(g, slab, need) <= budget) {
             *out = OocPlan{1, slab};
             return TIGRE_OK;
         }
