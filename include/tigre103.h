@@ -53,6 +53,7 @@
 #ifndef TIGRE103_H
 #define TIGRE103_H
 
+#include <stddef.h>
 #include <stdint.h>
 
 #if defined(__GNUC__)
@@ -209,10 +210,31 @@ typedef struct {
     int nonneg;                 /* clamp x >= 0 after each update (SIRT/OS-SART) */
     tigre_dtype storage;        /* storage type of the iterates (default F32) */
     int64_t device_budget_bytes;/* 0 = free device memory; used by out-of-core */
-    int64_t timeout_ms;         /* host waits (default 0 = none) */
+    int64_t timeout_ms;         /* SIRT / OS-SART / in-core CGLS: the final wait for
+                                   the queued iterations is bounded by this many ms
+                                   (default 0 = none).  On expiry TIGRE_ERR_TIMEOUT:
+                                   the work completes on its stream (device buffers
+                                   become valid once it drains), resid_hist is not
+                                   filled and host-resident vol is not copied back. */
     uint32_t flags;             /* TIGRE_HOST_RESIDENT, TIGRE_GRAPH */
     void* cuda_stream;          /* stream for all work (NULL = default) */
 } tigre_solver_opts;
+
+/* Device workspace allocator.  alloc(bytes, cuda_stream, ctx) returns device
+ * memory usable on cuda_stream (NULL on failure: the call then returns
+ * TIGRE_ERR_OOM); free_fn(ptr, cuda_stream, ctx) releases it once the work
+ * already queued on cuda_stream is done.  cuda_stream is NULL for buffers
+ * cached in a geometry handle, which the library frees only after a device
+ * synchronisation.  Every workspace the library allocates afterwards goes
+ * through the pair (e.g. a framework's caching allocator); both NULL restores
+ * cudaMallocAsync / cudaFreeAsync (cudaMalloc / cudaFree for cached buffers).
+ * Process-wide; TIGRE_ERR_INVALID_ARG while any geometry handle or CGLS state
+ * is alive, so each buffer is freed by the allocator that made it.  The
+ * paper's implementation allocates its outputs on every call (Sec. 4 names
+ * this as a cost); here outputs are the caller's and only workspaces remain. */
+typedef void* (*tigre_alloc_fn)(size_t bytes, void* cuda_stream, void* ctx);
+typedef void (*tigre_free_fn)(void* ptr, void* cuda_stream, void* ctx);
+TIGRE_API tigre_status tigre_set_allocator(tigre_alloc_fn alloc, tigre_free_fn free_fn, void* ctx);
 
 /* Fill *opts with the defaults listed above. */
 TIGRE_API tigre_status tigre_solver_opts_default(tigre_solver_opts* opts);

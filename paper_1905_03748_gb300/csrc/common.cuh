@@ -87,6 +87,16 @@ tigre_status dispatch_dtype(tigre_dtype t, F&& f)
 
 // ---------------------------------------------------------- device buffers
 
+// Device workspace allocation (see tigre_set_allocator): stream-ordered
+// pairs, and pairs for buffers not tied to one stream.
+cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t st);
+void dev_free(void* p, cudaStream_t st);
+cudaError_t dev_alloc_sync(void** p, size_t bytes);
+void dev_free_sync(void* p);
+// Live geometry handles and CGLS states (the allocator may change only at 0).
+void handle_created();
+void handle_destroyed();
+
 // A grow-only device buffer owned by a geometry handle.
 struct DeviceBuffer {
     void* ptr = nullptr;

@@ -104,11 +104,11 @@ tigre_status fdk_impl(tigre_geometry* g, const void* proj, tigre_dtype pt, void*
     std::copy(aw.begin(), aw.end(), host.begin() + (nu / 2 + 1));
     float* dtab = nullptr;
     float* filt = nullptr;
-    TIGRE_CUDA(cudaMallocAsync((void**)&dtab, sizeof(float) * host.size(), st));
-    cudaError_t e = cudaMallocAsync((void**)&filt, sizeof(float) * (size_t)(na * nv) * (size_t)nu, st);
+    TIGRE_CUDA(dev_alloc((void**)&dtab, sizeof(float) * host.size(), st));
+    cudaError_t e = dev_alloc((void**)&filt, sizeof(float) * (size_t)(na * nv) * (size_t)nu, st);
     if (e != cudaSuccess) {
-        cudaFreeAsync(dtab, st);
-        return cuda_fail(e, "cudaMallocAsync(fdk filtered projections)");
+        dev_free(dtab, st);
+        return cuda_fail(e, "device allocation (fdk filtered projections)");
     }
     tigre_status status = TIGRE_OK;
     e = cudaMemcpyAsync(dtab, host.data(), sizeof(float) * host.size(), cudaMemcpyHostToDevice, st);
@@ -134,8 +134,8 @@ tigre_status fdk_impl(tigre_geometry* g, const void* proj, tigre_dtype pt, void*
     }
     if (status == TIGRE_OK)
         status = backward_impl(g, filt, TIGRE_F32, vol, vt, 0, na, TIGRE_BP_FDK, 0, st);
-    cudaFreeAsync(filt, st);
-    cudaFreeAsync(dtab, st);
+    dev_free(filt, st);
+    dev_free(dtab, st);
     return status;
 }
 

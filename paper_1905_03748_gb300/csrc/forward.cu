@@ -807,7 +807,7 @@ extern "C" tigre_status tigre_forward_samples(tigre_geometry_t g, int64_t angle_
     if (!samples) return fail(TIGRE_ERR_INVALID_ARG, "null output");
     const FwdConst c = make_fwd_const(g->desc);
     unsigned long long* d = nullptr;
-    TIGRE_CUDA(cudaMalloc(&d, sizeof(unsigned long long)));
+    TIGRE_CUDA(dev_alloc_sync((void**)&d, sizeof(unsigned long long)));
     tigre_status st = TIGRE_OK;
     cudaError_t e = cudaMemset(d, 0, sizeof(unsigned long long));
     for (int64_t s = 0; e == cudaSuccess && s < angle_count; s += 65535) {
@@ -821,7 +821,7 @@ extern "C" tigre_status tigre_forward_samples(tigre_geometry_t g, int64_t angle_
     unsigned long long h = 0;
     if (e == cudaSuccess) e = cudaMemcpy(&h, d, sizeof(h), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) st = cuda_fail(e, "tigre_forward_samples");
-    cudaFree(d);
+    dev_free_sync(d);
     *samples = (int64_t)h;
     return st;
 }

@@ -5,6 +5,8 @@
 // D = -(DSD - DSO)(cos t, sin t, 0), e_u = (-sin t, cos t, 0), e_v = z) and
 // rounded once to FP32 for the kernels.
 #include <algorithm>
+#include <atomic>
+#include <mutex>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -30,17 +32,75 @@ tigre_status cuda_fail(cudaError_t err, const char* what)
     return err == cudaErrorMemoryAllocation ? TIGRE_ERR_OOM : TIGRE_ERR_CUDA;
 }
 
+// ------------------------------------------------------ workspace allocator
+// Every device workspace the library allocates goes through dev_alloc /
+// dev_free (stream-ordered) or dev_alloc_sync / dev_free_sync (buffers not
+// tied to one stream).  By default they are cudaMallocAsync / cudaFreeAsync
+// and cudaMalloc / cudaFree; tigre_set_allocator installs a caller's pair
+// instead.  The pair may only change while no geometry handle or CGLS state
+// is alive, so every pointer is freed by the allocator that made it.
+static std::mutex g_alloc_mu;
+static tigre_alloc_fn g_alloc = nullptr;
+static tigre_free_fn g_free = nullptr;
+static void* g_alloc_ctx = nullptr;
+static std::atomic<int64_t> g_live_handles{0};
+
+void handle_created() { g_live_handles.fetch_add(1); }
+void handle_destroyed() { g_live_handles.fetch_sub(1); }
+
+cudaError_t dev_alloc(void** p, size_t bytes, cudaStream_t st)
+{
+    if (bytes == 0) bytes = 1;
+    if (g_alloc) {
+        *p = g_alloc(bytes, (void*)st, g_alloc_ctx);
+        return *p ? cudaSuccess : cudaErrorMemoryAllocation;
+    }
+    return cudaMallocAsync(p, bytes, st);
+}
+
+void dev_free(void* p, cudaStream_t st)
+{
+    if (!p) return;
+    if (g_free)
+        g_free(p, (void*)st, g_alloc_ctx);
+    else
+        cudaFreeAsync(p, st);
+}
+
+cudaError_t dev_alloc_sync(void** p, size_t bytes)
+{
+    if (bytes == 0) bytes = 1;
+    if (g_alloc) {
+        *p = g_alloc(bytes, nullptr, g_alloc_ctx);
+        return *p ? cudaSuccess : cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(p, bytes);
+}
+
+void dev_free_sync(void* p)
+{
+    if (!p) return;
+    if (g_free) {
+        // the buffer may be in use on any stream: let all work finish first
+        // (cudaFree does the same implicitly)
+        cudaDeviceSynchronize();
+        g_free(p, nullptr, g_alloc_ctx);
+    } else {
+        cudaFree(p);
+    }
+}
+
 tigre_status DeviceBuffer::ensure(size_t need)
 {
     if (need <= bytes && ptr) return TIGRE_OK;
     release();
     if (need == 0) return TIGRE_OK;
-    cudaError_t e = cudaMalloc(&ptr, need);
+    cudaError_t e = dev_alloc_sync(&ptr, need);
     if (e != cudaSuccess) {
         ptr = nullptr;
         bytes = 0;
         cudaGetLastError();
-        return cuda_fail(e, "cudaMalloc(workspace)");
+        return cuda_fail(e, "device allocation (workspace)");
     }
     bytes = need;
     return TIGRE_OK;
@@ -48,7 +108,7 @@ tigre_status DeviceBuffer::ensure(size_t need)
 
 void DeviceBuffer::release()
 {
-    if (ptr) cudaFree(ptr);
+    if (ptr) dev_free_sync(ptr);
     ptr = nullptr;
     bytes = 0;
     tag = 0;
@@ -212,6 +272,7 @@ tigre_status tigre_geometry_create(const tigre_geometry_desc* desc, const double
     TIGRE_TRY(validate(desc, angles, n_angles));
     tigre_geometry* g = new (std::nothrow) tigre_geometry();
     if (!g) return fail(TIGRE_ERR_OOM, "host allocation failed");
+    handle_created();
     g->desc = *desc;
     g->angles.assign(angles, angles + n_angles);
     cudaError_t e = cudaGetDevice(&g->device);
@@ -247,6 +308,21 @@ tigre_status tigre_geometry_destroy(tigre_geometry_t g)
     g->scratch_vol.release();
     g->scratch_red.release();
     delete g;
+    handle_destroyed();
+    return TIGRE_OK;
+}
+
+tigre_status tigre_set_allocator(tigre_alloc_fn alloc, tigre_free_fn free_fn, void* ctx)
+{
+    if ((alloc == nullptr) != (free_fn == nullptr))
+        return fail(TIGRE_ERR_INVALID_ARG, "give both alloc and free, or neither");
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    if (g_live_handles.load() != 0)
+        return fail(TIGRE_ERR_INVALID_ARG,
+                    "the allocator can only change while no geometry or CGLS handle is alive");
+    g_alloc = alloc;
+    g_free = free_fn;
+    g_alloc_ctx = alloc ? ctx : nullptr;
     return TIGRE_OK;
 }
 

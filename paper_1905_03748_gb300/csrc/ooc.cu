@@ -87,16 +87,16 @@ struct Bufs {
     std::vector<void*> p;
     ~Bufs()
     {
-        for (void* x : p) cudaFree(x);
+        for (void* x : p) dev_free_sync(x);
     }
     template <typename T>
     tigre_status alloc(T** out, size_t count)
     {
         void* x = nullptr;
-        cudaError_t e = cudaMalloc(&x, sizeof(T) * std::max<size_t>(count, 1));
+        cudaError_t e = dev_alloc_sync(&x, sizeof(T) * std::max<size_t>(count, 1));
         if (e != cudaSuccess) {
             cudaGetLastError();
-            return cuda_fail(e, "cudaMalloc(out-of-core buffer)");
+            return cuda_fail(e, "device allocation (out-of-core buffer)");
         }
         p.push_back(x);
         *out = (T*)x;

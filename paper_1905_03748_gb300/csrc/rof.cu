@@ -93,7 +93,7 @@ tigre_status rof_impl(const int64_t n[3], const float* f, float* u, double lam, 
     // workspace: ubar, px, py, pz (and a copy of f when it aliases u)
     const bool alias = f == u;
     float* ws = nullptr;
-    TIGRE_CUDA(cudaMallocAsync((void**)&ws, bytes * (alias ? 5 : 4), st));
+    TIGRE_CUDA(dev_alloc((void**)&ws, bytes * (alias ? 5 : 4), st));
     float *ubar = ws, *px = ws + nv, *py = ws + 2 * nv, *pz = ws + 3 * nv;
     const float* src = f;
     tigre_status status = TIGRE_OK;
@@ -128,7 +128,7 @@ tigre_status rof_impl(const int64_t n[3], const float* f, float* u, double lam, 
             if (e != cudaSuccess) status = cuda_fail(e, "rof kernels");
         }
     }
-    cudaFreeAsync(ws, st);
+    dev_free(ws, st);
     return status;
 }
 

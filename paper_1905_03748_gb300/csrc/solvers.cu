@@ -13,6 +13,8 @@
 // they are staged to the device once, solved in-core, and the result copied
 // back (the whole problem must fit the device memory).
 #include <algorithm>
+#include <chrono>
+#include <thread>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -30,16 +32,16 @@ struct Scratch {
     explicit Scratch(cudaStream_t s) : st(s) {}
     ~Scratch()
     {
-        for (void* p : ptrs) cudaFreeAsync(p, st);
+        for (void* p : ptrs) dev_free(p, st);
     }
     template <typename T>
     tigre_status alloc(T** out, size_t count)
     {
         void* p = nullptr;
-        cudaError_t e = cudaMallocAsync(&p, sizeof(T) * (count ? count : 1), st);
+        cudaError_t e = dev_alloc(&p, sizeof(T) * (count ? count : 1), st);
         if (e != cudaSuccess) {
             cudaGetLastError();
-            return cuda_fail(e, "cudaMallocAsync(solver workspace)");
+            return cuda_fail(e, "device allocation (solver workspace)");
         }
         ptrs.push_back(p);
         *out = (T*)p;
@@ -78,6 +80,27 @@ tigre_status check_opts(const tigre_geometry* g, const tigre_solver_opts* o, con
     return TIGRE_OK;
 }
 
+// Wait until the work queued on st has finished, for at most timeout_ms
+// milliseconds (<= 0: no limit).  On expiry the work stays queued and
+// completes on its own; the caller gets TIGRE_ERR_TIMEOUT.
+tigre_status wait_stream(cudaStream_t st, int64_t timeout_ms)
+{
+    if (timeout_ms <= 0) {
+        TIGRE_CUDA(cudaStreamSynchronize(st));
+        return TIGRE_OK;
+    }
+    const auto deadline = std::chrono::steady_clock::now() + std::chrono::milliseconds(timeout_ms);
+    for (;;) {
+        const cudaError_t e = cudaStreamQuery(st);
+        if (e == cudaSuccess) return TIGRE_OK;
+        if (e != cudaErrorNotReady) return cuda_fail(e, "cudaStreamQuery");
+        if (std::chrono::steady_clock::now() >= deadline)
+            return fail(TIGRE_ERR_TIMEOUT, "solver work still running after timeout_ms; it "
+                                           "completes on its stream, results are not copied");
+        std::this_thread::sleep_for(std::chrono::microseconds(200));
+    }
+}
+
 // Run `body` on device-resident b and x, staging them when they are host pointers.
 template <typename F>
 tigre_status with_device_problem(tigre_geometry* g, const void* proj, void* vol,
@@ -104,13 +127,16 @@ tigre_status with_device_problem(tigre_geometry* g, const void* proj, void* vol,
     P.b = db;
     P.x = dx;
     TIGRE_TRY(body(P));
+    TIGRE_TRY(wait_stream(st, o->timeout_ms));
     TIGRE_CUDA(cudaMemcpyAsync(vol, dx, P.elem * (size_t)P.nvox, cudaMemcpyDeviceToHost, st));
     TIGRE_CUDA(cudaStreamSynchronize(st));
     return TIGRE_OK;
 }
 
-tigre_status finish_history(const double* d_hist, double* h_hist, int n, cudaStream_t st)
+tigre_status finish_history(const double* d_hist, double* h_hist, int n, cudaStream_t st,
+                            int64_t timeout_ms = 0)
 {
+    TIGRE_TRY(wait_stream(st, timeout_ms));
     if (h_hist && n > 0)
         TIGRE_CUDA(cudaMemcpyAsync(h_hist, d_hist, sizeof(double) * (size_t)n,
                                    cudaMemcpyDeviceToHost, st));
@@ -182,7 +208,7 @@ tigre_status run_sart(const Problem& P, int64_t subset, double* h_hist)
                               sc.slot(3), tv_g, tv_red, P.st));
         }
     }
-    return finish_history(hist, h_hist, o->n_iter, P.st);
+    return finish_history(hist, h_hist, o->n_iter, P.st, o->timeout_ms);
 }
 
 }  // namespace
@@ -220,18 +246,19 @@ void cgls_release(tigre_cgls_state* S)
         if (e) cudaGraphExecDestroy(e);
     for (void* ptr : {(void*)S->r, (void*)S->q, (void*)S->p, (void*)S->s, (void*)S->sc,
                       (void*)S->hist, (void*)S->counter})
-        if (ptr) cudaFreeAsync(ptr, S->st);
+        if (ptr) dev_free(ptr, S->st);
     delete S;
+    handle_destroyed();
 }
 
 template <typename T>
 tigre_status dalloc(T** out, size_t count, cudaStream_t st)
 {
     void* ptr = nullptr;
-    cudaError_t e = cudaMallocAsync(&ptr, sizeof(T) * (count ? count : 1), st);
+    cudaError_t e = dev_alloc(&ptr, sizeof(T) * (count ? count : 1), st);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        return cuda_fail(e, "cudaMallocAsync(cgls workspace)");
+        return cuda_fail(e, "device allocation (cgls workspace)");
     }
     *out = (T*)ptr;
     return TIGRE_OK;
@@ -271,7 +298,7 @@ tigre_status cgls_reserve(tigre_cgls_state* S, int more)
     TIGRE_TRY(dalloc(&nh, (size_t)cap, S->st));
     TIGRE_CUDA(cudaMemcpyAsync(nh, S->hist, sizeof(double) * (size_t)S->hist_cap,
                                cudaMemcpyDeviceToDevice, S->st));
-    cudaFreeAsync(S->hist, S->st);
+    dev_free(S->hist, S->st);
     S->hist = nh;
     S->hist_cap = cap;
     // Captured graphs hold the old history pointer: recapture on next use.
@@ -335,6 +362,7 @@ tigre_status cgls_begin_device(tigre_geometry* g, const void* b, void* x,
 {
     tigre_cgls_state* S = new (std::nothrow) tigre_cgls_state();
     if (!S) return fail(TIGRE_ERR_OOM, "host allocation failed");
+    handle_created();
     S->g = g;
     S->bw = o->bp_weight;
     // Graph replay needs a capturable stream (not the legacy default stream).
@@ -361,7 +389,7 @@ tigre_status run_cgls(const Problem& P, double* h_hist)
     TIGRE_TRY(cgls_begin_device(P.g, P.b, P.x, P.o, &S));
     tigre_status st = cgls_reserve(S, P.o->n_iter);
     for (int it = 0; it < P.o->n_iter && st == TIGRE_OK; ++it) st = cgls_step(S);
-    if (st == TIGRE_OK) st = finish_history(S->hist, h_hist, P.o->n_iter, P.st);
+    if (st == TIGRE_OK) st = finish_history(S->hist, h_hist, P.o->n_iter, P.st, P.o->timeout_ms);
     cgls_release(S);
     return st;
 }

@@ -147,14 +147,14 @@ extern "C" tigre_status tigre_tv_step(const int64_t n_voxel[3], void* vol, tigre
     const int64_t N = n_voxel[0] * n_voxel[1] * n_voxel[2];
     void* g = nullptr;
     void* red = nullptr;
-    TIGRE_CUDA(cudaMallocAsync(&g, sizeof(float) * (size_t)N, st));
-    cudaError_t e = cudaMallocAsync(&red, sizeof(double) * (kRedBlocks + 4), st);
+    TIGRE_CUDA(dev_alloc(&g, sizeof(float) * (size_t)N, st));
+    cudaError_t e = dev_alloc(&red, sizeof(double) * (kRedBlocks + 4), st);
     if (e != cudaSuccess) {
-        cudaFreeAsync(g, st);
-        return cuda_fail(e, "cudaMallocAsync(tv reduction)");
+        dev_free(g, st);
+        return cuda_fail(e, "device allocation (tv reduction)");
     }
     tigre_status s = tv_impl(n_voxel, vol, dtype, n_steps, alpha, eps, nullptr, g, (double*)red, st);
-    cudaFreeAsync(g, st);
-    cudaFreeAsync(red, st);
+    dev_free(g, st);
+    dev_free(red, st);
     return s;
 }

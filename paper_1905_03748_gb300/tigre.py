@@ -37,7 +37,7 @@ EXPORTED = ["tigre_geometry_create", "tigre_geometry_destroy", "tigre_forward", 
             "tigre_cgls_end", "tigre_forward_samples", "tigre_forward_ooc", "tigre_backward_ooc",
             "tigre_cgls_ooc_plan", "tigre_geometry_set_forward_path",
             "tigre_geometry_set_projector", "tigre_fdk", "tigre_rof_denoise",
-            "tigre_geometry_set_brick", "tigre_tv_step_ooc",
+            "tigre_geometry_set_brick", "tigre_tv_step_ooc", "tigre_set_allocator",
             "tigre_geometry_error_flags", "tigre_profile_enable",
             "tigre_profile_read", "tigre_launch_count", "tigre_last_error"]
 
@@ -95,6 +95,9 @@ _sigs = {
     "tigre_profile_enable": [ctypes.c_int],
     "tigre_profile_read": [ctypes.c_int, ctypes.POINTER(_I64), ctypes.POINTER(ctypes.c_double)],
 }
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+_sigs["tigre_set_allocator"] = [ALLOC_FN, FREE_FN, _P]
 for _name, _args in _sigs.items():
     _f = getattr(_lib, _name)
     _f.argtypes = _args
@@ -264,14 +267,15 @@ TIGRE_OUT_OF_CORE = 0x4
 
 
 def tigre_cgls(handle, proj, vol, n_iter, bp_weight="matched", stream=None,
-               host=False, out_of_core=False, device_budget_bytes=0) -> np.ndarray:
+               host=False, out_of_core=False, device_budget_bytes=0,
+               timeout_ms=0) -> np.ndarray:
     """CGLS.  host=True stages host tensors through the device; with
     out_of_core=True proj and vol are host tensors, part of the state stays in
     host memory and the volume streams through the GPU in z-slabs; the
     placement and slab thickness follow from device_budget_bytes (0 =
     automatic), see tigre_cgls_ooc_plan."""
     o = _opts(n_iter, stream, bp_weight=bp_weight,
-              device_budget_bytes=int(device_budget_bytes))
+              device_budget_bytes=int(device_budget_bytes), timeout_ms=int(timeout_ms))
     if out_of_core:
         o.flags |= TIGRE_OUT_OF_CORE
         hist = np.zeros(max(n_iter, 1), dtype=np.float64)
@@ -395,6 +399,55 @@ def tigre_tv_step_ooc(vol_host: torch.Tensor, n_steps: int, alpha: float, eps: f
     n = (ctypes.c_int64 * 3)(vol_host.shape[2], vol_host.shape[1], vol_host.shape[0])
     _check(_lib.tigre_tv_step_ooc(n, _host_f32(vol_host, "vol_host"), int(n_steps), float(alpha),
                                   float(eps), int(slab_planes), int(halo_depth), _stream(stream)))
+
+
+_allocator_refs = None  # keeps the installed ctypes callbacks alive
+
+
+def tigre_set_allocator(alloc=None, free=None) -> None:
+    """Install Python callables as the library's device workspace allocator:
+    alloc(nbytes, stream_ptr) -> device pointer (int, 0 on failure) and
+    free(ptr, stream_ptr); None, None restores the CUDA default.  Only while
+    no Geometry or CGLS state is alive."""
+    global _allocator_refs
+    if alloc is None and free is None:
+        _check(_lib.tigre_set_allocator(ALLOC_FN(), FREE_FN(), None))
+        _allocator_refs = None
+        return
+
+    def _a(nbytes, stream, ctx):
+        try:
+            return int(alloc(int(nbytes), int(stream or 0)) or 0)
+        except Exception:
+            return 0
+
+    def _f(ptr, stream, ctx):
+        try:
+            free(int(ptr), int(stream or 0))
+        except Exception:
+            pass
+
+    refs = (ALLOC_FN(_a), FREE_FN(_f))
+    _check(_lib.tigre_set_allocator(refs[0], refs[1], None))
+    _allocator_refs = refs
+
+
+def use_torch_allocator(on: bool = True) -> None:
+    """Route the library's device workspaces through PyTorch's caching
+    allocator (on the stream the library names, the current device), so the
+    library and the framework share one memory pool."""
+    if not on:
+        tigre_set_allocator(None, None)
+        return
+
+    def _alloc(nbytes, stream):
+        return torch.cuda.caching_allocator_alloc(nbytes, device=torch.cuda.current_device(),
+                                                  stream=stream)
+
+    def _free(ptr, stream):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    tigre_set_allocator(_alloc, _free)
 
 
 PROJ_INTERPOLATED, PROJ_SIDDON = 0, 1

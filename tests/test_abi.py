@@ -70,3 +70,11 @@ def test_solver_defaults(lib):
     o = tigre.tigre_solver_opts_default()
     assert o.n_iter == 10 and o.lambda_ == 1.0 and o.subset_size == 20
     assert o.bp_weight == tigre.TIGRE_BP_MATCHED and o.storage == tigre.TIGRE_F32
+
+
+def test_allocator_needs_both_functions_and_resets():
+    from paper_1905_03748_gb300 import tigre
+    alloc = tigre.ALLOC_FN(lambda n, s, c: 0)
+    assert tigre._lib.tigre_set_allocator(alloc, tigre.FREE_FN(), None) == tigre.TIGRE_ERR_INVALID_ARG
+    tigre.tigre_set_allocator(lambda n, s: 0, lambda p, s: None)
+    tigre.tigre_set_allocator(None, None)

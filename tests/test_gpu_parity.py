@@ -315,3 +315,23 @@ def test_cgls_reduced_storage_tracks_fp64_oracle(tigre, dtype, scale, tol_x, tol
     assert torch.isfinite(x.float()).all()
     assert rel(x.float().cpu().numpy() / scale, x_ref) < tol_x
     np.testing.assert_allclose(np.asarray(h) / scale, h_ref, rtol=tol_h)
+
+
+def test_solver_timeout_returns_and_the_work_completes(tigre):
+    """A bounded host wait: with timeout_ms far below the solve time the call
+    returns TIGRE_ERR_TIMEOUT at once, the queued iterations complete on
+    their stream, and the volume is the same as an unbounded solve's."""
+    geo, ang = synth.workload("cgls_512")
+    vol = synth.random_volume((512, 512, 512), seed=24)
+    with tigre.Geometry(geo, ang) as G:
+        b = G.forward(torch.from_numpy(vol).cuda())
+        x_ref = torch.zeros(G.vol_shape, device="cuda")
+        tigre.tigre_cgls(G.handle, b, x_ref, 3)
+        x = torch.zeros(G.vol_shape, device="cuda")
+        with pytest.raises(tigre.TigreError) as e:
+            tigre.tigre_cgls(G.handle, b, x, 3, timeout_ms=1)
+        assert e.value.status == tigre.TIGRE_ERR_TIMEOUT
+        torch.cuda.synchronize()
+        assert torch.equal(x, x_ref)
+        h = tigre.tigre_cgls(G.handle, b, torch.zeros_like(x), 3, timeout_ms=600000)
+        assert len(h) == 3
