@@ -277,7 +277,7 @@ tigre_status tigre_geometry_create(const tigre_geometry_desc* desc, const double
     g->angles.assign(angles, angles + n_angles);
     cudaError_t e = cudaGetDevice(&g->device);
     if (e != cudaSuccess) {
-        delete g;
+        tigre_geometry_destroy(g);
         return cuda_fail(e, "cudaGetDevice");
     }
     tigre_status st = upload_params(g);

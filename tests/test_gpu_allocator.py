@@ -73,3 +73,46 @@ def test_allocator_cannot_change_while_a_handle_is_alive(tigre):
             tigre.use_torch_allocator(True)
     tigre.use_torch_allocator(True)
     tigre.use_torch_allocator(False)
+
+
+@pytest.mark.parametrize("fail_at", [1, 3, 6])
+def test_injected_allocation_failure_is_reported_and_leaks_nothing(tigre, fail_at):
+    """Host-side fault injection: the allocator refuses its fail_at-th request.
+    The call returns TIGRE_ERR_OOM, every buffer handed out is given back, and
+    the next call (default allocator) works."""
+    gc.collect()
+    live = {}
+    n = {"calls": 0}
+
+    def alloc(nbytes, stream):
+        n["calls"] += 1
+        if n["calls"] == fail_at:
+            return 0
+        p = torch.cuda.caching_allocator_alloc(nbytes, device=torch.cuda.current_device(),
+                                               stream=stream)
+        live[p] = nbytes
+        return p
+
+    def free(ptr, stream):
+        live.pop(ptr)
+        torch.cuda.caching_allocator_delete(ptr)
+
+    geo = synth.geometry((21, 19, 17), 1.0, (31, 23), 1.0, dso=200.0, dsd=300.0)
+    ang = synth.angles(12)
+    vol = torch.from_numpy(synth.random_volume((17, 19, 21), seed=25)).cuda()
+    tigre.tigre_set_allocator(alloc, free)
+    try:
+        with pytest.raises(tigre.TigreError) as e:
+            with tigre.Geometry(geo, ang) as G:
+                b = G.forward(vol)
+                x = torch.zeros(G.vol_shape, device="cuda")
+                tigre.tigre_cgls(G.handle, b, x, 3)
+                G.fdk(b)
+        assert e.value.status == tigre.TIGRE_ERR_OOM
+        gc.collect()
+        torch.cuda.synchronize()
+        assert not live
+    finally:
+        tigre.tigre_set_allocator(None, None)
+    with tigre.Geometry(geo, ang) as G:
+        assert torch.isfinite(G.forward(vol)).all()
