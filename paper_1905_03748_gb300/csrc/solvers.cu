@@ -277,8 +277,14 @@ tigre_status cgls_init(tigre_cgls_state* S, int hist_cap)
     TIGRE_TRY(dalloc(&S->hist, (size_t)S->hist_cap, S->st));
     TIGRE_TRY(dalloc(&S->counter, 1, S->st));
     TIGRE_CUDA(cudaMemsetAsync(S->counter, 0, sizeof(int), S->st));
+    S->cur = 0;
+    return TIGRE_OK;
+}
+
+// r = b - A x0; p = A^T r; gamma = ||p||^2
+tigre_status cgls_start(tigre_cgls_state* S)
+{
     Scalars sc{S->sc};
-    // r = b - A x0; p = A^T r; gamma = ||p||^2
     TIGRE_TRY(forward_impl(S->g, S->x, S->dt, S->q, S->dt, 0, S->na, S->st));
     TIGRE_TRY(weighted_residual_dt(S->dt, S->b, S->q, nullptr, S->r, S->m, sc.partials(),
                                    sc.slot(3), S->st));
@@ -357,8 +363,10 @@ tigre_status cgls_capture(tigre_cgls_state* S, cudaGraphExec_t* out)
     return TIGRE_OK;
 }
 
-tigre_status cgls_begin_device(tigre_geometry* g, const void* b, void* x,
-                               const tigre_solver_opts* o, tigre_cgls_state** out)
+// A state with its buffers allocated and its fields set; r, p and gamma not
+// yet computed.
+tigre_status cgls_new_state(tigre_geometry* g, const void* b, void* x,
+                            const tigre_solver_opts* o, tigre_cgls_state** out)
 {
     tigre_cgls_state* S = new (std::nothrow) tigre_cgls_state();
     if (!S) return fail(TIGRE_ERR_OOM, "host allocation failed");
@@ -374,10 +382,49 @@ tigre_status cgls_begin_device(tigre_geometry* g, const void* b, void* x,
     S->dt = o->storage;
     S->b = b;
     S->x = x;
-    tigre_status st = cgls_init(S, o->n_iter);
+    const tigre_status st = cgls_init(S, o->n_iter);
     if (st != TIGRE_OK) {
         cgls_release(S);
         return st;
+    }
+    *out = S;
+    return TIGRE_OK;
+}
+
+tigre_status cgls_begin_device(tigre_geometry* g, const void* b, void* x,
+                               const tigre_solver_opts* o, tigre_cgls_state** out)
+{
+    tigre_cgls_state* S = nullptr;
+    TIGRE_TRY(cgls_new_state(g, b, x, o, &S));
+    const tigre_status st = cgls_start(S);
+    if (st != TIGRE_OK) {
+        cgls_release(S);
+        return st;
+    }
+    *out = S;
+    return TIGRE_OK;
+}
+
+// A state whose r, p and gamma come from a checkpoint (host buffers in the
+// storage type) instead of the initial A x0 / A^T r.  The copies complete
+// before it returns (gamma is read from the caller's stack).
+tigre_status cgls_resume_device(tigre_geometry* g, const void* b, void* x, const void* r_host,
+                                const void* p_host, double gamma, const tigre_solver_opts* o,
+                                tigre_cgls_state** out)
+{
+    tigre_cgls_state* S = nullptr;
+    TIGRE_TRY(cgls_new_state(g, b, x, o, &S));
+    const size_t e = dtype_size(S->dt);
+    cudaError_t ce = cudaMemcpyAsync(S->r, r_host, e * (size_t)S->m, cudaMemcpyHostToDevice, S->st);
+    if (ce == cudaSuccess)
+        ce = cudaMemcpyAsync(S->p, p_host, e * (size_t)S->nvox, cudaMemcpyHostToDevice, S->st);
+    if (ce == cudaSuccess)
+        ce = cudaMemcpyAsync(Scalars{S->sc}.slot(0), &gamma, sizeof(double),
+                             cudaMemcpyHostToDevice, S->st);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(S->st);
+    if (ce != cudaSuccess) {
+        cgls_release(S);
+        return cuda_fail(ce, "cgls resume");
     }
     *out = S;
     return TIGRE_OK;
@@ -469,6 +516,36 @@ tigre_status tigre_cgls_history(tigre_cgls_t S, double* resid_hist, int n)
     if (!S || n < 0 || n > S->done || (n > 0 && !resid_hist))
         return fail(TIGRE_ERR_INVALID_ARG, "history: need 0 <= n <= iterations done");
     return finish_history(S->hist, resid_hist, n, S->st);
+}
+
+tigre_status tigre_cgls_save(tigre_cgls_t S, void* r_host, void* p_host, double* gamma,
+                             int* iterations)
+{
+    if (!S || !r_host || !p_host || !gamma || !iterations)
+        return fail(TIGRE_ERR_INVALID_ARG, "null state or output");
+    const size_t e = dtype_size(S->dt);
+    TIGRE_CUDA(cudaMemcpyAsync(r_host, S->r, e * (size_t)S->m, cudaMemcpyDeviceToHost, S->st));
+    TIGRE_CUDA(cudaMemcpyAsync(p_host, S->p, e * (size_t)S->nvox, cudaMemcpyDeviceToHost, S->st));
+    TIGRE_CUDA(cudaMemcpyAsync(gamma, Scalars{S->sc}.slot(S->cur), sizeof(double),
+                               cudaMemcpyDeviceToHost, S->st));
+    TIGRE_CUDA(cudaStreamSynchronize(S->st));
+    *iterations = S->done;
+    return TIGRE_OK;
+}
+
+tigre_status tigre_cgls_resume(tigre_geometry_t geo, const void* proj, void* vol,
+                               const void* r_host, const void* p_host, double gamma,
+                               const tigre_solver_opts* opts, tigre_cgls_t* out)
+{
+    if (!out) return fail(TIGRE_ERR_INVALID_ARG, "null output handle pointer");
+    *out = nullptr;
+    TIGRE_TRY(check_geometry(geo));
+    TIGRE_TRY(check_opts(geo, opts, proj, vol));
+    if (!r_host || !p_host || !std::isfinite(gamma))
+        return fail(TIGRE_ERR_INVALID_ARG, "checkpoint buffers and a finite gamma are needed");
+    if (opts->flags & TIGRE_HOST_RESIDENT)
+        return fail(TIGRE_ERR_UNSUPPORTED, "stepwise CGLS takes device buffers");
+    return cgls_resume_device(geo, proj, vol, r_host, p_host, gamma, opts, out);
 }
 
 tigre_status tigre_cgls_end(tigre_cgls_t S)

@@ -34,7 +34,7 @@ EXPORTED = ["tigre_geometry_create", "tigre_geometry_destroy", "tigre_forward", 
             "tigre_tv_step", "tigre_tv_step_noalloc", "tigre_solver_opts_default", "tigre_sirt",
             "tigre_sart",
             "tigre_cgls", "tigre_cgls_begin", "tigre_cgls_iterate", "tigre_cgls_history",
-            "tigre_cgls_end", "tigre_forward_samples", "tigre_forward_ooc", "tigre_backward_ooc",
+            "tigre_cgls_end", "tigre_cgls_save", "tigre_cgls_resume", "tigre_forward_samples", "tigre_forward_ooc", "tigre_backward_ooc",
             "tigre_cgls_ooc_plan", "tigre_geometry_set_forward_path",
             "tigre_geometry_set_projector", "tigre_fdk", "tigre_rof_denoise",
             "tigre_geometry_set_brick", "tigre_tv_step_ooc", "tigre_set_allocator",
@@ -81,6 +81,9 @@ _sigs = {
     "tigre_cgls_iterate": [_P, ctypes.c_int],
     "tigre_cgls_history": [_P, _P, ctypes.c_int],
     "tigre_cgls_end": [_P],
+    "tigre_cgls_save": [_P, _P, _P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)],
+    "tigre_cgls_resume": [_P, _P, _P, _P, _P, ctypes.c_double, ctypes.POINTER(tigre_solver_opts),
+                          ctypes.POINTER(_P)],
     "tigre_forward_samples": [_P, _I64, _I64, ctypes.POINTER(_I64)],
     "tigre_forward_ooc": [_P, _P, _P, _I64, _I64, _I64, _P],
     "tigre_backward_ooc": [_P, _P, ctypes.c_int, _P, _I64, _I64, ctypes.c_int, _I64, _I64, _P],
@@ -330,6 +333,46 @@ def tigre_cgls_history(state, n: int) -> np.ndarray:
 
 def tigre_cgls_end(state) -> None:
     _check(_lib.tigre_cgls_end(state))
+
+
+def tigre_cgls_save(state, r_host: torch.Tensor, p_host: torch.Tensor) -> tuple:
+    """Copy a stepwise state's residual and search direction into host
+    tensors (projection- and volume-shaped, the state's storage dtype);
+    returns (gamma, iterations done).  With x these are the whole state."""
+    for t, name in ((r_host, "r_host"), (p_host, "p_host")):
+        if t.device.type != "cpu" or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous host tensor")
+    g = ctypes.c_double()
+    n = ctypes.c_int()
+    _check(_lib.tigre_cgls_save(state, ctypes.c_void_p(r_host.data_ptr()),
+                                ctypes.c_void_p(p_host.data_ptr()), ctypes.byref(g),
+                                ctypes.byref(n)))
+    return float(g.value), int(n.value)
+
+
+def tigre_cgls_resume(handle, proj, vol, r_host, p_host, gamma: float, n_iter_hint=16,
+                      bp_weight="matched", stream=None, graph=False):
+    """A stepwise state from a checkpoint taken by tigre_cgls_save: vol holds
+    the checkpoint's x, proj is b; the iterations continue as the saved
+    state's would have."""
+    o = _opts(n_iter_hint, stream, bp_weight=bp_weight)
+    if graph:
+        o.flags |= TIGRE_GRAPH
+    pp, pt = _dev(proj, "proj")
+    vp, vt = _dev(vol, "vol")
+    if pt != vt or r_host.dtype != vol.dtype or p_host.dtype != vol.dtype:
+        raise TypeError("proj, vol and the checkpoint must share one storage dtype")
+    for t, name in ((r_host, "r_host"), (p_host, "p_host")):
+        if t.device.type != "cpu" or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous host tensor")
+    if r_host.numel() != proj.numel() or p_host.numel() != vol.numel():
+        raise ValueError("checkpoint sizes do not match proj and vol")
+    o.storage = vt
+    s = ctypes.c_void_p()
+    _check(_lib.tigre_cgls_resume(handle, pp, vp, ctypes.c_void_p(r_host.data_ptr()),
+                                  ctypes.c_void_p(p_host.data_ptr()), float(gamma),
+                                  ctypes.byref(o), ctypes.byref(s)))
+    return s
 
 
 def tigre_forward_samples(handle, angle_begin: int, angle_count: int) -> int:
