@@ -5,8 +5,10 @@ with an N^2 detector (cube workload geometry) and a chosen number of angles.
     python -m paper_1905_03748_gb300.opbench --op backward --weight matched --n 512 --angles 16 --repeat 1
 
 Prints one JSON line: device ms per call (CUDA events on the launching
-stream, after one warm-up call) and Gvoxel*angles/s.  Also the small-case
-target of the committed ncu profiles.
+stream, after one warm-up call), Gvoxel*angles/s, and the projection or
+backprojection kernels' own device time per call (the library's event
+timer; for the out-of-core operators it excludes the host copies and the
+slab relayouts).  Also the small-case target of the committed ncu profiles.
 """
 from __future__ import annotations
 
@@ -47,6 +49,8 @@ def main():
     ap.add_argument("--path", choices=["auto", "l1", "tma", "quad", "pair"], default="auto",
                     help="forward-projector kernel")
     ap.add_argument("--projector", choices=["interpolated", "siddon"], default="interpolated")
+    ap.add_argument("--brick", type=int, default=0,
+                    help="x-y brick edge of slab projections (0 = library default)")
     a = ap.parse_args()
     dt = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}[a.dtype]
     geo = synth.cube_geometry(a.n, a.n)
@@ -55,6 +59,7 @@ def main():
     tigre.tigre_geometry_set_forward_path(G.handle, {"auto": 0, "l1": 1, "tma": 2, "quad": 3,
                                                      "pair": 4}[a.path])
     tigre.tigre_geometry_set_projector(G.handle, a.projector)
+    tigre.tigre_geometry_set_brick(G.handle, a.brick)
     vol = torch.from_numpy(cached_phantom(a.n)).cuda().to(dt)
     proj = torch.empty(G.proj_shape, device="cuda", dtype=dt)
     out = torch.empty(G.vol_shape, device="cuda", dtype=dt)
@@ -88,18 +93,25 @@ def main():
         fn()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    tigre.tigre_profile_enable(True)
     e0.record()
     for _ in range(a.repeat):
         fn()
     e1.record()
     torch.cuda.synchronize()
+    kind = {"forward": tigre.PROF_FORWARD, "forward_ooc": tigre.PROF_FORWARD,
+            "backward": tigre.PROF_BACKPROJECT, "backward_ooc": tigre.PROF_BACKPROJECT,
+            "fdk": tigre.PROF_BACKPROJECT, "adjoint": tigre.PROF_ADJOINT}.get(a.op, tigre.PROF_TV)
+    kernel_ms = tigre.tigre_profile_read(kind)[1] / max(a.repeat, 1)
+    tigre.tigre_profile_enable(False)
     ms = e0.elapsed_time(e1) / max(a.repeat, 1)
     va = float(a.n) ** 3 * a.angles
     print(json.dumps({"op": a.op, "weight": a.weight, "n": a.n, "angles": a.angles,
-                      "dtype": a.dtype, "path": a.path, "projector": a.projector, "ms": ms, "gvox_ang_s": va / ms / 1e6,
+                      "dtype": a.dtype, "path": a.path, "projector": a.projector, "brick": a.brick, "ms": ms,
+                      "kernel_ms": kernel_ms, "gvox_ang_s": va / ms / 1e6,
                       "error_flags": tigre.tigre_geometry_error_flags(G.handle),
-                      "checksum": float(out.float().sum() if a.op != "forward" else
-                                        proj.float().sum())}))
+                      "checksum": float(proj.float().sum() if a.op in ("forward", "forward_ooc") else
+                                        out.float().sum())}))
     G.close()
 
 
