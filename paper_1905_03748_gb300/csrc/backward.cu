@@ -46,6 +46,17 @@ struct BpConst {
     float wscale;          // (dx dy dz)/(du dv) * DSD^2
 };
 
+// 1/sqrt(x) straight from the special-function unit (PTX rsqrt.approx, inputs
+// below the smallest normal flushed to zero).  Used where x is a squared
+// source-voxel distance in mm^2, far inside the normal range, for which it
+// returns what rsqrtf does without rsqrtf's denormal handling.
+__device__ __forceinline__ float rsqrt_sfu(float x)
+{
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 template <typename T>
 __device__ __forceinline__ float ldp(const T* p)
 {
@@ -130,7 +141,7 @@ __global__ void __launch_bounds__(256, SART ? 3 : 5) bp_voxel_kernel(const TP* _
             if (MODE != TIGRE_BP_FDK) {
                 const float Z = fmaf((float)k, c.dz, Zb);
                 const float l2 = fmaf(Z, Z, lxy2);
-                wk = w * (l2 * rsqrtf(l2));
+                wk = w * (l2 * rsqrt_sfu(l2));
             }
             acc[k] = fmaf(wk, val, acc[k]);
             if (SART) {
