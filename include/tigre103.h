@@ -361,13 +361,18 @@ TIGRE_API tigre_status tigre_geometry_set_projector(tigre_geometry_t geo, int pr
 TIGRE_API tigre_status tigre_geometry_set_brick(tigre_geometry_t geo, int64_t edge);
 
 /* Forward-projector kernel choice for this handle: 0 = automatic (the quad
- * gather kernel), 1 = scalar L1 gather kernel, 2 = shared-memory slab kernel
+ * gather kernel; with 2 angles per warp for full-range calls when the rays of
+ * one pixel at paired angles stay within 16 voxels of each other, e.g. 512^3 x
+ * 360), 1 = scalar L1 gather kernel, 2 = shared-memory slab kernel
  * (TMA-staged; only for geometries whose ray bundles fit its staging box,
  * otherwise it reports error bit 2 and NaN), 3 = quad gather kernel (two
  * 16-byte loads per sample from a layout holding the four taps of a cell's
  * plane; four times the volume in workspace), 4 = quad gather kernel taking a
- * ray's samples two at a time (both samples' loads issued together).  All
- * compute the same sums in the same order and give identical results.
+ * ray's samples two at a time (both samples' loads issued together), 5 / 6 =
+ * quad gather kernel whose warps hold 16 pixels x 2 / 8 pixels x 4 angles
+ * (neighbouring angles of one memory layout and march direction, so a warp's
+ * gathers share cache lines; full-range calls, other ranges use path 3).
+ * All compute the same sums in the same order and give identical results.
  * Out-of-core slab projections use the quad kernel, two samples at a time for
  * path 4. */
 TIGRE_API tigre_status tigre_geometry_set_forward_path(tigre_geometry_t geo, int path);

@@ -107,6 +107,7 @@ struct DeviceBuffer {
 };
 
 constexpr int64_t kBrickDefault = 512;  // x-y brick edge of out-of-core slab projections
+constexpr double kPairDriftVoxels = 16.0;  // automatic 2-angle warps up to this ray drift
 
 // Per-angle parameters of the forward projector, expressed in the index
 // coordinates of the padded volume layout the angle uses.  "f", "m", "s" are
@@ -138,6 +139,13 @@ struct tigre_geometry {
     tigre::DeviceBuffer fwd_params;   // FwdAngle[n_angles]
     tigre::DeviceBuffer bp_params;    // BpAngle[n_angles]
     tigre::DeviceBuffer angle_order;  // int[n_angles]: angle indices grouped by layout
+    // Angle groups of 2 and 4 (index 0, 1) for the angle-interleaved forward
+    // kernel: int[n_groups * size], -1 filling a short group.
+    tigre::DeviceBuffer angle_groups[2];
+    int64_t n_groups[2] = {0, 0};
+    // Angles per warp of the automatic forward path (1 or 2): 2 when rays of
+    // one pixel at grouped angles stay within a few voxels of each other.
+    int auto_angle_group = 1;
     tigre::DeviceBuffer vol_xy;       // padded volume, x fastest
     tigre::DeviceBuffer vol_yx;       // padded volume, y fastest
     tigre::DeviceBuffer vol_qxy;      // quad volumes of the two padded layouts
@@ -148,7 +156,9 @@ struct tigre_geometry {
     tigre::DeviceBuffer scratch_vol;  // FP32 volume-sized scratch
     tigre::DeviceBuffer scratch_red;  // reduction partials / device scalars
     std::vector<int> layout;          // forward-projector layout per angle (host copy)
-    int fwd_path = 0;                 // 0 auto, 1 L1 scalar, 2 TMA slab, 3 quad, 4 quad pairs
+    // 0 auto, 1 L1 scalar, 2 TMA slab, 3 quad, 4 quad pairs, 5 / 6 quad with
+    // 2 / 4 angles per warp
+    int fwd_path = 0;
     int projector = 0;                // TIGRE_PROJ_INTERPOLATED or TIGRE_PROJ_SIDDON
     tigre::DeviceBuffer err_flag;     // int: error bits set by kernels (bounds, timeouts)
     tigre::DeviceBuffer brick_prange; // int2 per (x-y brick, angle): detector columns reaching it

@@ -15,9 +15,12 @@
 //    cache lines per warp.  The two-voxel zero border removes every bounds
 //    check from the sample loop.
 //  * Grid order: u-tiles fastest, then angles, then detector row bands.  The
-//    blocks resident at any time belong to one row band and many angles; they
-//    all read the same z-slab of the volume, which stays in the 126 MB L2, so
-//    HBM reads the volume about once per call.
+//    blocks resident at any time belong to one row band and many angles and
+//    read the same z-range of the volume.
+//  * Angle pairs: when neighbouring angles are close (the rays of one pixel at
+//    the two angles stay within a few voxels), a warp holds 16 pixels at two
+//    angles instead of 32 pixels at one, and its gathers touch fewer cache
+//    lines (3.3-3.9 % faster at 512^3 x 360 and 1024^3 x 360 / 720).
 //  * floor() without conversion instructions (split_floor).
 #include <algorithm>
 #include <cmath>
@@ -348,28 +351,35 @@ __device__ __forceinline__ void cut_axis(const Ray& R, int ax, int lo, int hi, i
 // The L1 kernel's depth-ordered march, gathering from quad volumes.  With
 // SLAB, each ray processes only its samples [kb, ke) inside the slab (and
 // brick).  With PAIR, the march advances two depth steps at a time and each
-// lane takes up to two samples per step (tri_pair_quad).
+// lane takes up to two samples per step (tri_pair_quad).  With AG > 1 a warp
+// holds 32 / AG pixels of one detector row at AG neighbouring angles (order
+// is then the angle-group table, blockIdx.y the group; full-range, in-core
+// launches only); each ray is marched exactly as with AG = 1.
 // Occupancy: 6 blocks per SM (40 registers) hides more gather latency than
 // the unconstrained 44-register build (5 blocks): 136 vs 144 ms per 512^3 x
 // 360 projection; 7 blocks spill.
-template <typename TV, typename TP, bool SLAB = false, bool PAIR = false>
+template <typename TV, typename TP, bool SLAB = false, bool PAIR = false, int AG = 1>
 __global__ void __launch_bounds__(256, 6) fwd_quad_kernel(
     const typename QuadOf<TV>::type* __restrict__ qxy,
     const typename QuadOf<TV>::type* __restrict__ qyx, TP* __restrict__ proj,
     const FwdAngle* __restrict__ params, FwdConst c, int a_first, const int* __restrict__ order,
     SlabRange sr)
 {
+    static_assert(AG == 1 || (!SLAB && !PAIR), "angle groups: in-core single-sample march only");
     using Q = typename QuadOf<TV>::type;
+    constexpr int CW = 32 / AG;  // detector columns per warp
     const unsigned full = 0xffffffffu;
-    const int p = blockIdx.x * 32 + threadIdx.x;
+    const int p = blockIdx.x * CW + (AG == 1 ? (int)threadIdx.x : (int)threadIdx.x % CW);
     const int q = (SLAB ? sr.q0 : 0) + (int)(blockIdx.z * blockDim.y + threadIdx.y);
-    const int a = order ? order[blockIdx.y] : (int)blockIdx.y;
+    const int a = AG > 1  ? order[blockIdx.y * AG + threadIdx.x / CW]
+                  : order ? order[blockIdx.y]
+                          : (int)blockIdx.y;
     if (SLAB && sr.prange) {  // uniform per block: all its rays miss the brick
         const int2 pr = sr.prange[a_first + a];
         const int p0 = (int)blockIdx.x * 32;
         if (p0 + 31 < pr.x || p0 > pr.y) return;
     }
-    const bool inside = p < c.nu && q < c.nv;
+    const bool inside = p < c.nu && q < c.nv && (AG == 1 || a >= 0);
 
     Ray R;
     R.K = 0;
@@ -384,7 +394,8 @@ __global__ void __launch_bounds__(256, 6) fwd_quad_kernel(
     }
     const bool active = inside && R.ok && ke > kb;
     const unsigned act = __ballot_sync(full, active);
-    const int layout = params[a_first + a].layout;  // uniform per block
+    // uniform per block (a group's first slot always holds an angle)
+    const int layout = params[a_first + (AG > 1 ? order[blockIdx.y * AG] : a)].layout;
     const Q* __restrict__ vol = layout ? qyx : qxy;
     const int PF = (layout ? c.ny : c.nx) + 2 * kPad;
     const int PFM = PF * ((layout ? c.nx : c.ny) + 2 * kPad);
@@ -602,6 +613,23 @@ tigre_status forward_impl(tigre_geometry* g, const void* vol, tigre_dtype vt, vo
                                                      (const TV*)g->vol_yx.ptr, (TP*)proj, a0, na,
                                                      order, st);
             ProfScope prof(kProfForward, st);
+            const int ag = g->fwd_path == 5   ? 2
+                           : g->fwd_path == 6 ? 4
+                           : g->fwd_path == 0 ? g->auto_angle_group
+                                              : 1;
+            if (use_quad && ag > 1 && order) {
+                const int gi = ag == 4 ? 1 : 0;
+                dim3 grid((unsigned)((c.nu + 32 / ag - 1) / (32 / ag)), (unsigned)g->n_groups[gi],
+                          (unsigned)((c.nv + 7) / 8));
+                auto kern = ag == 4 ? fwd_quad_kernel<TV, TP, false, false, 4>
+                                    : fwd_quad_kernel<TV, TP, false, false, 2>;
+                kern<<<grid, dim3(32, 8), 0, st>>>(
+                    (const Q*)g->vol_qxy.ptr, (const Q*)g->vol_qyx.ptr, (TP*)proj,
+                    (const FwdAngle*)g->fwd_params.ptr, c, 0, (const int*)g->angle_groups[gi].ptr,
+                    SlabRange{0, 0, 0, 0, 0, 0, 0, 0, nullptr});
+                TIGRE_LAUNCHED("fwd_quad_kernel");
+                return TIGRE_OK;
+            }
             if (use_quad) {
                 for (int64_t s = 0; s < na; s += 65535) {
                     const int64_t cnt = std::min<int64_t>(65535, na - s);
@@ -783,7 +811,7 @@ extern "C" tigre_status tigre_geometry_set_brick(tigre_geometry_t g, int64_t edg
 
 extern "C" tigre_status tigre_geometry_set_forward_path(tigre_geometry_t g, int path)
 {
-    if (!g || path < 0 || path > 4) return tigre::fail(TIGRE_ERR_INVALID_ARG, "path must be 0..4");
+    if (!g || path < 0 || path > 6) return tigre::fail(TIGRE_ERR_INVALID_ARG, "path must be 0..6");
     g->fwd_path = path;
     return TIGRE_OK;
 }

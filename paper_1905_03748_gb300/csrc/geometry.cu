@@ -246,6 +246,59 @@ tigre_status upload_params(tigre_geometry* g)
     TIGRE_TRY(g->angle_order.ensure(sizeof(int) * (size_t)na));
     TIGRE_CUDA(cudaMemcpy(g->angle_order.ptr, order.data(), sizeof(int) * (size_t)na,
                           cudaMemcpyHostToDevice));
+    // Angle groups for the angle-interleaved forward kernel.  Rays through
+    // one pixel at neighbouring angles pass within a few voxels of each
+    // other, so a warp of (32 / size) pixels x size angles gathers from fewer
+    // cache lines than 32 pixels of one angle.  A group holds angles of one
+    // layout and one march direction (the sign of the ray along the layout's
+    // depth axis), neighbours in angle; -1 fills a short group.
+    {
+        std::vector<int> cls[4];
+        const double pi = std::acos(-1.0);
+        const double centre[4] = {1.5 * pi, 0.5 * pi, pi, 0.0};
+        for (int64_t a = 0; a < na; ++a) {
+            const double t = g->angles[(size_t)a];
+            const int l = g->layout[(size_t)a];
+            const double main = l ? std::cos(t) : std::sin(t);
+            cls[l * 2 + (main > 0.0 ? 1 : 0)].push_back((int)a);
+        }
+        for (int k = 0; k < 4; ++k)
+            std::stable_sort(cls[k].begin(), cls[k].end(), [&](int i, int j) {
+                return std::remainder(g->angles[(size_t)i] - centre[k], 2.0 * pi) <
+                       std::remainder(g->angles[(size_t)j] - centre[k], 2.0 * pi);
+            });
+        // Median angular gap inside pairs x the largest distance of a voxel from
+        // the rotation axis = how far apart (in voxels) the rays of one pixel
+        // at paired angles get.  Pairs paid at 6.3 voxels (512^3 x 360: 3.8 %,
+        // 1024^3 x 720: 3.9 %) and 12.6 (1024^3 x 360: 3.3 %); groups of four
+        // lost 9 % at 50 (1024^3 x 90).
+        std::vector<double> gaps;
+        for (const std::vector<int>& v : cls)
+            for (size_t i = 0; i + 1 < v.size(); i += 2)
+                gaps.push_back(std::fabs(std::remainder(
+                    g->angles[(size_t)v[i + 1]] - g->angles[(size_t)v[i]], 2.0 * pi)));
+        g->auto_angle_group = 1;
+        if (!gaps.empty()) {
+            std::nth_element(gaps.begin(), gaps.begin() + gaps.size() / 2, gaps.end());
+            const double wx = 0.5 * (double)d.n_voxel[0] * d.d_voxel[0] + std::fabs(d.off_origin[0]);
+            const double wy = 0.5 * (double)d.n_voxel[1] * d.d_voxel[1] + std::fabs(d.off_origin[1]);
+            const double drift = gaps[gaps.size() / 2] * std::sqrt(wx * wx + wy * wy) /
+                                 std::min(d.d_voxel[0], d.d_voxel[1]);
+            if (drift <= kPairDriftVoxels) g->auto_angle_group = 2;
+        }
+        for (int gi = 0; gi < 2; ++gi) {
+            const size_t size = gi ? 4 : 2;
+            std::vector<int> tab;
+            for (const std::vector<int>& v : cls)
+                for (size_t i = 0; i < v.size(); i += size)
+                    for (size_t j = 0; j < size; ++j) tab.push_back(i + j < v.size() ? v[i + j] : -1);
+            g->n_groups[gi] = (int64_t)(tab.size() / size);
+            TIGRE_TRY(g->angle_groups[gi].ensure(sizeof(int) * std::max<size_t>(tab.size(), 1)));
+            if (!tab.empty())
+                TIGRE_CUDA(cudaMemcpy(g->angle_groups[gi].ptr, tab.data(), sizeof(int) * tab.size(),
+                                      cudaMemcpyHostToDevice));
+        }
+    }
     TIGRE_TRY(g->fwd_params.ensure(sizeof(FwdAngle) * (size_t)na));
     TIGRE_TRY(g->bp_params.ensure(sizeof(BpAngle) * (size_t)na));
     TIGRE_CUDA(cudaMemcpy(g->fwd_params.ptr, fwd.data(), sizeof(FwdAngle) * (size_t)na,
@@ -296,6 +349,8 @@ tigre_status tigre_geometry_destroy(tigre_geometry_t g)
     g->fwd_params.release();
     g->bp_params.release();
     g->angle_order.release();
+    g->angle_groups[0].release();
+    g->angle_groups[1].release();
     g->vol_xy.release();
     g->vol_yx.release();
     g->vol_qxy.release();

@@ -46,7 +46,8 @@ def main():
     ap.add_argument("--dtype", choices=["f32", "bf16", "f16"], default="f32")
     ap.add_argument("--repeat", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=1)
-    ap.add_argument("--path", choices=["auto", "l1", "tma", "quad", "pair"], default="auto",
+    ap.add_argument("--path", choices=["auto", "l1", "tma", "quad", "pair", "ag2", "ag4"],
+                    default="auto",
                     help="forward-projector kernel")
     ap.add_argument("--projector", choices=["interpolated", "siddon"], default="interpolated")
     ap.add_argument("--brick", type=int, default=0,
@@ -57,7 +58,7 @@ def main():
     ang = synth.angles(a.angles)
     G = tigre.Geometry(geo, ang)
     tigre.tigre_geometry_set_forward_path(G.handle, {"auto": 0, "l1": 1, "tma": 2, "quad": 3,
-                                                     "pair": 4}[a.path])
+                                                     "pair": 4, "ag2": 5, "ag4": 6}[a.path])
     tigre.tigre_geometry_set_projector(G.handle, a.projector)
     tigre.tigre_geometry_set_brick(G.handle, a.brick)
     vol = torch.from_numpy(cached_phantom(a.n)).cuda().to(dt)

@@ -410,6 +410,7 @@ def tigre_backward_ooc(handle, proj: torch.Tensor, vol_host: torch.Tensor, angle
 
 
 FWD_AUTO, FWD_L1, FWD_TMA, FWD_QUAD, FWD_QUAD_PAIR = 0, 1, 2, 3, 4
+FWD_QUAD_ANGLES2, FWD_QUAD_ANGLES4 = 5, 6  # warps of 16 pixels x 2 angles / 8 x 4
 
 
 def tigre_fdk(handle, proj: torch.Tensor, vol: torch.Tensor, stream=None) -> None:

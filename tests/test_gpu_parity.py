@@ -225,21 +225,29 @@ def test_cgls_host_resident_equals_device(tigre):
 
 @pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16, torch.float16])
 def test_forward_paths_are_bitwise_identical(tigre, case, dtype):
-    """The scalar and quad (one or two samples at a time) gather kernels and
-    the shared-memory slab kernel add the same samples in the same order:
-    identical bits, no error flags."""
+    """The scalar and quad (one or two samples at a time; one, two or four
+    angles per warp) gather kernels and the shared-memory slab kernel add the
+    same samples in the same order: identical bits, no error flags."""
     geo, ang, vol = case
     with tigre.Geometry(geo, ang) as G:
         v = torch.from_numpy(vol).cuda().to(dtype)
         out = {}
-        for path in (tigre.FWD_L1, tigre.FWD_TMA, tigre.FWD_QUAD, tigre.FWD_QUAD_PAIR,
-                     tigre.FWD_AUTO):
+        paths = (tigre.FWD_L1, tigre.FWD_TMA, tigre.FWD_QUAD, tigre.FWD_QUAD_PAIR,
+                 tigre.FWD_QUAD_ANGLES2, tigre.FWD_QUAD_ANGLES4, tigre.FWD_AUTO)
+        for path in paths:
             tigre.tigre_geometry_set_forward_path(G.handle, path)
             out[path] = G.forward(v, dtype=torch.float32)
+        # a sub-range takes the one-angle-per-warp kernel on the angle-group paths
+        sub = {}
+        for path in (tigre.FWD_L1, tigre.FWD_QUAD_ANGLES4):
+            tigre.tigre_geometry_set_forward_path(G.handle, path)
+            sub[path] = G.forward(v, dtype=torch.float32, angle_begin=1, angle_count=len(ang) - 2)
         assert tigre.tigre_geometry_error_flags(G.handle) == 0
-    for path in (tigre.FWD_TMA, tigre.FWD_QUAD, tigre.FWD_QUAD_PAIR, tigre.FWD_AUTO):
+    for path in paths[1:]:
         assert torch.isfinite(out[path]).all()
         assert torch.equal(out[tigre.FWD_L1], out[path]), path
+    assert torch.equal(sub[tigre.FWD_L1], sub[tigre.FWD_QUAD_ANGLES4])
+    assert torch.equal(sub[tigre.FWD_L1], out[tigre.FWD_L1][1:len(ang) - 1])
 
 
 def test_forward_large_pixels_fall_back_and_match_oracle(tigre):
