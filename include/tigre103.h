@@ -198,6 +198,11 @@ TIGRE_API tigre_status tigre_backward_ooc(tigre_geometry_t geo, const float* pro
  *      allocated for the call), b, r, q on the device.
  * Both give the in-core iterates up to FP32 summation order. */
 #define TIGRE_OUT_OF_CORE 0x4u
+/* The initial guess is zero, so vol is not read: the library zeroes it on the
+ * device (a host-resident vol is not copied in), and CGLS starts from r = b
+ * as the method's initialisation states, without projecting x0 (the same
+ * bits as projecting a zero x0).  Not with TIGRE_OUT_OF_CORE. */
+#define TIGRE_X0_ZERO 0x8u
 
 typedef struct {
     int n_iter;                 /* iterations (default 10) */
@@ -216,7 +221,8 @@ typedef struct {
                                    the work completes on its stream (device buffers
                                    become valid once it drains), resid_hist is not
                                    filled and host-resident vol is not copied back. */
-    uint32_t flags;             /* TIGRE_HOST_RESIDENT, TIGRE_GRAPH */
+    uint32_t flags;             /* TIGRE_HOST_RESIDENT, TIGRE_GRAPH, TIGRE_OUT_OF_CORE,
+                                   TIGRE_X0_ZERO */
     void* cuda_stream;          /* stream for all work (NULL = default) */
 } tigre_solver_opts;
 

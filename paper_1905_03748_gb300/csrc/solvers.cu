@@ -75,7 +75,7 @@ tigre_status check_opts(const tigre_geometry* g, const tigre_solver_opts* o, con
     if (o->n_iter < 0) return fail(TIGRE_ERR_INVALID_ARG, "n_iter must be >= 0");
     if (!dtype_ok(o->storage)) return fail(TIGRE_ERR_INVALID_ARG, "bad storage dtype");
     if (!(std::isfinite(o->lambda))) return fail(TIGRE_ERR_INVALID_ARG, "lambda must be finite");
-    if (o->flags & ~(TIGRE_HOST_RESIDENT | TIGRE_GRAPH | TIGRE_OUT_OF_CORE))
+    if (o->flags & ~(TIGRE_HOST_RESIDENT | TIGRE_GRAPH | TIGRE_OUT_OF_CORE | TIGRE_X0_ZERO))
         return fail(TIGRE_ERR_INVALID_ARG, "unknown flags");
     return TIGRE_OK;
 }
@@ -111,9 +111,11 @@ tigre_status with_device_problem(tigre_geometry* g, const void* proj, void* vol,
     cudaStream_t st = (cudaStream_t)o->cuda_stream;
     Problem P{g, o, st, n_vox(g), n_pix(g), (int64_t)g->angles.size(), nullptr, nullptr,
               o->storage, dtype_size(o->storage)};
+    const bool x0_zero = (o->flags & TIGRE_X0_ZERO) != 0;
     if (!(o->flags & TIGRE_HOST_RESIDENT)) {
         P.b = proj;
         P.x = vol;
+        if (x0_zero) TIGRE_CUDA(cudaMemsetAsync(vol, 0, P.elem * (size_t)P.nvox, st));
         return body(P);
     }
     Scratch s(st);
@@ -123,7 +125,10 @@ tigre_status with_device_problem(tigre_geometry* g, const void* proj, void* vol,
     TIGRE_TRY(s.alloc(&dx, P.elem * (size_t)P.nvox));
     TIGRE_CUDA(cudaMemcpyAsync(db, proj, P.elem * (size_t)(P.npix * P.na),
                                cudaMemcpyHostToDevice, st));
-    TIGRE_CUDA(cudaMemcpyAsync(dx, vol, P.elem * (size_t)P.nvox, cudaMemcpyHostToDevice, st));
+    if (x0_zero)
+        TIGRE_CUDA(cudaMemsetAsync(dx, 0, P.elem * (size_t)P.nvox, st));
+    else
+        TIGRE_CUDA(cudaMemcpyAsync(dx, vol, P.elem * (size_t)P.nvox, cudaMemcpyHostToDevice, st));
     P.b = db;
     P.x = dx;
     TIGRE_TRY(body(P));
@@ -234,6 +239,7 @@ struct tigre_cgls_state {
     int done = 0;
     int cur = 0;
     bool graph = false;              // replay captured iteration pairs
+    bool x0_zero = false;            // x0 = 0: r = b without projecting x0
     cudaGraphExec_t exec[2] = {};    // two iterations, by starting gamma slot
 };
 
@@ -285,7 +291,11 @@ tigre_status cgls_init(tigre_cgls_state* S, int hist_cap)
 tigre_status cgls_start(tigre_cgls_state* S)
 {
     Scalars sc{S->sc};
-    TIGRE_TRY(forward_impl(S->g, S->x, S->dt, S->q, S->dt, 0, S->na, S->st));
+    // A zero x0 projects to exact zeros, so q = 0 gives r = b bit for bit.
+    if (S->x0_zero)
+        TIGRE_CUDA(cudaMemsetAsync(S->q, 0, dtype_size(S->dt) * (size_t)S->m, S->st));
+    else
+        TIGRE_TRY(forward_impl(S->g, S->x, S->dt, S->q, S->dt, 0, S->na, S->st));
     TIGRE_TRY(weighted_residual_dt(S->dt, S->b, S->q, nullptr, S->r, S->m, sc.partials(),
                                    sc.slot(3), S->st));
     TIGRE_TRY(backward_impl(S->g, S->r, S->dt, S->p, S->dt, 0, S->na, S->bw, 0, S->st));
@@ -382,6 +392,7 @@ tigre_status cgls_new_state(tigre_geometry* g, const void* b, void* x,
     S->dt = o->storage;
     S->b = b;
     S->x = x;
+    S->x0_zero = (o->flags & TIGRE_X0_ZERO) != 0;
     const tigre_status st = cgls_init(S, o->n_iter);
     if (st != TIGRE_OK) {
         cgls_release(S);
@@ -469,6 +480,9 @@ tigre_status tigre_cgls(tigre_geometry_t geo, const void* proj, void* vol,
 {
     if (opts && (opts->flags & TIGRE_OUT_OF_CORE)) {
         TIGRE_TRY(check_opts(geo, opts, proj, vol));
+        if (opts->flags & TIGRE_X0_ZERO)
+            return fail(TIGRE_ERR_UNSUPPORTED,
+                        "out-of-core CGLS reads x0 from the host volume; zero it there");
         if (opts->storage != TIGRE_F32)
             return fail(TIGRE_ERR_UNSUPPORTED, "out-of-core CGLS stores F32");
         if (opts->bp_weight == TIGRE_BP_EXACT_ADJOINT)
@@ -488,6 +502,9 @@ tigre_status tigre_cgls_begin(tigre_geometry_t geo, const void* proj, void* vol,
     TIGRE_TRY(check_opts(geo, opts, proj, vol));
     if (opts->flags & TIGRE_HOST_RESIDENT)
         return fail(TIGRE_ERR_UNSUPPORTED, "stepwise CGLS takes device buffers");
+    if (opts->flags & TIGRE_X0_ZERO)
+        TIGRE_CUDA(cudaMemsetAsync(vol, 0, dtype_size(opts->storage) * (size_t)n_vox(geo),
+                                   (cudaStream_t)opts->cuda_stream));
     return cgls_begin_device(geo, proj, vol, opts, out);
 }
 
@@ -543,6 +560,8 @@ tigre_status tigre_cgls_resume(tigre_geometry_t geo, const void* proj, void* vol
     TIGRE_TRY(check_opts(geo, opts, proj, vol));
     if (!r_host || !p_host || !std::isfinite(gamma))
         return fail(TIGRE_ERR_INVALID_ARG, "checkpoint buffers and a finite gamma are needed");
+    if (opts->flags & TIGRE_X0_ZERO)
+        return fail(TIGRE_ERR_INVALID_ARG, "a resumed CGLS continues from the checkpoint's x");
     if (opts->flags & TIGRE_HOST_RESIDENT)
         return fail(TIGRE_ERR_UNSUPPORTED, "stepwise CGLS takes device buffers");
     return cgls_resume_device(geo, proj, vol, r_host, p_host, gamma, opts, out);

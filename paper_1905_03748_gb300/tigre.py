@@ -267,18 +267,22 @@ def tigre_sart(handle, proj, vol, n_iter, subset_size=20, lam=1.0, nonneg=False,
 
 
 TIGRE_OUT_OF_CORE = 0x4
+TIGRE_X0_ZERO = 0x8
 
 
 def tigre_cgls(handle, proj, vol, n_iter, bp_weight="matched", stream=None,
                host=False, out_of_core=False, device_budget_bytes=0,
-               timeout_ms=0) -> np.ndarray:
+               timeout_ms=0, x0_zero=False) -> np.ndarray:
     """CGLS.  host=True stages host tensors through the device; with
     out_of_core=True proj and vol are host tensors, part of the state stays in
     host memory and the volume streams through the GPU in z-slabs; the
     placement and slab thickness follow from device_budget_bytes (0 =
-    automatic), see tigre_cgls_ooc_plan."""
+    automatic), see tigre_cgls_ooc_plan.  x0_zero=True: start from x = 0
+    without reading vol (r = b, no projection of x0, no upload of x0)."""
     o = _opts(n_iter, stream, bp_weight=bp_weight,
               device_budget_bytes=int(device_budget_bytes), timeout_ms=int(timeout_ms))
+    if x0_zero:
+        o.flags |= TIGRE_X0_ZERO
     if out_of_core:
         o.flags |= TIGRE_OUT_OF_CORE
         hist = np.zeros(max(n_iter, 1), dtype=np.float64)
@@ -304,13 +308,16 @@ def tigre_cgls_ooc_plan(handle, device_budget_bytes: int = 0) -> tuple:
 
 
 def tigre_cgls_begin(handle, proj, vol, n_iter_hint=16, bp_weight="matched", stream=None,
-                     graph=False):
+                     graph=False, x0_zero=False):
     """Stepwise CGLS; graph=True replays captured iteration pairs as CUDA
     graphs (needs a non-default stream).  proj and vol share one storage
-    dtype (float32, bfloat16 or float16); arithmetic is FP32, scalars FP64."""
+    dtype (float32, bfloat16 or float16); arithmetic is FP32, scalars FP64.
+    x0_zero=True zeroes vol and starts from r = b without projecting it."""
     o = _opts(n_iter_hint, stream, bp_weight=bp_weight)
     if graph:
         o.flags |= TIGRE_GRAPH
+    if x0_zero:
+        o.flags |= TIGRE_X0_ZERO
     pp, pt = _dev(proj, "proj")
     vp, vt = _dev(vol, "vol")
     if pt != vt:

@@ -30,6 +30,15 @@ def test_header_declares_the_boundary():
         assert n in names
 
 
+def test_binding_flag_values_match_header():
+    from paper_1905_03748_gb300 import tigre
+    text = open(HEADER).read()
+    flags = dict(re.findall(r"#define\s+(TIGRE_[A-Z0-9_]+)\s+(0x[0-9a-fA-F]+)u", text))
+    assert {"TIGRE_HOST_RESIDENT", "TIGRE_GRAPH", "TIGRE_OUT_OF_CORE", "TIGRE_X0_ZERO"} <= set(flags)
+    for name, value in flags.items():
+        assert getattr(tigre, name) == int(value, 16), name
+
+
 def test_library_exports_every_declared_symbol(lib):
     for name in declared_functions():
         assert hasattr(lib, name), name

@@ -74,3 +74,45 @@ def test_resume_rejects_bad_checkpoints(tigre):
             tigre.tigre_cgls_resume(G.handle, b, x, r.bfloat16(), p, 1.0)
         with pytest.raises(ValueError):
             tigre.tigre_cgls_resume(G.handle, b, x, r[:1], p, 1.0)
+
+
+@pytest.mark.parametrize("host", [False, True])
+def test_x0_zero_flag_gives_the_zero_start_bits(tigre, host):
+    """TIGRE_X0_ZERO: vol is not read (here it holds garbage), q = 0 replaces
+    the projection of x0; the iterates and residuals are the bits of a run
+    from an explicit zero x0."""
+    geo, ang, vol = case()
+    with tigre.Geometry(geo, ang) as G:
+        b = G.forward(torch.from_numpy(vol).cuda())
+        dev = "cpu" if host else "cuda"
+        bb = b.cpu() if host else b
+        x_ref = torch.zeros(G.vol_shape, device=dev)
+        h_ref = tigre.tigre_cgls(G.handle, bb, x_ref, 5, host=host)
+        x = torch.full(G.vol_shape, float("nan"), device=dev)
+        h = tigre.tigre_cgls(G.handle, bb, x, 5, host=host, x0_zero=True)
+        torch.cuda.synchronize()
+    np.testing.assert_array_equal(h, h_ref)
+    assert torch.equal(x.cpu(), x_ref.cpu())
+
+
+def test_x0_zero_stepwise_and_refusals(tigre):
+    geo, ang, vol = case()
+    with tigre.Geometry(geo, ang) as G:
+        b = G.forward(torch.from_numpy(vol).cuda())
+        x_ref = torch.zeros(G.vol_shape, device="cuda")
+        st = tigre.tigre_cgls_begin(G.handle, b, x_ref)
+        tigre.tigre_cgls_iterate(st, 3)
+        h_ref = tigre.tigre_cgls_history(st, 3)
+        tigre.tigre_cgls_end(st)
+        x = torch.full(G.vol_shape, 7.0, device="cuda")
+        st = tigre.tigre_cgls_begin(G.handle, b, x, x0_zero=True)
+        tigre.tigre_cgls_iterate(st, 3)
+        h = tigre.tigre_cgls_history(st, 3)
+        tigre.tigre_cgls_end(st)
+        torch.cuda.synchronize()
+        assert torch.equal(x, x_ref)
+        np.testing.assert_array_equal(h, h_ref)
+        with pytest.raises(tigre.TigreError):  # out of core reads x0 from the host volume
+            tigre.tigre_cgls(G.handle, b.cpu(), torch.zeros(G.vol_shape), 1, out_of_core=True,
+                             x0_zero=True)
+
