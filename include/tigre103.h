@@ -72,7 +72,7 @@ typedef enum {
     TIGRE_ERR_OOM = 2,         /* device or pinned allocation failed / over budget */
     TIGRE_ERR_CUDA = 3,        /* CUDA runtime error; see tigre_last_error() */
     TIGRE_ERR_TIMEOUT = 4,     /* a host wait exceeded opts.timeout_ms */
-    TIGRE_ERR_UNSUPPORTED = 5  /* valid request this build does not implement */
+    TIGRE_ERR_UNSUPPORTED = 5  /* valid request the library does not implement */
 } tigre_status;
 
 /* Storage type of a volume / projection buffer.  Arithmetic is FP32 along
