@@ -383,6 +383,21 @@ TIGRE_API tigre_status tigre_geometry_set_brick(tigre_geometry_t geo, int64_t ed
  * path 4. */
 TIGRE_API tigre_status tigre_geometry_set_forward_path(tigre_geometry_t geo, int path);
 
+/* The angle groups the forward projector's paths 5 / 6 (and path 0 when it
+ * pairs angles) read, computed on the host (no device needed): size (2 or 4)
+ * angle indices per group, each group of one memory layout (|cos| > |sin| or
+ * not) and one march direction, neighbours in angle, -1 filling a short
+ * group; n_groups groups.  drift = the median angle gap inside pairs times
+ * the largest distance of a voxel from the rotation axis, in voxels;
+ * auto_pairs = 1 when the automatic path pairs angles (drift <= 16).  table
+ * may be NULL (sizes only); otherwise it holds capacity ints, at least
+ * n_groups * size, or the call fails with INVALID_ARG. */
+TIGRE_API tigre_status tigre_forward_angle_groups(const tigre_geometry_desc* desc,
+                                                  const double* angles, int64_t n_angles,
+                                                  int size, int* table, int64_t capacity,
+                                                  int64_t* n_groups, double* drift,
+                                                  int* auto_pairs);
+
 /* Error bits raised by kernels of this handle (1 = a bounded wait timed out,
  * 2 = a slab did not fit its staging box, 4 = rays of one block ran opposite
  * ways; the affected outputs are NaN).  Synchronous; clear != 0 resets. */

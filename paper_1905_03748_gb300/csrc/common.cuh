@@ -109,6 +109,14 @@ struct DeviceBuffer {
 constexpr int64_t kBrickDefault = 512;  // x-y brick edge of out-of-core slab projections
 constexpr double kPairDriftVoxels = 16.0;  // automatic 2-angle warps up to this ray drift
 
+// Host-side angle groups of the forward projector (sizes 2 and 4).
+struct AngleGroups {
+    std::vector<int> table[2];  // group size 2, 4: angle indices, -1 filling short groups
+    double drift = 0.0;         // voxels between the rays of one pixel at paired angles
+    bool auto_pairs = false;    // the automatic path uses 2-angle warps
+};
+int angle_layout(double t);
+
 // Per-angle parameters of the forward projector, expressed in the index
 // coordinates of the padded volume layout the angle uses.  "f", "m", "s" are
 // the fastest, middle and slowest memory axes of that layout.

@@ -197,6 +197,61 @@ bool detector_row_range(const tigre_geometry_desc& d, double za, double zb, doub
     return true;
 }
 
+// Memory layout an angle's forward projection reads: rays of one detector
+// row spread along e_u = (-sin, cos, 0), so the layout whose fastest axis is
+// the one e_u is closest to (1: y fastest, when |cos| > |sin|).
+int angle_layout(double t) { return std::fabs(std::cos(t)) > std::fabs(std::sin(t)) ? 1 : 0; }
+
+// Angle groups for the angle-interleaved forward kernel.  Rays through one
+// pixel at neighbouring angles pass within a few voxels of each other, so a
+// warp of (32 / size) pixels x size angles gathers from fewer cache lines
+// than 32 pixels of one angle.  A group holds angles of one layout and one
+// march direction (the sign of the ray along the layout's depth axis),
+// neighbours in angle; -1 fills a short group.
+AngleGroups build_angle_groups(const tigre_geometry_desc& d, const double* angles, int64_t na)
+{
+    AngleGroups out;
+    std::vector<int> cls[4];
+    const double pi = std::acos(-1.0);
+    const double centre[4] = {1.5 * pi, 0.5 * pi, pi, 0.0};
+    for (int64_t a = 0; a < na; ++a) {
+        const double t = angles[a];
+        const int l = angle_layout(t);
+        const double main = l ? std::cos(t) : std::sin(t);
+        cls[l * 2 + (main > 0.0 ? 1 : 0)].push_back((int)a);
+    }
+    for (int k = 0; k < 4; ++k)
+        std::stable_sort(cls[k].begin(), cls[k].end(), [&](int i, int j) {
+            return std::remainder(angles[i] - centre[k], 2.0 * pi) <
+                   std::remainder(angles[j] - centre[k], 2.0 * pi);
+        });
+    // Median angular gap inside pairs x the largest distance of a voxel from
+    // the rotation axis = how far apart (in voxels) the rays of one pixel at
+    // paired angles get.  Pairs paid at 6.3 voxels (512^3 x 360: 3.8 %,
+    // 1024^3 x 720: 3.9 %) and 12.6 (1024^3 x 360: 3.3 %); groups of four
+    // lost 9 % at 50 (1024^3 x 90).
+    std::vector<double> gaps;
+    for (const std::vector<int>& v : cls)
+        for (size_t i = 0; i + 1 < v.size(); i += 2)
+            gaps.push_back(std::fabs(std::remainder(angles[v[i + 1]] - angles[v[i]], 2.0 * pi)));
+    if (!gaps.empty()) {
+        std::nth_element(gaps.begin(), gaps.begin() + gaps.size() / 2, gaps.end());
+        const double wx = 0.5 * (double)d.n_voxel[0] * d.d_voxel[0] + std::fabs(d.off_origin[0]);
+        const double wy = 0.5 * (double)d.n_voxel[1] * d.d_voxel[1] + std::fabs(d.off_origin[1]);
+        out.drift = gaps[gaps.size() / 2] * std::sqrt(wx * wx + wy * wy) /
+                    std::min(d.d_voxel[0], d.d_voxel[1]);
+        out.auto_pairs = out.drift <= kPairDriftVoxels;
+    }
+    for (int gi = 0; gi < 2; ++gi) {
+        const size_t size = gi ? 4 : 2;
+        for (const std::vector<int>& v : cls)
+            for (size_t i = 0; i < v.size(); i += size)
+                for (size_t j = 0; j < size; ++j)
+                    out.table[gi].push_back(i + j < v.size() ? v[i + j] : -1);
+    }
+    return out;
+}
+
 tigre_status upload_params(tigre_geometry* g)
 {
     const tigre_geometry_desc& d = g->desc;
@@ -223,7 +278,7 @@ tigre_status upload_params(tigre_geometry* g)
         }
         // Rays of one detector row spread along e_u: choose the memory layout
         // whose fastest axis is the one e_u is closest to.
-        const int layout = std::fabs(c) > std::fabs(s) ? 1 : 0;
+        const int layout = angle_layout(t);
         const int perm[3] = {layout ? 1 : 0, layout ? 0 : 1, 2};
         FwdAngle& f = fwd[(size_t)a];
         std::memset(&f, 0, sizeof(f));
@@ -246,53 +301,12 @@ tigre_status upload_params(tigre_geometry* g)
     TIGRE_TRY(g->angle_order.ensure(sizeof(int) * (size_t)na));
     TIGRE_CUDA(cudaMemcpy(g->angle_order.ptr, order.data(), sizeof(int) * (size_t)na,
                           cudaMemcpyHostToDevice));
-    // Angle groups for the angle-interleaved forward kernel.  Rays through
-    // one pixel at neighbouring angles pass within a few voxels of each
-    // other, so a warp of (32 / size) pixels x size angles gathers from fewer
-    // cache lines than 32 pixels of one angle.  A group holds angles of one
-    // layout and one march direction (the sign of the ray along the layout's
-    // depth axis), neighbours in angle; -1 fills a short group.
     {
-        std::vector<int> cls[4];
-        const double pi = std::acos(-1.0);
-        const double centre[4] = {1.5 * pi, 0.5 * pi, pi, 0.0};
-        for (int64_t a = 0; a < na; ++a) {
-            const double t = g->angles[(size_t)a];
-            const int l = g->layout[(size_t)a];
-            const double main = l ? std::cos(t) : std::sin(t);
-            cls[l * 2 + (main > 0.0 ? 1 : 0)].push_back((int)a);
-        }
-        for (int k = 0; k < 4; ++k)
-            std::stable_sort(cls[k].begin(), cls[k].end(), [&](int i, int j) {
-                return std::remainder(g->angles[(size_t)i] - centre[k], 2.0 * pi) <
-                       std::remainder(g->angles[(size_t)j] - centre[k], 2.0 * pi);
-            });
-        // Median angular gap inside pairs x the largest distance of a voxel from
-        // the rotation axis = how far apart (in voxels) the rays of one pixel
-        // at paired angles get.  Pairs paid at 6.3 voxels (512^3 x 360: 3.8 %,
-        // 1024^3 x 720: 3.9 %) and 12.6 (1024^3 x 360: 3.3 %); groups of four
-        // lost 9 % at 50 (1024^3 x 90).
-        std::vector<double> gaps;
-        for (const std::vector<int>& v : cls)
-            for (size_t i = 0; i + 1 < v.size(); i += 2)
-                gaps.push_back(std::fabs(std::remainder(
-                    g->angles[(size_t)v[i + 1]] - g->angles[(size_t)v[i]], 2.0 * pi)));
-        g->auto_angle_group = 1;
-        if (!gaps.empty()) {
-            std::nth_element(gaps.begin(), gaps.begin() + gaps.size() / 2, gaps.end());
-            const double wx = 0.5 * (double)d.n_voxel[0] * d.d_voxel[0] + std::fabs(d.off_origin[0]);
-            const double wy = 0.5 * (double)d.n_voxel[1] * d.d_voxel[1] + std::fabs(d.off_origin[1]);
-            const double drift = gaps[gaps.size() / 2] * std::sqrt(wx * wx + wy * wy) /
-                                 std::min(d.d_voxel[0], d.d_voxel[1]);
-            if (drift <= kPairDriftVoxels) g->auto_angle_group = 2;
-        }
+        const AngleGroups ag = build_angle_groups(d, g->angles.data(), na);
+        g->auto_angle_group = ag.auto_pairs ? 2 : 1;
         for (int gi = 0; gi < 2; ++gi) {
-            const size_t size = gi ? 4 : 2;
-            std::vector<int> tab;
-            for (const std::vector<int>& v : cls)
-                for (size_t i = 0; i < v.size(); i += size)
-                    for (size_t j = 0; j < size; ++j) tab.push_back(i + j < v.size() ? v[i + j] : -1);
-            g->n_groups[gi] = (int64_t)(tab.size() / size);
+            const std::vector<int>& tab = ag.table[gi];
+            g->n_groups[gi] = (int64_t)(tab.size() / (gi ? 4 : 2));
             TIGRE_TRY(g->angle_groups[gi].ensure(sizeof(int) * std::max<size_t>(tab.size(), 1)));
             if (!tab.empty())
                 TIGRE_CUDA(cudaMemcpy(g->angle_groups[gi].ptr, tab.data(), sizeof(int) * tab.size(),
@@ -402,3 +416,33 @@ tigre_status tigre_solver_opts_default(tigre_solver_opts* o)
 }
 
 }  // extern "C"
+
+extern "C" tigre_status tigre_forward_angle_groups(const tigre_geometry_desc* desc,
+                                                   const double* angles, int64_t n_angles,
+                                                   int size, int* table, int64_t capacity,
+                                                   int64_t* n_groups, double* drift,
+                                                   int* auto_pairs)
+{
+    using namespace tigre;
+    if (!desc || !angles || n_angles <= 0 || !n_groups || !drift || !auto_pairs)
+        return fail(TIGRE_ERR_INVALID_ARG, "null argument or no angles");
+    if (size != 2 && size != 4) return fail(TIGRE_ERR_INVALID_ARG, "group size must be 2 or 4");
+    for (int k = 0; k < 3; ++k)
+        if (desc->n_voxel[k] <= 0 || !(desc->d_voxel[k] > 0.0) || !std::isfinite(desc->d_voxel[k]) ||
+            !std::isfinite(desc->off_origin[k]))
+            return fail(TIGRE_ERR_INVALID_ARG, "voxel counts and sizes must be > 0 and finite");
+    for (int64_t a = 0; a < n_angles; ++a)
+        if (!std::isfinite(angles[a])) return fail(TIGRE_ERR_INVALID_ARG, "angles must be finite");
+    const AngleGroups ag = build_angle_groups(*desc, angles, n_angles);
+    const std::vector<int>& tab = ag.table[size == 4 ? 1 : 0];
+    *n_groups = (int64_t)(tab.size() / (size_t)size);
+    *drift = ag.drift;
+    *auto_pairs = ag.auto_pairs ? 1 : 0;
+    if (table) {
+        if (capacity < (int64_t)tab.size())
+            return fail(TIGRE_ERR_INVALID_ARG, "table capacity below n_groups * size");
+        std::copy(tab.begin(), tab.end(), table);
+    }
+    return TIGRE_OK;
+}
+

@@ -35,7 +35,7 @@ EXPORTED = ["tigre_geometry_create", "tigre_geometry_destroy", "tigre_forward", 
             "tigre_sart",
             "tigre_cgls", "tigre_cgls_begin", "tigre_cgls_iterate", "tigre_cgls_history",
             "tigre_cgls_end", "tigre_cgls_save", "tigre_cgls_resume", "tigre_forward_samples", "tigre_forward_ooc", "tigre_backward_ooc",
-            "tigre_cgls_ooc_plan", "tigre_geometry_set_forward_path",
+            "tigre_cgls_ooc_plan", "tigre_geometry_set_forward_path", "tigre_forward_angle_groups",
             "tigre_geometry_set_projector", "tigre_fdk", "tigre_rof_denoise",
             "tigre_geometry_set_brick", "tigre_tv_step_ooc", "tigre_set_allocator",
             "tigre_geometry_error_flags", "tigre_profile_enable",
@@ -88,6 +88,9 @@ _sigs = {
     "tigre_forward_ooc": [_P, _P, _P, _I64, _I64, _I64, _P],
     "tigre_backward_ooc": [_P, _P, ctypes.c_int, _P, _I64, _I64, ctypes.c_int, _I64, _I64, _P],
     "tigre_cgls_ooc_plan": [_P, _I64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_I64)],
+    "tigre_forward_angle_groups": [ctypes.POINTER(tigre_geometry_desc), _P, _I64, ctypes.c_int, _P,
+                                   _I64, ctypes.POINTER(_I64), ctypes.POINTER(ctypes.c_double),
+                                   ctypes.POINTER(ctypes.c_int)],
     "tigre_geometry_set_forward_path": [_P, ctypes.c_int],
     "tigre_geometry_set_projector": [_P, ctypes.c_int],
     "tigre_geometry_set_brick": [_P, _I64],
@@ -418,6 +421,24 @@ def tigre_backward_ooc(handle, proj: torch.Tensor, vol_host: torch.Tensor, angle
 
 FWD_AUTO, FWD_L1, FWD_TMA, FWD_QUAD, FWD_QUAD_PAIR = 0, 1, 2, 3, 4
 FWD_QUAD_ANGLES2, FWD_QUAD_ANGLES4 = 5, 6  # warps of 16 pixels x 2 angles / 8 x 4
+
+
+def tigre_forward_angle_groups(geo: dict, angles, size: int = 2):
+    """The forward projector's angle groups (host only): (table of shape
+    (n_groups, size) with -1 filling short groups, drift in voxels, whether
+    the automatic path pairs angles)."""
+    ang = np.ascontiguousarray(angles, dtype=np.float64)
+    d = make_desc(geo)
+    ng, drift, auto = _I64(), ctypes.c_double(), ctypes.c_int()
+    _check(_lib.tigre_forward_angle_groups(ctypes.byref(d), ang.ctypes.data_as(_P), ang.size,
+                                           int(size), None, 0, ctypes.byref(ng),
+                                           ctypes.byref(drift), ctypes.byref(auto)))
+    tab = np.zeros(ng.value * size, dtype=np.int32)
+    _check(_lib.tigre_forward_angle_groups(ctypes.byref(d), ang.ctypes.data_as(_P), ang.size,
+                                           int(size), tab.ctypes.data_as(_P), tab.size,
+                                           ctypes.byref(ng), ctypes.byref(drift),
+                                           ctypes.byref(auto)))
+    return tab.reshape(-1, size), float(drift.value), bool(auto.value)
 
 
 def tigre_fdk(handle, proj: torch.Tensor, vol: torch.Tensor, stream=None) -> None:
