@@ -159,6 +159,13 @@ TIGRE_API tigre_status tigre_tv_step_noalloc(const int64_t n_voxel[3], void* vol
  * one-plane slabs.  Queries free memory only; allocates nothing. */
 TIGRE_API tigre_status tigre_cgls_ooc_plan(tigre_geometry_t geo, int64_t device_budget_bytes,
                                            int* placement, int64_t* slab_planes);
+/* The same decision from a geometry description and its angles, on the host
+ * alone (no device, no handle): device_budget_bytes must be > 0.  Errors as
+ * tigre_geometry_create for the description, TIGRE_ERR_OOM as above. */
+TIGRE_API tigre_status tigre_cgls_ooc_plan_desc(const tigre_geometry_desc* desc,
+                                                const double* angles, int64_t n_angles,
+                                                int64_t device_budget_bytes, int* placement,
+                                                int64_t* slab_planes);
 
 /* Out-of-core forward projection (paper Alg. 1 on one GPU): vol_host is a
  * HOST pointer (F32, (nz, ny, nx)), streamed to the device in axial slabs of

@@ -116,6 +116,8 @@ struct AngleGroups {
     bool auto_pairs = false;    // the automatic path uses 2-angle warps
 };
 int angle_layout(double t);
+// Checks of a geometry description and its angles (host only).
+tigre_status validate_desc(const tigre_geometry_desc* d, const double* angles, int64_t na);
 
 // Per-angle parameters of the forward projector, expressed in the index
 // coordinates of the padded volume layout the angle uses.  "f", "m", "s" are

@@ -116,7 +116,7 @@ void DeviceBuffer::release()
 
 static bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
 
-static tigre_status validate(const tigre_geometry_desc* d, const double* angles, int64_t na)
+tigre_status validate_desc(const tigre_geometry_desc* d, const double* angles, int64_t na)
 {
     if (!d || !angles) return fail(TIGRE_ERR_INVALID_ARG, "null geometry or angles");
     if (na <= 0) return fail(TIGRE_ERR_INVALID_ARG, "n_angles must be > 0");
@@ -336,7 +336,7 @@ tigre_status tigre_geometry_create(const tigre_geometry_desc* desc, const double
 {
     if (!out) return fail(TIGRE_ERR_INVALID_ARG, "null output handle pointer");
     *out = nullptr;
-    TIGRE_TRY(validate(desc, angles, n_angles));
+    TIGRE_TRY(validate_desc(desc, angles, n_angles));
     tigre_geometry* g = new (std::nothrow) tigre_geometry();
     if (!g) return fail(TIGRE_ERR_OOM, "host allocation failed");
     handle_created();

@@ -744,6 +744,30 @@ extern "C" tigre_status tigre_cgls_ooc_plan(tigre_geometry_t geo, int64_t device
     return TIGRE_OK;
 }
 
+extern "C" tigre_status tigre_cgls_ooc_plan_desc(const tigre_geometry_desc* desc,
+                                                 const double* angles, int64_t n_angles,
+                                                 int64_t device_budget_bytes, int* placement,
+                                                 int64_t* slab_planes)
+{
+    using namespace tigre;
+    if (!placement || !slab_planes) return fail(TIGRE_ERR_INVALID_ARG, "null output");
+    if (device_budget_bytes <= 0)
+        return fail(TIGRE_ERR_INVALID_ARG, "planning without a device needs an explicit budget");
+    TIGRE_TRY(validate_desc(desc, angles, n_angles));
+    // A host-only geometry: the planner reads the description, the number of
+    // angles and the memory layouts they use; no device state is made.
+    tigre_geometry g;
+    g.desc = *desc;
+    g.angles.assign(angles, angles + n_angles);
+    g.layout.resize((size_t)n_angles);
+    for (int64_t a = 0; a < n_angles; ++a) g.layout[(size_t)a] = angle_layout(angles[a]);
+    OocPlan plan;
+    TIGRE_TRY(plan_ooc(&g, device_budget_bytes, &plan));
+    *placement = plan.placement;
+    *slab_planes = plan.slab;
+    return TIGRE_OK;
+}
+
 // ------------------------------------------------ out-of-core TV (halo buffers)
 //
 // The paper's splitting of a regulariser (Sec. 2.3) on one GPU whose volume

@@ -36,6 +36,7 @@ EXPORTED = ["tigre_geometry_create", "tigre_geometry_destroy", "tigre_forward", 
             "tigre_cgls", "tigre_cgls_begin", "tigre_cgls_iterate", "tigre_cgls_history",
             "tigre_cgls_end", "tigre_cgls_save", "tigre_cgls_resume", "tigre_forward_samples", "tigre_forward_ooc", "tigre_backward_ooc",
             "tigre_cgls_ooc_plan", "tigre_geometry_set_forward_path", "tigre_forward_angle_groups",
+            "tigre_cgls_ooc_plan_desc",
             "tigre_geometry_set_projector", "tigre_fdk", "tigre_rof_denoise",
             "tigre_geometry_set_brick", "tigre_tv_step_ooc", "tigre_set_allocator",
             "tigre_geometry_error_flags", "tigre_profile_enable",
@@ -88,6 +89,8 @@ _sigs = {
     "tigre_forward_ooc": [_P, _P, _P, _I64, _I64, _I64, _P],
     "tigre_backward_ooc": [_P, _P, ctypes.c_int, _P, _I64, _I64, ctypes.c_int, _I64, _I64, _P],
     "tigre_cgls_ooc_plan": [_P, _I64, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_I64)],
+    "tigre_cgls_ooc_plan_desc": [ctypes.POINTER(tigre_geometry_desc), _P, _I64, _I64,
+                                 ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_I64)],
     "tigre_forward_angle_groups": [ctypes.POINTER(tigre_geometry_desc), _P, _I64, ctypes.c_int, _P,
                                    _I64, ctypes.POINTER(_I64), ctypes.POINTER(ctypes.c_double),
                                    ctypes.POINTER(ctypes.c_int)],
@@ -307,6 +310,19 @@ def tigre_cgls_ooc_plan(handle, device_budget_bytes: int = 0) -> tuple:
     sl = _I64()
     _check(_lib.tigre_cgls_ooc_plan(handle, int(device_budget_bytes), ctypes.byref(pl),
                                     ctypes.byref(sl)))
+    return int(pl.value), int(sl.value)
+
+
+def tigre_cgls_ooc_plan_desc(geo: dict, angles, device_budget_bytes: int) -> tuple:
+    """tigre_cgls_ooc_plan from a geometry dict and angles, host only (an
+    explicit budget in bytes): (placement, slab planes)."""
+    ang = np.ascontiguousarray(angles, dtype=np.float64)
+    d = make_desc(geo)
+    pl = ctypes.c_int()
+    sl = _I64()
+    _check(_lib.tigre_cgls_ooc_plan_desc(ctypes.byref(d), ang.ctypes.data_as(_P), ang.size,
+                                         int(device_budget_bytes), ctypes.byref(pl),
+                                         ctypes.byref(sl)))
     return int(pl.value), int(sl.value)
 
 

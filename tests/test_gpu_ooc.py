@@ -212,3 +212,12 @@ def test_tv_out_of_core_rejects_a_buffer_deeper_than_the_slab(tigre):
     h = torch.zeros((8, 4, 4))
     with pytest.raises(tigre.TigreError):
         tigre.tigre_tv_step_ooc(h, 2, 0.1, slab_planes=2, halo_depth=3)
+
+
+def test_plan_from_a_description_equals_the_handle_plan(tigre):
+    """The host-only planner and the handle's planner take the same decision."""
+    geo, ang = synth.workload("cgls_512")
+    with tigre.Geometry(geo, ang) as G:
+        for budget in (40 * 10 ** 9, 2 * 10 ** 9, 1_500_000_000, 1_300_000_000):
+            assert (tigre.tigre_cgls_ooc_plan(G.handle, budget)
+                    == tigre.tigre_cgls_ooc_plan_desc(geo, ang, budget))

@@ -1,0 +1,64 @@
+"""Host logic of the out-of-core CGLS planner (no GPU): the placement and
+slab thickness a device budget gives.  Placement 2 keeps x, r and q on the
+device (at least nvox + 2 m floats), placement 1 keeps b, r and q (at least
+3 m floats); slabs fill the backprojector's 16-voxel z chunks; less memory
+never gives a larger plan."""
+import numpy as np
+import pytest
+
+from paper_1905_03748_gb300 import synth
+
+
+@pytest.fixture(scope="module")
+def tigre():
+    from paper_1905_03748_gb300 import tigre as t
+    return t
+
+
+def sizes(geo, ang):
+    nvox = int(np.prod(geo["n_voxel"]))
+    m = int(np.prod(geo["n_det"])) * len(ang)
+    return nvox, m
+
+
+@pytest.mark.parametrize("name", ["cgls_512", "ooc_3072"])
+def test_plans_shrink_with_the_budget(tigre, name):
+    geo, ang = synth.workload(name)
+    nvox, m = sizes(geo, ang)
+    nz = geo["n_voxel"][2]
+    top = 4 * (nvox + 3 * m) * 2
+    prev = (3, 10 ** 9)
+    saw = set()
+    for budget in np.geomspace(top, 4 * m, 60).astype(np.int64):
+        try:
+            pl, slab = tigre.tigre_cgls_ooc_plan_desc(geo, ang, int(budget))
+        except tigre.TigreError:
+            assert budget < 4 * 3 * m * 1.05  # only below about three projection sets
+            continue
+        saw.add(pl)
+        assert (pl, slab) <= prev  # lexicographic: placement 2 before 1, then thicker slabs
+        prev = (pl, slab)
+        assert 1 <= slab <= min(nz, 256)
+        assert slab < 16 or slab % 16 == 0 or slab >= nz
+        if pl == 2:
+            assert budget >= 4 * (nvox + 2 * m)
+        else:
+            assert budget >= 4 * 3 * m
+    assert saw == {1, 2}
+
+
+def test_the_3072_run_fits_placement_2(tigre):
+    """3072^3 x 1500 on a 297 GB device: x, r, q stay in HBM."""
+    geo, ang = synth.workload("ooc_3072")
+    pl, slab = tigre.tigre_cgls_ooc_plan_desc(geo, ang, 297 * 10 ** 9)
+    assert pl == 2 and slab % 16 == 0
+
+
+def test_refusals(tigre):
+    geo, ang = synth.workload("cgls_512")
+    with pytest.raises(tigre.TigreError):
+        tigre.tigre_cgls_ooc_plan_desc(geo, ang, 0)  # no device to ask for its free memory
+    with pytest.raises(tigre.TigreError):
+        tigre.tigre_cgls_ooc_plan_desc(geo, ang, 10 ** 6)  # below three projection sets
+    with pytest.raises(tigre.TigreError):
+        tigre.tigre_cgls_ooc_plan_desc(dict(geo, DSD=500.0), ang, 10 ** 10)  # DSD < DSO
