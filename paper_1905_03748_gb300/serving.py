@@ -81,6 +81,26 @@ def work_estimate(req: Request) -> float:
     return float(np.prod(req.geo["n_voxel"])) * len(req.angles) * (req.n_iter + 1)
 
 
+def admit(queue: list[Request], n_active: int, used: int, max_slots: int, budget: int,
+          policy: str = "fifo") -> list[Request]:
+    """Take from `queue` (in place) the requests to admit now, in order: while
+    a slot is free and the next request's footprint fits the HBM left (a
+    request that fits nothing is admitted alone, when nothing else is
+    resident).  fifo keeps arrival order (a large request at the head waits
+    and holds the ones behind it); sjf first sorts the queue by estimated
+    work."""
+    if policy == "sjf":
+        queue.sort(key=lambda r: (work_estimate(r), r.arrival, r.rid))
+    out: list[Request] = []
+    while queue and n_active + len(out) < max_slots:
+        need = request_bytes(queue[0])
+        if used + need > budget and n_active + len(out) > 0:
+            break
+        out.append(queue.pop(0))
+        used += need
+    return out
+
+
 @dataclass
 class _Slot:
     req: Request
@@ -120,9 +140,9 @@ class Server:
             G = tigre.Geometry(req.geo, req.angles)
             dt = storage_dtype(req)
             b = req.proj.to(self.device, dtype=dt, non_blocking=True)
-            x = torch.zeros(G.vol_shape, device=self.device, dtype=dt)
+            x = torch.empty(G.vol_shape, device=self.device, dtype=dt)  # zeroed by the library
             state = tigre.tigre_cgls_begin(G.handle, b, x, n_iter_hint=req.n_iter,
-                                           stream=stream, graph=self.graph)
+                                           stream=stream, graph=self.graph, x0_zero=True)
         return _Slot(req, G, stream, b, x, state, 0, now, bytes=request_bytes(req))
 
     def _finish(self, s: _Slot, now: float) -> Result:
@@ -147,13 +167,8 @@ class Server:
                 queue.append(pending.pop(0))
             # Admission as slots and memory free up (arrival order, or least
             # work first).
-            if self.policy == "sjf":
-                queue.sort(key=lambda r: (work_estimate(r), r.arrival))
-            while queue and len(active) < self.max_slots:
-                need = request_bytes(queue[0])
-                if used + need > self.hbm_budget and active:
-                    break
-                req = queue.pop(0)
+            for req in admit(queue, len(active), used, self.max_slots, self.hbm_budget,
+                             self.policy):
                 slot = self._admit(req, time.perf_counter() - t0)
                 used += slot.bytes
                 active.append(slot)
@@ -196,8 +211,8 @@ def run_plain(requests: list[Request], realtime: bool = True,
         with tigre.Geometry(req.geo, req.angles) as G:
             dt = storage_dtype(req)
             b = req.proj.to(dev, dtype=dt)
-            x = torch.zeros(G.vol_shape, device=dev, dtype=dt)
-            resid = tigre.tigre_cgls(G.handle, b, x, req.n_iter)
+            x = torch.empty(G.vol_shape, device=dev, dtype=dt)  # zeroed by the library
+            resid = tigre.tigre_cgls(G.handle, b, x, req.n_iter, x0_zero=True)
             xh = x.float().cpu()
         results.append(Result(req.rid, xh, resid, req.arrival, admitted,
                               time.perf_counter() - t0))
