@@ -1,0 +1,53 @@
+"""The one worked problem the paper prints sizes for (Sec. 4, coffee bean,
+CGLS; tests/golden/sec4_coffee_bean_cgls.txt): F32 storage gives its 29 GB
+of projections and 40 GB of image, and the out-of-core planner places that
+problem on one GB300 with x, r and q in HBM.  On one of the paper's 11 GiB
+GPUs it is refused: the planner's placements keep three projection sets on
+the device, where the paper also streams the projections in angle chunks."""
+import os
+
+import numpy as np
+import pytest
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "sec4_coffee_bean_cgls.txt")
+
+
+def golden():
+    out = {}
+    for line in open(GOLDEN):
+        line = line.split("#")[0].strip()
+        if line:
+            k, v = (s.strip() for s in line.split("="))
+            out[k] = [float(x) for x in v.split()]
+    return out
+
+
+def coffee_geometry(g):
+    nx, ny, nz = (int(v) for v in g["image_voxels"])
+    d = g["voxel_um"][0] * 1e-3
+    dso = g["source_object_mm"][0]
+    mag = g["magnification"][0]
+    nu, nv = (int(v) for v in g["detector_pixels"])
+    return {"DSO": dso, "DSD": dso * mag, "n_voxel": (nx, ny, nz), "d_voxel": (d, d, d),
+            "off_origin": (0.0, 0.0, 0.0), "n_det": (nu, nv), "d_det": (d * mag, d * mag),
+            "off_det": (0.0, 0.0), "accuracy": 0.5}
+
+
+def test_printed_sizes_are_f32_storage():
+    g = golden()
+    nu, nv = g["detector_pixels"]
+    assert 4 * nu * nv * g["angles"][0] / 1e9 == pytest.approx(g["projections_gb"][0], abs=0.5)
+    assert 4 * np.prod(g["image_voxels"]) / 1e9 == pytest.approx(g["image_gb"][0], abs=0.5)
+    size = np.array(g["image_voxels"]) * g["voxel_um"][0] * 1e-3
+    np.testing.assert_allclose(size, g["image_size_mm"], rtol=0.01)
+
+
+def test_planner_on_the_paper_problem():
+    from paper_1905_03748_gb300 import tigre
+    g = golden()
+    geo = coffee_geometry(g)
+    ang = np.arange(int(g["angles"][0])) * (2 * np.pi / g["angles"][0])
+    pl, slab = tigre.tigre_cgls_ooc_plan_desc(geo, ang, 280 * 10 ** 9)
+    assert pl == 2 and slab >= 16
+    with pytest.raises(tigre.TigreError):
+        tigre.tigre_cgls_ooc_plan_desc(geo, ang, int(g["gpu_memory_gib"][0] * 2 ** 30))
