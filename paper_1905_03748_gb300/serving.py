@@ -17,7 +17,6 @@ alone with tigre_cgls, in arrival order.
 """
 from __future__ import annotations
 
-import math
 import time
 from dataclasses import dataclass, field
 
