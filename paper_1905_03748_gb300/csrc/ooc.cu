@@ -27,7 +27,6 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
-#include <thread>
 
 #include "ray.cuh"
 #include "vecops.cuh"
@@ -243,9 +242,12 @@ tigre_status forward_ooc_impl(tigre_geometry* g, const float* vol_host, float* p
     return TIGRE_OK;
 }
 
+// With slab_dots (device, one double per slab), slab_dots[s] = ||slab s||^2 of
+// the backprojection, summed on the device before the slab is copied out.
 tigre_status backward_ooc_impl(tigre_geometry* g, const float* proj, int proj_on_host,
                                float* vol_host, int64_t a0, int64_t na, tigre_bp_weight w,
-                               int64_t slab, int64_t chunk, cudaStream_t st)
+                               int64_t slab, int64_t chunk, cudaStream_t st,
+                               double* slab_dots = nullptr)
 {
     TIGRE_TRY(check_geometry(g));
     TIGRE_TRY(check_range(g, a0, na));
@@ -272,6 +274,8 @@ tigre_status backward_ooc_impl(tigre_geometry* g, const float* proj, int proj_on
     for (int i = 0; i < 2; ++i) TIGRE_TRY(B.alloc(&out[i], (size_t)(plane * slab)));
     if (proj_on_host)
         for (int i = 0; i < 2; ++i) TIGRE_TRY(B.alloc(&pbuf[i], (size_t)(pix * chunk)));
+    double* dot_partials = nullptr;
+    if (slab_dots) TIGRE_TRY(B.alloc(&dot_partials, (size_t)kRedBlocks));
     cudaEvent_t* out_free = S.ev;       // [2] slab buffer copied out
     cudaEvent_t* out_ready = S.ev + 2;  // [2] slab buffer computed
     cudaEvent_t* p_ready = S.ev + 4;    // [2] projection chunk landed
@@ -303,6 +307,8 @@ tigre_status backward_ooc_impl(tigre_geometry* g, const float* proj, int proj_on
                 TIGRE_CUDA(cudaEventRecord(p_free[pb], st));
             }
         }
+        if (slab_dots)
+            TIGRE_TRY(dot_f64(dst, dst, (int64_t)(z1 - z0) * plane, dot_partials, slab_dots + s, st));
         TIGRE_CUDA(cudaEventRecord(out_ready[b], st));
         TIGRE_CUDA(cudaStreamWaitEvent(S.copy, out_ready[b], 0));
         TIGRE_CUDA(cudaMemcpyAsync(vol_host + (int64_t)z0 * plane, out[b],
@@ -341,10 +347,11 @@ extern "C" tigre_status tigre_backward_ooc(tigre_geometry_t geo, const float* pr
 // device.  Two placements, chosen from the device budget:
 //
 // Placement 1 ("host vectors"): the volume-sized vectors x, p, s live in
-// pinned host memory and reach the GPU only through the out-of-core
-// operators; the projection-sized b, r, q stay on the device.  Volume-sized
-// updates and their FP64 inner products run on the host cores.  Device
-// memory: three projection sets plus slab buffers.
+// pinned host memory and are streamed through the GPU in z-slabs; the
+// projection-sized b, r, q stay on the device.  ||s||^2 is summed slab by
+// slab on the device as the backprojection produces s; x += alpha p and
+// p = s + beta p run in one pass over the x, p and s slabs.  Device memory:
+// three projection sets plus slab buffers.
 //
 // Placement 2 ("streamed direction"): x, r, q stay on the device; only the
 // search direction p lives in host memory (in the caller's x buffer, which
@@ -362,28 +369,35 @@ extern "C" tigre_status tigre_backward_ooc(tigre_geometry_t geo, const float* pr
 namespace tigre {
 namespace {
 
-// Parallel loop over [0, n) on the host cores (fixed split: deterministic sums).
-template <typename F>
-void host_parallel(int64_t n, F&& f)
+// The placement-1 direction update on one slab, in the in-core CGLS's FP32
+// fused multiply-adds: x += alpha p, then p = s + beta p.
+__global__ void __launch_bounds__(256) cgls_slab_axpy_kernel(float* __restrict__ x,
+                                                             const float* __restrict__ p,
+                                                             int64_t n, float alpha)
 {
-    const int nt = (int)std::max(1u, std::min(64u, std::thread::hardware_concurrency()));
-    std::vector<std::thread> th;
-    for (int t = 0; t < nt; ++t)
-        th.emplace_back([&, t] { f(n * t / nt, n * (t + 1) / nt, t); });
-    for (auto& x : th) x.join();
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        x[i] = fmaf(alpha, p[i], x[i]);
 }
 
-double host_dot(const float* a, const float* b, int64_t n)
+__global__ void __launch_bounds__(256) cgls_slab_xpay_kernel(float* __restrict__ p,
+                                                             const float* __restrict__ s,
+                                                             int64_t n, float beta)
 {
-    std::vector<double> part(64, 0.0);
-    host_parallel(n, [&](int64_t lo, int64_t hi, int t) {
-        double s = 0.0;
-        for (int64_t i = lo; i < hi; ++i) s += (double)a[i] * (double)b[i];
-        part[(size_t)t] = s;
-    });
-    double s = 0.0;
-    for (double v : part) s += v;
-    return s;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        p[i] = fmaf(beta, p[i], s[i]);
+}
+
+// Sum of the per-slab values in slab order (host FP64 combine of nslab scalars).
+tigre_status sum_slab_dots(const double* d_dots, int64_t nslab, double* out)
+{
+    std::vector<double> h((size_t)nslab);
+    TIGRE_CUDA(cudaMemcpy(h.data(), d_dots, sizeof(double) * (size_t)nslab, cudaMemcpyDeviceToHost));
+    double t = 0.0;
+    for (double v : h) t += v;
+    *out = t;
+    return TIGRE_OK;
 }
 
 __global__ void set_dscalar_kernel(double* dst, double v) { *dst = v; }
@@ -445,10 +459,12 @@ size_t placement1_workspace(const tigre_geometry* g, int64_t slab, const bool ne
 {
     const tigre_geometry_desc& d = g->desc;
     const int64_t plane = d.n_voxel[0] * d.n_voxel[1];
+    const int64_t nslab = (d.n_voxel[2] + slab - 1) / slab;
     const size_t fwd = sizeof(float) * (size_t)(2 * plane * (slab + 1)) + FwdSlabs::bytes(d, slab, need);
+    // the backprojection's two slab buffers, or the direction update's two
     const size_t bwd = sizeof(float) * (size_t)(2 * plane * slab) +
                        bp_slab_pad_bytes(d, slab, (int64_t)g->angles.size());
-    return std::max(fwd, bwd) + sizeof(double) * (size_t)(kRedBlocks + kScalarSlots);
+    return std::max(fwd, bwd) + sizeof(double) * (size_t)(nslab + 2 * kRedBlocks + kScalarSlots);
 }
 
 // Slab thicknesses the backprojector fills without waste: it computes z in
@@ -497,7 +513,11 @@ static tigre_status cgls_host_vectors(tigre_geometry* g, const float* b_host, fl
                                       const tigre_solver_opts* o, double* h_hist, int64_t slab)
 {
     cudaStream_t st = (cudaStream_t)o->cuda_stream;
+    const tigre_geometry_desc& d = g->desc;
     const int64_t nvox = n_vox(g), na = (int64_t)g->angles.size(), m = n_pix(g) * na;
+    const int64_t nz = d.n_voxel[2], plane = d.n_voxel[0] * d.n_voxel[1];
+    slab = std::max<int64_t>(1, std::min(slab, nz));
+    const int64_t nslab = (nz + slab - 1) / slab;
     HostPin pin_x;
     TIGRE_TRY(pin_x.pin(x_host, sizeof(float) * (size_t)nvox));
     float *hp = nullptr, *hs = nullptr;
@@ -510,21 +530,49 @@ static tigre_status cgls_host_vectors(tigre_geometry* g, const float* b_host, fl
     HostFree free_s{hs};
     Bufs B;
     float *b, *r, *q;
-    double* sc;
+    double *sc, *sdots;
     TIGRE_TRY(B.alloc(&b, (size_t)m));
     TIGRE_TRY(B.alloc(&r, (size_t)m));
     TIGRE_TRY(B.alloc(&q, (size_t)m));
     TIGRE_TRY(B.alloc(&sc, (size_t)(kRedBlocks + kScalarSlots)));
+    TIGRE_TRY(B.alloc(&sdots, (size_t)nslab));
     double* partials = sc;
     double* qq = sc + kRedBlocks;       // [2]
     double* rr = sc + kRedBlocks + 2;   // [2]
     double* gam = sc + kRedBlocks + 4;  // gamma (host-set)
+    // x += alpha p and p = s + beta p, slab by slab through the device, in
+    // two slab buffers that exist only for the pass (the backprojection's
+    // footprint): p and x in, x out; then s in where x was, p out.
+    auto update = [&](float alpha, float beta) -> tigre_status {
+        Bufs U;
+        float *up, *uv;
+        TIGRE_TRY(U.alloc(&up, (size_t)(plane * slab)));
+        TIGRE_TRY(U.alloc(&uv, (size_t)(plane * slab)));
+        const dim3 grid(4 * 152), block(256);
+        for (int64_t z0 = 0; z0 < nz; z0 += slab) {
+            const int64_t n = plane * std::min(slab, nz - z0), off = plane * z0;
+            const size_t bytes = sizeof(float) * (size_t)n;
+            TIGRE_CUDA(cudaMemcpyAsync(up, hp + off, bytes, cudaMemcpyHostToDevice, st));
+            TIGRE_CUDA(cudaMemcpyAsync(uv, x_host + off, bytes, cudaMemcpyHostToDevice, st));
+            cgls_slab_axpy_kernel<<<grid, block, 0, st>>>(uv, up, n, alpha);
+            TIGRE_LAUNCHED("cgls_slab_axpy_kernel");
+            TIGRE_CUDA(cudaMemcpyAsync(x_host + off, uv, bytes, cudaMemcpyDeviceToHost, st));
+            TIGRE_CUDA(cudaMemcpyAsync(uv, hs + off, bytes, cudaMemcpyHostToDevice, st));
+            cgls_slab_xpay_kernel<<<grid, block, 0, st>>>(up, uv, n, beta);
+            TIGRE_LAUNCHED("cgls_slab_xpay_kernel");
+            TIGRE_CUDA(cudaMemcpyAsync(hp + off, up, bytes, cudaMemcpyDeviceToHost, st));
+        }
+        // the next projection reads p from host memory on its own stream
+        TIGRE_CUDA(cudaStreamSynchronize(st));
+        return TIGRE_OK;
+    };
     TIGRE_CUDA(cudaMemcpyAsync(b, b_host, sizeof(float) * (size_t)m, cudaMemcpyHostToDevice, st));
     // r = b - A x0; p = A^T r; gamma = ||p||^2
     TIGRE_TRY(forward_ooc_impl(g, x_host, q, 0, na, slab, st));
     TIGRE_TRY(weighted_residual(b, q, nullptr, r, m, partials, rr, st));
-    TIGRE_TRY(backward_ooc_impl(g, r, 0, hp, 0, na, o->bp_weight, slab, 0, st));
-    double gamma = host_dot(hp, hp, nvox);
+    TIGRE_TRY(backward_ooc_impl(g, r, 0, hp, 0, na, o->bp_weight, slab, 0, st, sdots));
+    double gamma = 0.0;
+    TIGRE_TRY(sum_slab_dots(sdots, nslab, &gamma));
     for (int it = 0; it < o->n_iter; ++it) {
         TIGRE_TRY(forward_ooc_impl(g, hp, q, 0, na, slab, st));
         TIGRE_TRY(dot_f64(q, q, m, partials, qq, st));
@@ -535,23 +583,18 @@ static tigre_status cgls_host_vectors(tigre_geometry* g, const float* b_host, fl
         // r -= alpha q on the device (alpha = gamma / qq from device slots)
         TIGRE_TRY(set_dscalar(gam, gamma, st));
         TIGRE_TRY(axpy_ratio_norm(r, q, m, gam, qq, -1.0f, partials, rr, st));
-        // x += alpha p on the host, while the device updates r
-        const float af = (float)alpha;
-        host_parallel(nvox, [&](int64_t lo, int64_t hi, int) {
-            for (int64_t i = lo; i < hi; ++i) x_host[i] = fmaf(af, hp[i], x_host[i]);
-        });
         if (h_hist) {
             double rn[2];
             TIGRE_CUDA(cudaMemcpyAsync(rn, rr, sizeof(rn), cudaMemcpyDeviceToHost, st));
             TIGRE_CUDA(cudaStreamSynchronize(st));
             h_hist[it] = rn[1];
         }
-        TIGRE_TRY(backward_ooc_impl(g, r, 0, hs, 0, na, o->bp_weight, slab, 0, st));
-        const double gamma_new = host_dot(hs, hs, nvox);
+        // s = A^T r with ||s||^2 per slab; then x += alpha p, p = s + beta p
+        TIGRE_TRY(backward_ooc_impl(g, r, 0, hs, 0, na, o->bp_weight, slab, 0, st, sdots));
+        double gamma_new = 0.0;
+        TIGRE_TRY(sum_slab_dots(sdots, nslab, &gamma_new));
         const float beta = (float)(gamma != 0.0 ? gamma_new / gamma : 0.0);
-        host_parallel(nvox, [&](int64_t lo, int64_t hi, int) {
-            for (int64_t i = lo; i < hi; ++i) hp[i] = fmaf(beta, hp[i], hs[i]);
-        });
+        TIGRE_TRY(update((float)alpha, beta));
         gamma = gamma_new;
     }
     TIGRE_CUDA(cudaStreamSynchronize(st));
