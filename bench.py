@@ -34,6 +34,7 @@ sys.path.insert(0, ROOT)
 METRIC = "Ax/Aᵀy Gvoxel·angles/s and CGLS s/iter at 512³×360"
 UNIT = "Gvoxel*angles/s"
 FLOPS_PER_SAMPLE = 22  # trilinear interpolation: 7 lerps x 3 flops + 1 accumulation
+L1_BYTES_PER_SAMPLE = 32  # the eight FP32 taps a trilinear sample gathers
 KERNEL_SOURCES = ["paper_1905_03748_gb300/csrc/forward.cu", "paper_1905_03748_gb300/csrc/ray.cuh"]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "fwd_kernel_traffic.json")
 
@@ -271,6 +272,8 @@ def run_ours(args):
     sm_max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     fp32_peak = 152 * 128 * 2 * sm_max_mhz * 1e6 / 1e12  # TFLOP/s, FMA = 2 flops
     achieved = samples * FLOPS_PER_SAMPLE / (fwd_avg / 1e3) / 1e12
+    l1_peak = 152 * 128 * sm_max_mhz * 1e6 / 1e12  # TB/s
+    l1_achieved = samples * L1_BYTES_PER_SAMPLE / (fwd_avg / 1e3) / 1e12
     traffic = None
     sol = None
     try:
@@ -301,7 +304,13 @@ def run_ours(args):
                                        f"{sm_max_mhz:.0f} MHz (derived)",
                         "binding_unit": "L1/TEX gathers (latency and throughput), not the "
                                         "FP32 pipe and not DRAM",
-                        "binding_unit_sol_ncu": sol},
+                        "binding_unit_sol_ncu": sol,
+                        "l1": {"achieved_tbs": l1_achieved, "peak_tbs": l1_peak,
+                               "frac": l1_achieved / l1_peak,
+                               "per_unit": f"{L1_BYTES_PER_SAMPLE} B gathered per sample "
+                                           f"x {samples} samples per launch",
+                               "peak_source": "152 SMs x 128 B per clock (L1 load width) x "
+                                              f"max SM clock {sm_max_mhz:.0f} MHz (derived)"}},
            "gpu_launches": launches, "clocks": clk.summary(),
            "paper_context": "CGLS 512^3, 15 it in 61 s (4.1 s/iter incl. host copies), "
                             "1x GTX 1080 Ti (Sec. 4); detector/angles not stated"}
