@@ -390,8 +390,10 @@ TIGRE_API tigre_status tigre_geometry_set_brick(tigre_geometry_t geo, int64_t ed
  * path 4. */
 TIGRE_API tigre_status tigre_geometry_set_forward_path(tigre_geometry_t geo, int path);
 
-/* The angle groups the forward projector's paths 5 / 6 (and path 0 when it
- * pairs angles) read, computed on the host (no device needed): size (2 or 4)
+/* Scheduling of the Sec. 2.1 projector's threads (no counterpart in the
+ * paper, whose kernel gives each thread one pixel of one angle): the angle
+ * groups the forward projector's paths 5 / 6 (and path 0 when it pairs
+ * angles) read, computed on the host (no device needed): size (2 or 4)
  * angle indices per group, each group of one memory layout (|cos| > |sin| or
  * not) and one march direction, neighbours in angle, -1 filling a short
  * group; n_groups groups.  drift = the median angle gap inside pairs times
