@@ -100,7 +100,9 @@ typedef struct {
 
 typedef struct tigre_geometry* tigre_geometry_t;
 
-/* Validate the description and copy the angles (host array of n_angles
+/* The circular cone-beam geometry of the paper's experiments (Sec. 3.1:
+ * DSO, DSD, voxel and detector grids, projection angles).  Validate the
+ * description and copy the angles (host array of n_angles
  * doubles).  Requires DSO > 0, DSD > DSO, all sizes > 0, finite values, and a
  * source orbit outside the volume.  Invalid arguments are rejected before any
  * CUDA call; a valid geometry is bound to the current device and its
@@ -110,7 +112,8 @@ TIGRE_API tigre_status tigre_geometry_create(const tigre_geometry_desc* desc, co
                                    int64_t n_angles, tigre_geometry_t* out);
 TIGRE_API tigre_status tigre_geometry_destroy(tigre_geometry_t geo);
 
-/* proj[0 .. angle_count) = A vol for angles angle_begin .. +angle_count.
+/* Sec. 2.1, the interpolated ray-driven projection:
+ * proj[0 .. angle_count) = A vol for angles angle_begin .. +angle_count.
  * vol: device (nz, ny, nx) in vol_dtype; proj: device (angle_count, nv, nu) in
  * proj_dtype, overwritten.  Asynchronous on cuda_stream (a cudaStream_t; NULL
  * = legacy default stream). */
@@ -118,14 +121,17 @@ TIGRE_API tigre_status tigre_forward(tigre_geometry_t geo, const void* vol, tigr
                            void* proj, tigre_dtype proj_dtype, int64_t angle_begin,
                            int64_t angle_count, void* cuda_stream);
 
-/* vol = sum over angles angle_begin .. +angle_count of the weighted
+/* Sec. 2.2, the voxel-driven backprojection (FDK or pseudo-matched weights,
+ * or the exact transpose of tigre_forward):
+ * vol = sum over angles angle_begin .. +angle_count of the weighted
  * backprojection of proj (device (angle_count, nv, nu), proj_dtype).  vol:
  * device (nz, ny, nx) in vol_dtype, overwritten.  Asynchronous. */
 TIGRE_API tigre_status tigre_backward(tigre_geometry_t geo, const void* proj, tigre_dtype proj_dtype,
                             void* vol, tigre_dtype vol_dtype, int64_t angle_begin,
                             int64_t angle_count, tigre_bp_weight weight, void* cuda_stream);
 
-/* n_steps of x <- x - alpha g / ||g||_2, g the gradient of
+/* Sec. 2.3, TV minimisation by gradient descent:
+ * n_steps of x <- x - alpha g / ||g||_2, g the gradient of
  * TV_eps(x) = sum sqrt(Dx^2 + Dy^2 + Dz^2 + eps) with backward differences
  * (zero across the low boundary); a step with ||g|| = 0 leaves x unchanged.
  * vol: device (nz, ny, nx), updated in place.  ||g|| is reduced in FP64.
@@ -249,24 +255,27 @@ typedef void* (*tigre_alloc_fn)(size_t bytes, void* cuda_stream, void* ctx);
 typedef void (*tigre_free_fn)(void* ptr, void* cuda_stream, void* ctx);
 TIGRE_API tigre_status tigre_set_allocator(tigre_alloc_fn alloc, tigre_free_fn free_fn, void* ctx);
 
-/* Fill *opts with the defaults listed above. */
+/* Fill *opts with the defaults listed above (no counterpart in the paper). */
 TIGRE_API tigre_status tigre_solver_opts_default(tigre_solver_opts* opts);
 
-/* SIRT (x <- x + lambda V A_w^T W (b - A x), W = 1/(A 1), V = 1/(A_w^T 1),
+/* SIRT, one of the iterative methods that apply A and A^T every iteration
+ * (Sec. 2): (x <- x + lambda V A_w^T W (b - A x), W = 1/(A 1), V = 1/(A_w^T 1),
  * reciprocals of values <= 1e-12 set to 0).  proj: b (n_angles, nv, nu) F32;
  * vol: (nz, ny, nx) F32 initial guess in, result out.  resid_hist (host,
  * n_iter doubles, may be NULL) receives ||b - A x_k|| before update k. */
 TIGRE_API tigre_status tigre_sirt(tigre_geometry_t geo, const void* proj, void* vol,
                         const tigre_solver_opts* opts, double* resid_hist);
 
-/* OS-SART: the SIRT update applied per subset of subset_size consecutive
+/* OS-SART (Sec. 3.2 reconstructs the Ichthyosaur with it, subsets of 200
+ * angles): the SIRT update applied per subset of subset_size consecutive
  * angles, subsets in order; with tv_steps > 0, tigre_tv_step after each full
  * iteration with alpha = tv_alpha * ||x - x_prev||.  resid_hist[k] =
  * sqrt(sum over subsets of ||b_s - A_s x||^2) during iteration k. */
 TIGRE_API tigre_status tigre_sart(tigre_geometry_t geo, const void* proj, void* vol,
                         const tigre_solver_opts* opts, double* resid_hist);
 
-/* CGLS with FP64 inner products computed on the device; x0 = vol on entry
+/* CGLS (Sec. 3.2 reconstructs the coffee bean with it) with FP64 inner
+ * products computed on the device; x0 = vol on entry
  * (r0 = b - A x0).  resid_hist[k] = ||r|| after iteration k.  proj, vol and
  * the iterates are stored in opts->storage (F32, BF16 or F16): every ray and
  * voxel sum and every vector update is computed in FP32 and rounded once to
@@ -278,7 +287,8 @@ TIGRE_API tigre_status tigre_sart(tigre_geometry_t geo, const void* proj, void* 
 TIGRE_API tigre_status tigre_cgls(tigre_geometry_t geo, const void* proj, void* vol,
                         const tigre_solver_opts* opts, double* resid_hist);
 
-/* Stepwise CGLS (the same iteration as tigre_cgls) for callers that
+/* Stepwise CGLS (no counterpart in the paper; the same iteration as
+ * tigre_cgls) for callers that
  * interleave several reconstructions or time single iterations.
  * begin: device proj (b) and vol (x0, updated in place) must stay valid until
  *        end; computes r = b - A x0, p = A^T r, gamma = ||p||^2 and allocates
@@ -367,13 +377,15 @@ TIGRE_API tigre_status tigre_fdk(tigre_geometry_t geo, const void* proj, tigre_d
 typedef enum { TIGRE_PROJ_INTERPOLATED = 0, TIGRE_PROJ_SIDDON = 1 } tigre_projector;
 TIGRE_API tigre_status tigre_geometry_set_projector(tigre_geometry_t geo, int projector);
 
-/* Edge (voxels) of the x-y bricks into which out-of-core projections cut
+/* Alg. 1 on one GPU: edge (voxels) of the x-y bricks into which out-of-core
+ * projections cut
  * each z-slab (0 = default 512).  Rays resident on the GPU at one time then
  * read one brick's planes, which stay in L2; at 3072^2 a single quad plane
  * of the slab is larger than L2.  Only the partial sums' order changes. */
 TIGRE_API tigre_status tigre_geometry_set_brick(tigre_geometry_t geo, int64_t edge);
 
-/* Forward-projector kernel choice for this handle: 0 = automatic (the quad
+/* Kernel choice for this handle's Sec. 2.1 projector (no counterpart in the
+ * paper): 0 = automatic (the quad
  * gather kernel; with 2 angles per warp for full-range calls when the rays of
  * one pixel at paired angles stay within 16 voxels of each other, e.g. 512^3 x
  * 360), 1 = scalar L1 gather kernel, 2 = shared-memory slab kernel
@@ -407,18 +419,22 @@ TIGRE_API tigre_status tigre_forward_angle_groups(const tigre_geometry_desc* des
                                                   int64_t* n_groups, double* drift,
                                                   int* auto_pairs);
 
-/* Error bits raised by kernels of this handle (1 = a bounded wait timed out,
+/* (No counterpart in the paper.)  Error bits raised by kernels of this
+ * handle (1 = a bounded wait timed out,
  * 2 = a slab did not fit its staging box, 4 = rays of one block ran opposite
  * ways; the affected outputs are NaN).  Synchronous; clear != 0 resets. */
 TIGRE_API tigre_status tigre_geometry_error_flags(tigre_geometry_t geo, int* flags, int clear);
 
-/* Total quadrature samples (sum of K over rays) of tigre_forward for the
+/* The work of one Sec. 2.1 forward projection: total quadrature samples
+ * (sum of K over rays) of tigre_forward for the
  * angle range: the algorithmic work of one forward projection.  Runs a
  * ray-setup kernel on the current device and synchronises. */
 TIGRE_API tigre_status tigre_forward_samples(tigre_geometry_t geo, int64_t angle_begin,
                                              int64_t angle_count, int64_t* samples);
 
-/* Profiling: tigre_profile_enable(1) resets the counters and starts timing
+/* Profiling (no counterpart in the paper; Sec. 3.1 reports kernel and
+ * transfer times apart): tigre_profile_enable(1) resets the counters and
+ * starts timing
  * the main kernel of each operator call with CUDA events on its stream;
  * tigre_profile_read(kind, ...) waits for the recorded events and returns the
  * number of timed calls and their total device time.  kind: 0 forward
@@ -429,7 +445,8 @@ TIGRE_API tigre_status tigre_profile_enable(int on);
 TIGRE_API tigre_status tigre_profile_read(int kind, int64_t* calls, double* total_ms);
 TIGRE_API int64_t tigre_launch_count(void);
 
-/* Message describing the last failure on the calling thread ("" if none). */
+/* Message describing the last failure on the calling thread ("" if none;
+ * no counterpart in the paper). */
 TIGRE_API const char* tigre_last_error(void);
 
 #ifdef __cplusplus

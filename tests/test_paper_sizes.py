@@ -1,5 +1,5 @@
-"""The one worked problem the paper prints sizes for (Sec. 4, coffee bean,
-CGLS; tests/golden/sec4_coffee_bean_cgls.txt): F32 storage gives its 29 GB
+"""The one worked problem the paper prints sizes for (Sec. 3.2, coffee bean,
+CGLS; tests/golden/sec3_2_coffee_bean_cgls.txt): F32 storage gives its 29 GB
 of projections and 40 GB of image, and the out-of-core planner places that
 problem on one GB300 with x, r and q in HBM.  On one of the paper's 11 GiB
 GPUs it is refused: the planner's placements keep three projection sets on
@@ -9,7 +9,7 @@ import os
 import numpy as np
 import pytest
 
-GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "sec4_coffee_bean_cgls.txt")
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "sec3_2_coffee_bean_cgls.txt")
 
 
 def golden():
