@@ -365,8 +365,8 @@ TIGRE_API tigre_status tigre_rof_denoise(const int64_t n_voxel[3], const float* 
 TIGRE_API tigre_status tigre_fdk(tigre_geometry_t geo, const void* proj, tigre_dtype proj_dtype,
                                  void* vol, tigre_dtype vol_dtype, void* cuda_stream);
 
-/* Projector of this handle (Sec. 2.1 offers both; Sec. 3.1 reconstructs with
- * each): INTERPOLATED (default) samples the trilinear interpolant at the
+/* Projector of this handle (Sec. 2.1 offers both; Sec. 3.1 times SIDDON, which
+ * is TIGRE's default): INTERPOLATED (default here) samples the trilinear interpolant at the
  * midpoints of K equal steps; SIDDON integrates the piecewise-constant volume
  * exactly, voxel (i,j,k) filling [i-1/2, i+1/2] x ... in index space, as the
  * sum of its intersection lengths (mm) with the ray times the voxel values.

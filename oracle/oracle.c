@@ -41,7 +41,7 @@
  *     h * (trilinear corner weight) * y into its 8 corner voxels.
  *
  *   Ray-voxel intersection (Siddon) projector (Sec. 2.1, the second
- *   projector TIGRE offers; Sec. 3.1 uses both): the volume is piecewise
+ *   projector TIGRE offers, the one Sec. 3.1 times): the volume is piecewise
  *   constant, voxel (i,j,k) filling the index-space box
  *   [i-1/2, i+1/2] x [j-1/2, j+1/2] x [k-1/2, k+1/2]; proj = sum over the
  *   voxels the segment S->P crosses of (intersection length, mm) x value.

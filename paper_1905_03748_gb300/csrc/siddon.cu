@@ -1,5 +1,5 @@
 // Ray-voxel intersection (Siddon) projector -- the paper's other projector
-// (Sec. 2.1 names both; Sec. 3.1 reconstructs with each) -- and its exact
+// (Sec. 2.1 names both; Sec. 3.1 times this one, TIGRE's default) -- and its exact
 // transpose.
 //
 // The volume is piecewise constant: voxel (i, j, k) fills the index-space box
