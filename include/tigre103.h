@@ -309,17 +309,21 @@ TIGRE_API tigre_status tigre_cgls_end(tigre_cgls_t state);
  * long reconstruction stop and continue, e.g. across job limits or when a
  * server preempts it).  save: copies the state's residual r (n_angles x nv x
  * nu) and search direction p (nz x ny x nx), in the state's storage type, to
- * HOST buffers, and returns gamma = ||A^T r||^2 and the iterations done;
- * synchronises the stream.  With the caller's x at that point these are the
- * whole state.  resume: a stepwise state from such a checkpoint -- proj is
- * b, vol holds the checkpoint's x (DEVICE, opts->storage), r_host / p_host /
+ * HOST buffers of r_bytes and p_bytes (TIGRE_ERR_INVALID_ARG, nothing copied,
+ * when either is smaller than its vector), and returns gamma = ||A^T r||^2
+ * and the iterations done; synchronises the stream.  With the caller's x at
+ * that point these are the whole state.  resume: a stepwise state from such
+ * a checkpoint -- proj is b, vol holds the checkpoint's x (DEVICE,
+ * opts->storage), r_host / p_host (r_bytes / p_bytes, checked as for save) /
  * gamma as saved -- that skips the initial A x0 and A^T r; its iterations
  * continue bitwise as the saved state's would have.  Its history covers the
  * iterations run after resuming. */
-TIGRE_API tigre_status tigre_cgls_save(tigre_cgls_t state, void* r_host, void* p_host,
-                                       double* gamma, int* iterations);
+TIGRE_API tigre_status tigre_cgls_save(tigre_cgls_t state, void* r_host, size_t r_bytes,
+                                       void* p_host, size_t p_bytes, double* gamma,
+                                       int* iterations);
 TIGRE_API tigre_status tigre_cgls_resume(tigre_geometry_t geo, const void* proj, void* vol,
-                                         const void* r_host, const void* p_host, double gamma,
+                                         const void* r_host, size_t r_bytes, const void* p_host,
+                                         size_t p_bytes, double gamma,
                                          const tigre_solver_opts* opts, tigre_cgls_t* out);
 
 /* Out-of-core gradient-descent TV (Sec. 2.3's splitting of a regulariser,

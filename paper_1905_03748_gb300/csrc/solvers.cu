@@ -535,12 +535,14 @@ tigre_status tigre_cgls_history(tigre_cgls_t S, double* resid_hist, int n)
     return finish_history(S->hist, resid_hist, n, S->st);
 }
 
-tigre_status tigre_cgls_save(tigre_cgls_t S, void* r_host, void* p_host, double* gamma,
-                             int* iterations)
+tigre_status tigre_cgls_save(tigre_cgls_t S, void* r_host, size_t r_bytes, void* p_host,
+                             size_t p_bytes, double* gamma, int* iterations)
 {
     if (!S || !r_host || !p_host || !gamma || !iterations)
         return fail(TIGRE_ERR_INVALID_ARG, "null state or output");
     const size_t e = dtype_size(S->dt);
+    if (r_bytes < e * (size_t)S->m || p_bytes < e * (size_t)S->nvox)
+        return fail(TIGRE_ERR_INVALID_ARG, "checkpoint buffers smaller than r and p");
     TIGRE_CUDA(cudaMemcpyAsync(r_host, S->r, e * (size_t)S->m, cudaMemcpyDeviceToHost, S->st));
     TIGRE_CUDA(cudaMemcpyAsync(p_host, S->p, e * (size_t)S->nvox, cudaMemcpyDeviceToHost, S->st));
     TIGRE_CUDA(cudaMemcpyAsync(gamma, Scalars{S->sc}.slot(S->cur), sizeof(double),
@@ -551,8 +553,9 @@ tigre_status tigre_cgls_save(tigre_cgls_t S, void* r_host, void* p_host, double*
 }
 
 tigre_status tigre_cgls_resume(tigre_geometry_t geo, const void* proj, void* vol,
-                               const void* r_host, const void* p_host, double gamma,
-                               const tigre_solver_opts* opts, tigre_cgls_t* out)
+                               const void* r_host, size_t r_bytes, const void* p_host,
+                               size_t p_bytes, double gamma, const tigre_solver_opts* opts,
+                               tigre_cgls_t* out)
 {
     if (!out) return fail(TIGRE_ERR_INVALID_ARG, "null output handle pointer");
     *out = nullptr;
@@ -562,6 +565,12 @@ tigre_status tigre_cgls_resume(tigre_geometry_t geo, const void* proj, void* vol
         return fail(TIGRE_ERR_INVALID_ARG, "checkpoint buffers and a finite gamma are needed");
     if (opts->flags & TIGRE_X0_ZERO)
         return fail(TIGRE_ERR_INVALID_ARG, "a resumed CGLS continues from the checkpoint's x");
+    {
+        const size_t e = dtype_size(opts->storage);
+        const int64_t m = n_pix(geo) * (int64_t)geo->angles.size();
+        if (r_bytes < e * (size_t)m || p_bytes < e * (size_t)n_vox(geo))
+            return fail(TIGRE_ERR_INVALID_ARG, "checkpoint buffers smaller than r and p");
+    }
     if (opts->flags & TIGRE_HOST_RESIDENT)
         return fail(TIGRE_ERR_UNSUPPORTED, "stepwise CGLS takes device buffers");
     return cgls_resume_device(geo, proj, vol, r_host, p_host, gamma, opts, out);

@@ -82,9 +82,10 @@ _sigs = {
     "tigre_cgls_iterate": [_P, ctypes.c_int],
     "tigre_cgls_history": [_P, _P, ctypes.c_int],
     "tigre_cgls_end": [_P],
-    "tigre_cgls_save": [_P, _P, _P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)],
-    "tigre_cgls_resume": [_P, _P, _P, _P, _P, ctypes.c_double, ctypes.POINTER(tigre_solver_opts),
-                          ctypes.POINTER(_P)],
+    "tigre_cgls_save": [_P, _P, ctypes.c_size_t, _P, ctypes.c_size_t,
+                        ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)],
+    "tigre_cgls_resume": [_P, _P, _P, _P, ctypes.c_size_t, _P, ctypes.c_size_t, ctypes.c_double,
+                          ctypes.POINTER(tigre_solver_opts), ctypes.POINTER(_P)],
     "tigre_forward_samples": [_P, _I64, _I64, ctypes.POINTER(_I64)],
     "tigre_forward_ooc": [_P, _P, _P, _I64, _I64, _I64, _P],
     "tigre_backward_ooc": [_P, _P, ctypes.c_int, _P, _I64, _I64, ctypes.c_int, _I64, _I64, _P],
@@ -371,7 +372,9 @@ def tigre_cgls_save(state, r_host: torch.Tensor, p_host: torch.Tensor) -> tuple:
     g = ctypes.c_double()
     n = ctypes.c_int()
     _check(_lib.tigre_cgls_save(state, ctypes.c_void_p(r_host.data_ptr()),
-                                ctypes.c_void_p(p_host.data_ptr()), ctypes.byref(g),
+                                r_host.numel() * r_host.element_size(),
+                                ctypes.c_void_p(p_host.data_ptr()),
+                                p_host.numel() * p_host.element_size(), ctypes.byref(g),
                                 ctypes.byref(n)))
     return float(g.value), int(n.value)
 
@@ -396,7 +399,9 @@ def tigre_cgls_resume(handle, proj, vol, r_host, p_host, gamma: float, n_iter_hi
     o.storage = vt
     s = ctypes.c_void_p()
     _check(_lib.tigre_cgls_resume(handle, pp, vp, ctypes.c_void_p(r_host.data_ptr()),
-                                  ctypes.c_void_p(p_host.data_ptr()), float(gamma),
+                                  r_host.numel() * r_host.element_size(),
+                                  ctypes.c_void_p(p_host.data_ptr()),
+                                  p_host.numel() * p_host.element_size(), float(gamma),
                                   ctypes.byref(o), ctypes.byref(s)))
     return s
 

@@ -116,3 +116,19 @@ def test_x0_zero_stepwise_and_refusals(tigre):
             tigre.tigre_cgls(G.handle, b.cpu(), torch.zeros(G.vol_shape), 1, out_of_core=True,
                              x0_zero=True)
 
+
+
+def test_save_rejects_buffers_smaller_than_the_state(tigre):
+    geo, ang, _ = case()
+    with tigre.Geometry(geo, ang) as G:
+        b = torch.zeros(G.proj_shape, device="cuda")
+        x = torch.zeros(G.vol_shape, device="cuda")
+        st = tigre.tigre_cgls_begin(G.handle, b, x)
+        try:
+            with pytest.raises(tigre.TigreError):
+                tigre.tigre_cgls_save(st, torch.empty(10), torch.empty(G.vol_shape))
+            with pytest.raises(tigre.TigreError):  # half the bytes of the F32 state's p
+                tigre.tigre_cgls_save(st, torch.empty(G.proj_shape),
+                                      torch.empty(G.vol_shape, dtype=torch.bfloat16))
+        finally:
+            tigre.tigre_cgls_end(st)
