@@ -625,3 +625,135 @@ def test_split_tv_buffer_as_deep_as_the_steps_is_enough():
     c = oracle.tv_steps_split(f, 3, 0.03, 1e-8, slab=4, depth=3, halo=1)
     np.testing.assert_allclose(a, b, rtol=1e-12, atol=1e-14)
     assert np.abs(a - c).max() > 1e-6
+
+
+# ------------------------------------------ OS-SART subsets and TV coupling
+
+def dense_os_sart(A, Bm, b, na, subset, n_iter, order=None, global_v=False):
+    """OS-SART written on dense matrices: rows of A and columns of Bm are
+    angle-major, a subset is `subset` consecutive angles, W_s = 1/(A_s 1) and
+    V_s = 1/(Bm_s 1) with the zero guard, subsets visited in `order`."""
+    m = A.shape[0] // na
+    blocks = [np.arange(s, min(s + subset, na)) for s in range(0, na, subset)]
+    rows = [np.concatenate([np.arange(a * m, (a + 1) * m) for a in blk]) for blk in blocks]
+
+    def recip(v):
+        return np.where(v > 1e-12, 1.0 / np.where(v > 1e-12, v, 1.0), 0.0)
+
+    V_all = recip(Bm @ np.ones(A.shape[0]))
+    x = np.zeros(A.shape[1])
+    res = []
+    for _ in range(n_iter):
+        rr = 0.0
+        for s in (order if order is not None else range(len(blocks))):
+            As, Bs = A[rows[s]], Bm[:, rows[s]]
+            W = recip(As @ np.ones(A.shape[1]))
+            V = V_all if global_v else recip(Bs @ np.ones(len(rows[s])))
+            r = b[rows[s]] - As @ x
+            rr += float(r @ r)
+            x = x + V * (Bs @ (W * r))
+        res.append(np.sqrt(rr))
+    return x, np.array(res)
+
+
+@pytest.mark.parametrize("subset", [2, 4])
+def test_os_sart_subsets_equal_the_dense_per_subset_iteration(subset):
+    """Sec. 3.2's OS-SART with 3 subsets of 2 angles and with a ragged split
+    (4 + 2): the oracle equals the dense iteration with per-subset weights
+    W_s, V_s and the subsets in acquisition order.  A global V, or the
+    subsets visited in reverse, lands far away, so either mistake fails."""
+    geo = tiny_geo(nx=4, ny=4, nz=3, nu=6, nv=5)
+    ang = synth.angles(6)
+    A, Bm = dense_operators(geo, ang)
+    b = A @ np.random.default_rng(2).random(A.shape[1])
+    x_ref, r_ref = dense_os_sart(A, Bm, b, 6, subset, 3)
+    xo, ro = oracle.os_sart(geo, ang, b.reshape(6, 5, 6), 3, subset=subset)
+    np.testing.assert_allclose(xo.ravel(), x_ref, rtol=1e-11, atol=1e-13)
+    np.testing.assert_allclose(ro, r_ref, rtol=1e-11)
+    nb = (6 + subset - 1) // subset
+    for wrong in (dense_os_sart(A, Bm, b, 6, subset, 3, global_v=True)[0],
+                  dense_os_sart(A, Bm, b, 6, subset, 3, order=range(nb - 1, -1, -1))[0]):
+        assert np.linalg.norm(wrong - x_ref) > 1e-3 * np.linalg.norm(x_ref)
+
+
+def tv_grad_autograd(x: np.ndarray, eps: float) -> np.ndarray:
+    """Gradient of TV_eps(f) = sum sqrt(Dx^2 + Dy^2 + Dz^2 + eps), backward
+    differences with zero across the low boundary, by reverse-mode automatic
+    differentiation of that sum (FP64, CPU) -- not the oracle's stencil."""
+    import torch
+    f = torch.tensor(x, dtype=torch.float64, requires_grad=True)
+    dz = torch.cat([torch.zeros_like(f[:1]), f[1:] - f[:-1]], 0)
+    dy = torch.cat([torch.zeros_like(f[:, :1]), f[:, 1:] - f[:, :-1]], 1)
+    dx = torch.cat([torch.zeros_like(f[:, :, :1]), f[:, :, 1:] - f[:, :, :-1]], 2)
+    torch.sqrt(dx * dx + dy * dy + dz * dz + eps).sum().backward()
+    return f.grad.numpy()
+
+
+@pytest.mark.parametrize("n_iter", [1, 2])
+def test_os_sart_tv_runs_after_each_full_sweep_with_the_update_norm_as_step(n_iter):
+    """Sec. 2.3 couples the regulariser to the data step through the norm of
+    the image update.  Each OS-SART+TV iteration here is the dense data
+    sweep over all subsets, then tv_steps steps x <- x - a g/||g|| with
+    a = tv_alpha * ||x_after_sweep - x_before_sweep|| and g from automatic
+    differentiation of TV_eps.  TV before the sweep, after every subset, or
+    a step scaled by ||x|| instead of the update would not match."""
+    geo = tiny_geo(nx=4, ny=4, nz=3, nu=6, nv=5)
+    ang = synth.angles(6)
+    A, Bm = dense_operators(geo, ang)
+    b = A @ np.random.default_rng(3).random(A.shape[1])
+    tv_alpha, n_tv, eps = 0.3, 4, 1e-6
+    x = np.zeros(A.shape[1])
+    for _ in range(n_iter):
+        x_prev = x.copy()
+        # one full sweep from x: dense OS-SART iteration started there
+        m = A.shape[0] // 6
+        for s in range(3):
+            rows = np.arange(2 * s * m, (2 * s + 2) * m)
+            As, Bs = A[rows], Bm[:, rows]
+            W = 1.0 / np.where(As.sum(1) > 1e-12, As.sum(1), np.inf)
+            cs = Bs.sum(1)
+            V = np.where(cs > 1e-12, 1.0 / np.where(cs > 1e-12, cs, 1.0), 0.0)
+            x = x + V * (Bs @ (W * (b[rows] - As @ x)))
+        a = tv_alpha * np.linalg.norm(x - x_prev)
+        v = x.reshape(3, 4, 4)
+        for _ in range(n_tv):
+            g = tv_grad_autograd(v, eps)
+            v = v - a * g / np.linalg.norm(g)
+        x = v.ravel()
+    xo, _ = oracle.os_sart(geo, ang, b.reshape(6, 5, 6), n_iter, subset=2, tv_steps_n=n_tv,
+                           tv_alpha=tv_alpha, tv_eps=eps)
+    np.testing.assert_allclose(xo.ravel(), x, rtol=1e-9, atol=1e-11)
+    x_plain, _ = oracle.os_sart(geo, ang, b.reshape(6, 5, 6), n_iter, subset=2)
+    assert np.linalg.norm(x_plain.ravel() - x) > 1e-3 * np.linalg.norm(x)  # TV mattered
+
+
+def test_sample_count_is_the_chord_rule_on_the_enlarged_box():
+    """The work count of Ax: per ray K = max(1, ceil(len/D - 1e-9)) with len
+    the chord (mm) of the ray through the interpolant's support -- the box
+    of voxel centres -1 .. n on each axis -- and D = accuracy * min(d); rays
+    that miss it count 0.  The chord comes from world-space slab clipping
+    of the rotated frame; summed over every ray it equals sample_count, and
+    ray by ray the K the oracle places."""
+    geo = tiny_geo(nx=9, ny=7, nz=5, nu=19, nv=13, d=(1.0, 1.2, 0.8), du=(1.1, 0.9),
+                   off_origin=(0.37, -0.21, 0.13), off_det=(0.61, -0.43), accuracy=0.45)
+    ang = synth.angles(7) + 0.113
+    n = np.array(geo["n_voxel"], dtype=float)
+    d = np.array(geo["d_voxel"])
+    o = np.array(geo["off_origin"])
+    lo = (-1.0 - (n - 1) / 2.0) * d + o
+    hi = (n - (n - 1) / 2.0) * d + o
+    step = geo["accuracy"] * d.min()
+    nu, nv = geo["n_det"]
+    Ks, total = [], 0
+    for th in ang:
+        S = pins.frame(geo, th)[0]
+        for q in range(nv):
+            for p in range(nu):
+                ln = pins.box_chord(S, pins.pixel_centre(geo, th, p, q), lo, hi)
+                K = 0 if ln <= 0.0 else max(1, int(np.ceil(ln / step - 1e-9)))
+                Ks.append(K)
+                total += K
+    assert 0 in Ks and total > 0                   # some rays miss the support
+    assert oracle.sample_count(geo, ang) == total
+    rays = np.array([(a, q, p) for a in range(len(ang)) for q in range(nv) for p in range(nu)])
+    np.testing.assert_array_equal(oracle.ray_params(geo, ang, rays)[:, 0].astype(np.int64), Ks)
