@@ -148,11 +148,14 @@ TIGRE_API tigre_status tigre_tv_step(const int64_t n_voxel[3], void* vol, tigre_
  * live in one fixed scratch array compiled into the library (16 MiB + 5 KiB,
  * held on every GPU that loads the library until the process exits).
  * Volumes of more than 4,194,304 voxels are rejected with
- * TIGRE_ERR_INVALID_ARG.  The first call on a device looks up the scratch
- * address (cudaGetSymbolAddress) with that device current, so make it before
- * any stream capture.  All calls share the scratch: calls that overlap on the
- * GPU (other streams or host threads) race and must be serialised by the
- * caller.  No state carries over between calls. */
+ * TIGRE_ERR_INVALID_ARG.  The first call on a device (n_steps = 0 is
+ * enough) is its set-up: with that device current it looks up the scratch
+ * address (cudaGetSymbolAddress) and loads the TV kernels, and CUDA's lazy
+ * module loading takes device memory for that code then.  Make that call at
+ * start-up, before reserving the device memory and before any stream capture;
+ * later calls allocate nothing.  All calls share the scratch: calls that
+ * overlap on the GPU (other streams or host threads) race and must be
+ * serialised by the caller.  No state carries over between calls. */
 TIGRE_API tigre_status tigre_tv_step_noalloc(const int64_t n_voxel[3], void* vol, tigre_dtype dtype,
                                              int n_steps, double alpha, double eps,
                                              void* cuda_stream);

@@ -344,6 +344,26 @@ size_t bp_slab_pad_bytes(const tigre_geometry_desc& d, int64_t slab, int64_t na)
     return most;
 }
 
+tigre_status backward_workspace(tigre_geometry* g, tigre_dtype pt, tigre_bp_weight w, int64_t a0,
+                                int64_t na)
+{
+    TIGRE_TRY(check_geometry(g));
+    TIGRE_TRY(check_range(g, a0, na));
+    if (!dtype_ok(pt)) return fail(TIGRE_ERR_INVALID_ARG, "bad dtype");
+    const tigre_geometry_desc& d = g->desc;
+    if (w == TIGRE_BP_EXACT_ADJOINT) {
+        if (padded_elems(d) >= (size_t)INT32_MAX) return TIGRE_OK;  // refused by the operator
+        bool need[2] = {false, false};
+        for (int64_t a = a0; a < a0 + na; ++a) need[g->layout[(size_t)a]] = true;
+        DeviceBuffer* bufs[2] = {&g->adj_xy, &g->adj_yx};
+        for (int l = 0; l < 2; ++l)
+            if (need[l]) TIGRE_TRY(bufs[l]->ensure(padded_elems(d) * sizeof(float)));
+        return TIGRE_OK;
+    }
+    const BpConst c = make_bp_const(d);
+    return g->proj_pad.ensure((size_t)na * (size_t)c.PU * (size_t)c.PV * dtype_size(pt));
+}
+
 // Voxel planes [z_first, z_end) into an output buffer whose first plane is
 // z_out0 (in-core: 0, nz, 0; out-of-core slabs: the slab's planes).
 template <typename TP, typename TV>

@@ -218,6 +218,21 @@ bool tma_forward_fits(const tigre_geometry_desc& d, size_t elem);
 template <typename TV, typename TP>
 tigre_status launch_forward_tma(tigre_geometry* g, const TV* vol, TP* proj, int64_t a0, int64_t na,
                                 const bool need[2], int* d_err, cudaStream_t st);
+// Pitched volume copies the TMA path reads (elem: bytes per element).
+tigre_status tma_workspace(tigre_geometry* g, size_t elem, const bool need[2]);
+// Every cached workspace of the geometry handle that a forward projection
+// (volume stored as vt) or a backprojection (projections stored as pt) of
+// the angles [a0, a0 + na) uses, allocated and zero-bordered ahead of the
+// call.  The operators allocate only through these, and nothing once they
+// have run with the same arguments; a stream capture (where allocation is
+// refused) therefore runs them first.
+tigre_status forward_workspace(tigre_geometry* g, tigre_dtype vt, int64_t a0, int64_t na,
+                               cudaStream_t st);
+tigre_status backward_workspace(tigre_geometry* g, tigre_dtype pt, tigre_bp_weight w, int64_t a0,
+                                int64_t na);
+// Identity of the cached workspaces (addresses and layout tags); a captured
+// graph that holds these addresses replays only while it is unchanged.
+std::vector<uint64_t> workspace_signature(const tigre_geometry* g);
 tigre_status ensure_padded(DeviceBuffer& buf, const tigre_geometry_desc& d, size_t elem, int layout,
                            cudaStream_t st);
 tigre_status check_geometry(tigre_geometry* g);

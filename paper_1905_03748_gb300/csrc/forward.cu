@@ -546,6 +546,43 @@ tigre_status fill_padded_f32(const tigre_geometry_desc& d, const float* vol, flo
     return fill_padded<float>(d, vol, out, layout, st);
 }
 
+// Layouts the angles [a0, a0 + na) read.
+static void needed_layouts(const tigre_geometry* g, int64_t a0, int64_t na, bool need[2])
+{
+    need[0] = need[1] = false;
+    for (int64_t a = a0; a < a0 + na; ++a) need[g->layout[(size_t)a]] = true;
+}
+
+tigre_status forward_workspace(tigre_geometry* g, tigre_dtype vt, int64_t a0, int64_t na,
+                               cudaStream_t st)
+{
+    TIGRE_TRY(check_geometry(g));
+    TIGRE_TRY(check_range(g, a0, na));
+    if (!dtype_ok(vt)) return fail(TIGRE_ERR_INVALID_ARG, "bad dtype");
+    const tigre_geometry_desc& d = g->desc;
+    if (padded_elems(d) >= (size_t)INT32_MAX) return TIGRE_OK;  // refused by the projection
+    bool need[2];
+    needed_layouts(g, a0, na, need);
+    const bool siddon = g->projector == TIGRE_PROJ_SIDDON;
+    if (!siddon && g->fwd_path == 2) {
+        if (!g->err_flag.ptr) {
+            TIGRE_TRY(g->err_flag.ensure(sizeof(int)));
+            TIGRE_CUDA(cudaMemsetAsync(g->err_flag.ptr, 0, sizeof(int), st));
+        }
+        return tma_workspace(g, dtype_size(vt), need);
+    }
+    const bool use_quad = !siddon && (g->fwd_path == 0 || g->fwd_path >= 3);
+    DeviceBuffer* bufs[2] = {&g->vol_xy, &g->vol_yx};
+    DeviceBuffer* qbufs[2] = {&g->vol_qxy, &g->vol_qyx};
+    for (int l = 0; l < 2; ++l) {
+        if (!need[l]) continue;
+        TIGRE_TRY(ensure_padded(*bufs[l], d, dtype_size(vt), l, st));
+        // a quad holds four elements of the storage type
+        if (use_quad) TIGRE_TRY(qbufs[l]->ensure(padded_elems(d) * 4 * dtype_size(vt)));
+    }
+    return TIGRE_OK;
+}
+
 tigre_status forward_impl(tigre_geometry* g, const void* vol, tigre_dtype vt, void* proj,
                           tigre_dtype pt, int64_t a0, int64_t na, cudaStream_t st)
 {
@@ -560,8 +597,9 @@ tigre_status forward_impl(tigre_geometry* g, const void* vol, tigre_dtype vt, vo
     if (d.n_det[1] > 65535 * 8)
         return fail(TIGRE_ERR_UNSUPPORTED, "detector too large for one launch");
     const FwdConst c = make_fwd_const(d);
-    bool need[2] = {false, false};
-    for (int64_t a = a0; a < a0 + na; ++a) need[g->layout[(size_t)a]] = true;
+    TIGRE_TRY(forward_workspace(g, vt, a0, na, st));
+    bool need[2];
+    needed_layouts(g, a0, na, need);
     const bool siddon = g->projector == TIGRE_PROJ_SIDDON;
     const bool use_tma = !siddon && g->fwd_path == 2;
     const bool use_quad = !siddon && (g->fwd_path == 0 || g->fwd_path >= 3);
@@ -573,10 +611,6 @@ tigre_status forward_impl(tigre_geometry* g, const void* vol, tigre_dtype vt, vo
                            ? (const int*)g->angle_order.ptr
                            : nullptr;
     if (use_tma) {
-        if (!g->err_flag.ptr) {
-            TIGRE_TRY(g->err_flag.ensure(sizeof(int)));
-            TIGRE_CUDA(cudaMemsetAsync(g->err_flag.ptr, 0, sizeof(int), st));
-        }
         return dispatch_dtype(vt, [&](auto vtag) -> tigre_status {
             using TV = decltype(vtag);
             return dispatch_dtype(pt, [&](auto ptag) -> tigre_status {
@@ -592,15 +626,14 @@ tigre_status forward_impl(tigre_geometry* g, const void* vol, tigre_dtype vt, vo
         using Q = typename QuadOf<TV>::type;
         DeviceBuffer* bufs[2] = {&g->vol_xy, &g->vol_yx};
         DeviceBuffer* qbufs[2] = {&g->vol_qxy, &g->vol_qyx};
+        static_assert(sizeof(Q) == 4 * sizeof(TV), "a quad is four elements");
         for (int l = 0; l < 2; ++l) {
             if (!need[l]) continue;
-            TIGRE_TRY(ensure_padded(*bufs[l], d, sizeof(TV), l, st));
             TIGRE_TRY(fill_padded<TV>(d, (const TV*)vol, (TV*)bufs[l]->ptr, l, st));
             if (use_quad) {
                 const int PF = (int)(l ? d.n_voxel[1] : d.n_voxel[0]) + 2 * kPad;
                 const int PM = (int)(l ? d.n_voxel[0] : d.n_voxel[1]) + 2 * kPad;
                 const int64_t rows = (int64_t)PM * (d.n_voxel[2] + 2 * kPad);
-                TIGRE_TRY(qbufs[l]->ensure(padded_elems(d) * sizeof(Q)));
                 quad_kernel<TV><<<(unsigned)rows, 128, 0, st>>>((const TV*)bufs[l]->ptr,
                                                                 (Q*)qbufs[l]->ptr, PF, PM, rows);
                 TIGRE_LAUNCHED("quad_kernel");

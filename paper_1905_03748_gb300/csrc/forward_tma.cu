@@ -425,6 +425,22 @@ bool tma_forward_fits(const tigre_geometry_desc& d, size_t elem)
     return need_f <= (double)kTmaFB && need_s <= (double)kTmaSB;
 }
 
+tigre_status tma_workspace(tigre_geometry* g, size_t elem, const bool need[2])
+{
+    const tigre_geometry_desc& d = g->desc;
+    const size_t nx = (size_t)d.n_voxel[0], ny = (size_t)d.n_voxel[1], nz = (size_t)d.n_voxel[2];
+    const size_t align = 16 / elem;  // TileCfg<TV>::ALIGN
+    if (need[0]) {
+        const size_t pitch = (nx + align - 1) / align * align;
+        TIGRE_TRY(g->vol_xy.ensure(pitch * ny * nz * elem));
+    }
+    if (need[1]) {
+        const size_t pitch = (ny + align - 1) / align * align;
+        TIGRE_TRY(g->vol_yx.ensure(pitch * nx * nz * elem));
+    }
+    return TIGRE_OK;
+}
+
 template <typename TV, typename TP>
 tigre_status launch_forward_tma(tigre_geometry* g, const TV* vol, TP* proj, int64_t a0, int64_t na,
                                 const bool need[2], int* d_err, cudaStream_t st)

@@ -114,6 +114,19 @@ void DeviceBuffer::release()
     tag = 0;
 }
 
+std::vector<uint64_t> workspace_signature(const tigre_geometry* g)
+{
+    std::vector<uint64_t> sig;
+    for (const DeviceBuffer* b : {&g->vol_xy, &g->vol_yx, &g->vol_qxy, &g->vol_qyx, &g->proj_pad,
+                                  &g->adj_xy, &g->adj_yx, &g->err_flag, &g->brick_prange}) {
+        sig.push_back((uint64_t)(uintptr_t)b->ptr);
+        sig.push_back(b->tag);
+    }
+    sig.push_back((uint64_t)g->fwd_path);
+    sig.push_back((uint64_t)g->projector);
+    return sig;
+}
+
 static bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
 
 tigre_status validate_desc(const tigre_geometry_desc* d, const double* angles, int64_t na)

@@ -32,6 +32,12 @@ bool profiling() { return g_profiling.load(std::memory_order_relaxed) != 0; }
 ProfScope::ProfScope(int kind, cudaStream_t st) : kind_(kind), st_(st)
 {
     if (!profiling()) return;
+    // Work captured into a graph does not run now: nothing to time.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st_, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) {
+        cudaGetLastError();
+        return;
+    }
     if (cudaEventCreate(&a_) != cudaSuccess || cudaEventCreate(&b_) != cudaSuccess) {
         cudaGetLastError();
         return;

@@ -241,15 +241,24 @@ struct tigre_cgls_state {
     bool graph = false;              // replay captured iteration pairs
     bool x0_zero = false;            // x0 = 0: r = b without projecting x0
     cudaGraphExec_t exec[2] = {};    // two iterations, by starting gamma slot
+    std::vector<uint64_t> ws_sig;    // the handle's workspaces the graphs were captured with
 };
 
 namespace tigre {
 namespace {
 
+void drop_graphs(tigre_cgls_state* S)
+{
+    for (cudaGraphExec_t& e : S->exec)
+        if (e) {
+            cudaGraphExecDestroy(e);
+            e = nullptr;
+        }
+}
+
 void cgls_release(tigre_cgls_state* S)
 {
-    for (cudaGraphExec_t e : S->exec)
-        if (e) cudaGraphExecDestroy(e);
+    drop_graphs(S);
     for (void* ptr : {(void*)S->r, (void*)S->q, (void*)S->p, (void*)S->s, (void*)S->sc,
                       (void*)S->hist, (void*)S->counter})
         if (ptr) dev_free(ptr, S->st);
@@ -318,11 +327,32 @@ tigre_status cgls_reserve(tigre_cgls_state* S, int more)
     S->hist = nh;
     S->hist_cap = cap;
     // Captured graphs hold the old history pointer: recapture on next use.
-    for (cudaGraphExec_t& e : S->exec)
-        if (e) {
-            cudaGraphExecDestroy(e);
-            e = nullptr;
-        }
+    drop_graphs(S);
+    return TIGRE_OK;
+}
+
+// Every cached workspace of the geometry handle that an iteration's A p and
+// A^T r use, allocated (and zero-bordered) on the state's stream.  Runs when
+// the state is made, whatever the initial guess, so that no operator
+// allocates inside a stream capture.
+tigre_status cgls_workspaces(tigre_cgls_state* S)
+{
+    TIGRE_TRY(forward_workspace(S->g, S->dt, 0, S->na, S->st));
+    return backward_workspace(S->g, S->dt, S->bw, 0, S->na);
+}
+
+// Before graphs replay: another call on the handle may have reallocated a
+// workspace the graphs hold, or laid it out for another storage type.  The
+// workspaces are prepared again (which restores their zero borders) and the
+// graphs are recaptured when their addresses or layouts changed.
+tigre_status cgls_graph_check(tigre_cgls_state* S)
+{
+    TIGRE_TRY(cgls_workspaces(S));
+    std::vector<uint64_t> sig = workspace_signature(S->g);
+    if (sig != S->ws_sig) {
+        drop_graphs(S);
+        S->ws_sig = std::move(sig);
+    }
     return TIGRE_OK;
 }
 
@@ -393,7 +423,8 @@ tigre_status cgls_new_state(tigre_geometry* g, const void* b, void* x,
     S->b = b;
     S->x = x;
     S->x0_zero = (o->flags & TIGRE_X0_ZERO) != 0;
-    const tigre_status st = cgls_init(S, o->n_iter);
+    tigre_status st = cgls_init(S, o->n_iter);
+    if (st == TIGRE_OK) st = cgls_workspaces(S);
     if (st != TIGRE_OK) {
         cgls_release(S);
         return st;
@@ -513,7 +544,8 @@ tigre_status tigre_cgls_iterate(tigre_cgls_t S, int n_iter)
     if (!S || n_iter < 0) return fail(TIGRE_ERR_INVALID_ARG, "null state or n_iter < 0");
     TIGRE_TRY(cgls_reserve(S, n_iter));
     int left = n_iter;
-    if (S->graph) {
+    if (S->graph && left >= 2) {
+        TIGRE_TRY(cgls_graph_check(S));
         // Two iterations return the gamma slots to where they started, so a
         // captured pair replays correctly from the same parity.
         while (left >= 2) {

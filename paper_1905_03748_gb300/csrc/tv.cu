@@ -95,6 +95,18 @@ __global__ void tv_update_kernel(T* __restrict__ x, const float* __restrict__ g,
         x[i] = from_f32<T>(fmaf(-s, g[i], to_f32<T>(x[i])));
 }
 
+tigre_status tv_load_kernels()
+{
+    cudaFuncAttributes fa;
+    TIGRE_CUDA(cudaFuncGetAttributes(&fa, tv_grad_kernel<float>));
+    TIGRE_CUDA(cudaFuncGetAttributes(&fa, tv_grad_kernel<__nv_bfloat16>));
+    TIGRE_CUDA(cudaFuncGetAttributes(&fa, tv_grad_kernel<__half>));
+    TIGRE_CUDA(cudaFuncGetAttributes(&fa, tv_update_kernel<float>));
+    TIGRE_CUDA(cudaFuncGetAttributes(&fa, tv_update_kernel<__nv_bfloat16>));
+    TIGRE_CUDA(cudaFuncGetAttributes(&fa, tv_update_kernel<__half>));
+    return reduce_load_kernels();
+}
+
 tigre_status tv_impl(const int64_t n[3], void* vol, tigre_dtype t, int n_steps, double alpha,
                      double eps, const double* d_alpha_scale, void* scratch_g, double* d_red,
                      cudaStream_t st)

@@ -12,11 +12,16 @@
 // area on every call; this entry point instead uses one fixed scratch array
 // compiled into the library.
 //
-// The scratch array below is a device symbol: every GPU that loads this
-// library holds it (16 MiB + 5 KiB) until the process exits.  In host code its
-// name is only a stand-in for the symbol, not a device address, so the address
-// is looked up once per device with cudaGetSymbolAddress (on the first call
-// made with that device current) and cached.
+// The scratch array below is a device symbol: a GPU holds it (16 MiB + 5 KiB)
+// from the moment this library's code is loaded on it until the process
+// exits.  In host code its name is only a stand-in for the symbol, not a
+// device address, so the address is looked up once per device with
+// cudaGetSymbolAddress and cached.  That look-up, and the loading of the TV
+// kernels (CUDA loads a module's code lazily, on first use, and loading takes
+// device memory), happen in the first call made with a device current --
+// also when that call has n_steps = 0.  A caller that reserves its device
+// memory at start-up therefore makes one call per device first (n_steps = 0
+// is enough), before the reservation and before any stream capture.
 #include <cmath>
 #include <mutex>
 
@@ -52,6 +57,7 @@ tigre_status scratch_address(float** out)
             return cuda_fail(e != cudaSuccess ? e : cudaErrorInvalidSymbol,
                              "cudaGetSymbolAddress(TV scratch)");
         }
+        TIGRE_TRY(tv_load_kernels());
         g_scratch_addr[dev] = p;
     }
     *out = (float*)g_scratch_addr[dev];
@@ -79,9 +85,9 @@ extern "C" tigre_status tigre_tv_step_noalloc(const int64_t n_voxel[3], void* vo
         return fail(TIGRE_ERR_INVALID_ARG,
                     "tigre_tv_step_noalloc: the volume has " + std::to_string(N) +
                         " voxels, more than its fixed scratch holds (4194304); use tigre_tv_step");
-    if (n_steps == 0) return TIGRE_OK;
     float* scratch = nullptr;
-    TIGRE_TRY(scratch_address(&scratch));
+    TIGRE_TRY(scratch_address(&scratch));  // first call on a device: the set-up
+    if (n_steps == 0) return TIGRE_OK;
     // Every kernel writes the gradient and the reduction partials in full
     // before reading them, so nothing left by an earlier call is used.
     double* red = reinterpret_cast<double*>(scratch + kNoAllocMaxVoxels);

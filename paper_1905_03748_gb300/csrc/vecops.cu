@@ -57,6 +57,13 @@ __global__ void __launch_bounds__(kRedThreads) reduce_partials_kernel(
     }
 }
 
+tigre_status reduce_load_kernels()
+{
+    cudaFuncAttributes fa;
+    TIGRE_CUDA(cudaFuncGetAttributes(&fa, reduce_partials_kernel));
+    return TIGRE_OK;
+}
+
 tigre_status reduce_partials(const double* partials, double* out, int sqrt_out, cudaStream_t st)
 {
     reduce_partials_kernel<<<1, kRedThreads, 0, st>>>(partials, kRedBlocks, out, sqrt_out);

@@ -7,6 +7,10 @@ namespace tigre {
 
 // out[0] = sum partials (fixed order); with sqrt_out also out[1] = sqrt(out[0]).
 tigre_status reduce_partials(const double* partials, double* out, int sqrt_out, cudaStream_t st);
+// Load (under lazy module loading) the kernels of reduce_partials / of the
+// TV steps on the current device, so that a later launch loads nothing.
+tigre_status reduce_load_kernels();
+tigre_status tv_load_kernels();
 // y += sign * (num/den) x        (num, den: device doubles; den == 0 -> no-op)
 tigre_status axpy_ratio(float* y, const float* x, int64_t n, const double* num, const double* den,
                         float sign, cudaStream_t st);

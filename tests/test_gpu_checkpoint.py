@@ -42,14 +42,16 @@ def test_resume_continues(tigre, dtype, graph, bp):
         tigre.tigre_cgls_end(st)
         torch.cuda.synchronize()
         x_ref = x.cpu()
-        # resumed in a fresh state from the checkpoint
+        # resumed in a fresh state on a fresh handle (no workspace cached yet:
+        # with graph=True the first replay is captured before any projection)
         x2 = x_ck.cuda()
-        st2 = tigre.tigre_cgls_resume(G.handle, b, x2, r_host, p_host, gamma, n_iter_hint=8,
-                                      stream=s, graph=graph, bp_weight=bp)
-        tigre.tigre_cgls_iterate(st2, 4)
-        h2 = tigre.tigre_cgls_history(st2, 4)
-        tigre.tigre_cgls_end(st2)
-        torch.cuda.synchronize()
+        with tigre.Geometry(geo, ang) as G2:
+            st2 = tigre.tigre_cgls_resume(G2.handle, b, x2, r_host, p_host, gamma,
+                                          n_iter_hint=8, stream=s, graph=graph, bp_weight=bp)
+            tigre.tigre_cgls_iterate(st2, 4)
+            h2 = tigre.tigre_cgls_history(st2, 4)
+            tigre.tigre_cgls_end(st2)
+            torch.cuda.synchronize()
     assert done == 3 and gamma > 0 and np.isfinite(gamma)
     if bp == "matched":
         assert torch.equal(x2.cpu(), x_ref)
@@ -59,6 +61,84 @@ def test_resume_continues(tigre, dtype, graph, bp):
         assert float(d) < 1e-5
         np.testing.assert_allclose(h2, h_ref[3:], rtol=1e-5)
         assert np.all(np.diff(h_ref) < 0)  # exact adjoint: the residual norm decreases
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
+def test_graph_replay_from_a_zero_start_on_a_fresh_handle(tigre, dtype):
+    """begin(graph=True, x0_zero=True) on a handle that has never projected:
+    the zero start skips A x0, so the first projection of the run is the
+    one captured into the graph.  The workspaces it needs are made when the
+    state is, and the replayed iterations are the eager ones bit for bit."""
+    geo, ang, vol = case()
+    with tigre.Geometry(geo, ang) as G0:
+        b = G0.forward(torch.from_numpy(vol).cuda()).to(dtype)
+        x_ref = torch.zeros(G0.vol_shape, device="cuda", dtype=dtype)
+        st = tigre.tigre_cgls_begin(G0.handle, b, x_ref, x0_zero=True)
+        tigre.tigre_cgls_iterate(st, 5)
+        h_ref = tigre.tigre_cgls_history(st, 5)
+        tigre.tigre_cgls_end(st)
+    s = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(s), tigre.Geometry(geo, ang) as G:
+        x = torch.full(G.vol_shape, 3.0, device="cuda", dtype=dtype)
+        st = tigre.tigre_cgls_begin(G.handle, b, x, stream=s, graph=True, x0_zero=True)
+        tigre.tigre_cgls_iterate(st, 5)  # two captured pairs, then one eager step
+        h = tigre.tigre_cgls_history(st, 5)
+        tigre.tigre_cgls_end(st)
+        torch.cuda.synchronize()
+    assert torch.equal(x, x_ref)
+    np.testing.assert_array_equal(h, h_ref)
+
+
+def test_graph_replay_after_the_handle_served_another_storage_type(tigre):
+    """Between replays, a call on the same handle in BF16 re-lays the cached
+    forward workspaces out for 16-bit elements.  The next replay restores
+    the F32 layout (and recaptures if an address changed): the run equals
+    an uninterrupted eager run bit for bit."""
+    geo, ang, vol = case()
+    v = torch.from_numpy(vol).cuda()
+    with tigre.Geometry(geo, ang) as G0:
+        b = G0.forward(v)
+        x_ref = torch.zeros(G0.vol_shape, device="cuda")
+        st = tigre.tigre_cgls_begin(G0.handle, b, x_ref)
+        tigre.tigre_cgls_iterate(st, 4)
+        h_ref = tigre.tigre_cgls_history(st, 4)
+        tigre.tigre_cgls_end(st)
+    s = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(s), tigre.Geometry(geo, ang) as G:
+        x = torch.zeros(G.vol_shape, device="cuda")
+        st = tigre.tigre_cgls_begin(G.handle, b, x, stream=s, graph=True)
+        tigre.tigre_cgls_iterate(st, 2)
+        G.forward(v.bfloat16())  # same handle, other storage type, same stream
+        G.backward(b.half())
+        tigre.tigre_cgls_iterate(st, 2)
+        h = tigre.tigre_cgls_history(st, 4)
+        tigre.tigre_cgls_end(st)
+        torch.cuda.synchronize()
+    assert torch.equal(x, x_ref)
+    np.testing.assert_array_equal(h, h_ref)
+
+
+def test_resume_rejects_a_search_direction_buffer_smaller_than_p(tigre):
+    """The C entry point itself refuses a p buffer below the volume's bytes
+    (with a large enough r) before copying anything."""
+    import ctypes
+    geo, ang, _ = case()
+    with tigre.Geometry(geo, ang) as G:
+        b = torch.zeros(G.proj_shape, device="cuda")
+        x = torch.zeros(G.vol_shape, device="cuda")
+        r = torch.zeros(G.proj_shape)
+        p = torch.zeros(G.vol_shape)
+        o = tigre._opts(8, None)
+        out = ctypes.c_void_p()
+        st = tigre._lib.tigre_cgls_resume(
+            G.handle, ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()),
+            ctypes.c_void_p(r.data_ptr()), r.numel() * 4, ctypes.c_void_p(p.data_ptr()), 4,
+            1.0, ctypes.byref(o), ctypes.byref(out))
+        assert st == tigre.TIGRE_ERR_INVALID_ARG
+        assert out.value is None
+        assert b"smaller" in tigre._lib.tigre_last_error()
 
 
 def test_resume_rejects_bad_checkpoints(tigre):

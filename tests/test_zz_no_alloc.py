@@ -6,6 +6,8 @@ the same result as tigre_tv_step, call after call, through the C ABI.
 This file is collected last on purpose (name order), so a run that stops at
 its first failure has already run every other test.
 """
+import gc
+
 import numpy as np
 import pytest
 import torch
@@ -41,3 +43,42 @@ def test_noalloc_tv_step_rejects_volumes_beyond_its_scratch(tigre):
     big = torch.zeros((161, 160, 164), device="cuda")  # 4,224,640 voxels > 4,194,304
     with pytest.raises(tigre.TigreError, match="scratch"):
         tigre.tigre_tv_step_noalloc(big, 1, 0.1, 1e-8)
+
+
+def test_noalloc_tv_step_calls_no_allocator(tigre):
+    """After the set-up call (n_steps = 0) on this device, two calls go
+    through with an allocator that refuses everything and counts its calls:
+    it is never called.  tigre_tv_step, which allocates its scratch per
+    call, fails under the same allocator."""
+    vol = synth.random_volume((24, 30, 34), seed=6)
+    x = torch.from_numpy(vol).cuda()
+    ref = x.clone()
+    tigre.tigre_tv_step_noalloc(x, 0, 0.5, 1e-8)  # the per-device set-up
+    torch.cuda.synchronize()
+    calls = {"alloc": 0, "free": 0}
+
+    def alloc(nbytes, stream):
+        calls["alloc"] += 1
+        return 0  # refuse
+
+    def free(ptr, stream):
+        calls["free"] += 1
+
+    gc.collect()  # handles left to the garbage collector by earlier tests
+    tigre.tigre_set_allocator(alloc, free)
+    try:
+        for _ in range(2):
+            tigre.tigre_tv_step_noalloc(x, 3, 0.5, 1e-8)
+        torch.cuda.synchronize()
+        seen = dict(calls)
+        with pytest.raises(tigre.TigreError) as err:
+            tigre.tigre_tv_step(ref.clone(), 3, 0.5, 1e-8)
+        assert err.value.status == tigre.TIGRE_ERR_OOM
+    finally:
+        torch.cuda.synchronize()
+        tigre.tigre_set_allocator(None, None)
+    assert seen == {"alloc": 0, "free": 0}
+    for _ in range(2):
+        tigre.tigre_tv_step(ref, 3, 0.5, 1e-8)
+    torch.cuda.synchronize()
+    assert rel(x, ref) < TOL
