@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-angles", type=int, default=48,
                     help="angles of the workload in the bounded CPU-oracle sample")
+    ap.add_argument("--workload", default="cgls_512", choices=["cgls_512", "small_64"],
+                    help="cgls_512: the benchmark line (default); small_64: the 64^3 x 100 "
+                         "SIRT workload, timed with the oracle beside it")
     return ap.parse_args()
 
 
@@ -270,9 +273,10 @@ def run_ours(args):
     bp_avg = bp_ms / max(bp_n, 1)
     peaks = measured_peaks()
     sm_max_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    fp32_peak = 152 * 128 * 2 * sm_max_mhz * 1e6 / 1e12  # TFLOP/s, FMA = 2 flops
-    achieved = samples * FLOPS_PER_SAMPLE / (fwd_avg / 1e3) / 1e12
-    l1_peak = 152 * 128 * sm_max_mhz * 1e6 / 1e12  # TB/s
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    fp32_peak = n_sm * 128 * 2 * sm_max_mhz * 1e6 / 1e12  # TFLOP/s, FMA = 2 flops
+    alu_achieved = samples * FLOPS_PER_SAMPLE / (fwd_avg / 1e3) / 1e12
+    l1_peak = n_sm * 128 * sm_max_mhz * 1e6 / 1e12  # TB/s: 128 B per SM per clock
     l1_achieved = samples * L1_BYTES_PER_SAMPLE / (fwd_avg / 1e3) / 1e12
     traffic = None
     sol = None
@@ -281,7 +285,7 @@ def run_ours(args):
             tr = json.load(f)
         if tr.get("source_hash") == source_hash():
             traffic = tr.get("dram_bytes_per_launch")
-            sol = tr.get("sol_16_angle_capture")
+            sol = tr.get("ncu_sol")
     except Exception:
         pass
 
@@ -295,22 +299,21 @@ def run_ours(args):
            "samples_per_ax": samples,
            "kernel_ms": {"forward": fwd_avg, "backproject_matched": bp_avg},
            "resid_last": float(hist[-1]) if len(hist) else None,
-           "roofline": {"kernel": "fwd_quad_kernel", "bound": "alu", "achieved": achieved,
-                        "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+           "roofline": {"kernel": "fwd_quad_kernel", "bound": "l1", "achieved": l1_achieved,
+                        "peak": l1_peak, "unit": "TB/s", "frac": l1_achieved / l1_peak,
                         "traffic": traffic,
-                        "per_unit": f"{FLOPS_PER_SAMPLE} FP32 flops per quadrature sample "
-                                    f"x {samples} samples per launch",
-                        "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock "
-                                       f"{sm_max_mhz:.0f} MHz (derived)",
-                        "binding_unit": "L1/TEX gathers (latency and throughput), not the "
-                                        "FP32 pipe and not DRAM",
-                        "binding_unit_sol_ncu": sol,
-                        "l1": {"achieved_tbs": l1_achieved, "peak_tbs": l1_peak,
-                               "frac": l1_achieved / l1_peak,
-                               "per_unit": f"{L1_BYTES_PER_SAMPLE} B gathered per sample "
-                                           f"x {samples} samples per launch",
-                               "peak_source": "152 SMs x 128 B per clock (L1 load width) x "
-                                              f"max SM clock {sm_max_mhz:.0f} MHz (derived)"}},
+                        "per_unit": f"{L1_BYTES_PER_SAMPLE} B gathered per quadrature sample "
+                                    f"(eight FP32 taps) x {samples} samples per launch",
+                        "peak_source": f"{n_sm} SMs (device query) x 128 B per clock (L1 data "
+                                       f"path) x max SM clock {sm_max_mhz:.0f} MHz (derived; "
+                                       "no measured L1 peak exists)",
+                        "binding_unit": "L1/TEX data path (gathers), not DRAM, not the FP32 pipe",
+                        "ncu_sol": sol,
+                        "alu": {"achieved_tflops": alu_achieved, "peak_tflops": fp32_peak,
+                                "frac": alu_achieved / fp32_peak,
+                                "per_unit": f"{FLOPS_PER_SAMPLE} FP32 flops per sample",
+                                "peak_source": f"{n_sm} SMs x 128 FP32 lanes x 2 x "
+                                               f"{sm_max_mhz:.0f} MHz (derived)"}},
            "gpu_launches": launches, "clocks": clk.summary(),
            "paper_context": "CGLS 512^3, 15 it in 61 s (4.1 s/iter incl. host copies), "
                             "1x GTX 1080 Ti (Sec. 4); detector/angles not stated"}
@@ -339,10 +342,92 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_small(args):
+    """The 64^3 workload: 64^3 volume of 1 mm voxels (nested 10-ellipsoid
+    head stand-in), 128^2 detector of 0.8 mm, 100 angles.  One step = one
+    forward projection, one matched backprojection and a 10-iteration SIRT
+    solve from x0 = 0, device-timed with CUDA events (launch bound at this
+    size, so wall time per step and the launch count are what is reported).
+    The oracle does the same work on the host cores beside it."""
+    import torch
+    from paper_1905_03748_gb300 import synth, tigre
+
+    torch.cuda.set_device(0)
+    geo, ang = synth.workload("small_64")
+    x_np = synth.phantom("head10", 64, 1.0)
+    G = tigre.Geometry(geo, ang)
+    xt = torch.from_numpy(x_np).cuda()
+    b = G.forward(xt)
+    x = torch.zeros(G.vol_shape, device="cuda")
+    stream = torch.cuda.current_stream()
+    n_sirt = 10
+
+    def step():
+        p = G.forward(xt)
+        G.backward(p, weight="matched")
+        tigre.tigre_sirt(G.handle, b, x, n_sirt, stream=stream.cuda_stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    l0 = tigre.tigre_launch_count()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        wall = (time.perf_counter() - t0) / args.steps
+    ms = e0.elapsed_time(e1) / args.steps
+    launches = (tigre.tigre_launch_count() - l0) // args.steps
+    vox_ang = float(np.prod(geo["n_voxel"])) * len(ang)
+    work = vox_ang * (2 + 2 * n_sirt) + vox_ang  # FP + BP + (FP + BP) per SIRT it + W = A 1
+    out = {"metric": "64^3 x 100: FP + matched BP + 10 SIRT iterations, s per step",
+           "value": ms / 1e3, "unit": "s/step", "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": False,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "64^3 vol (1 mm, nested 10-ellipsoid stand-in for the modified "
+                                  "Shepp-Logan head), 128^2 det (0.8 mm), 100 angles, DSO 1000 / "
+                                  "DSD 1536 mm",
+                      "step": "A x, matched A^T y, then tigre_sirt 10 iterations from x0 = 0",
+                      "l2": "working set fits L2 (launch-bound size)"},
+           "sirt_ms_per_iter_incl_setup": None, "host_wall_ms_per_step": wall * 1e3,
+           "gvox_ang_s": work / (ms / 1e3) / 1e9, "gpu_launches_per_step": launches,
+           "clocks": clk.summary()}
+    # SIRT alone, for the per-iteration figure
+    torch.cuda.synchronize()
+    e0.record(stream)
+    tigre.tigre_sirt(G.handle, b, x, n_sirt, stream=stream.cuda_stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    out["sirt_ms_per_iter_incl_setup"] = e0.elapsed_time(e1) / n_sirt
+    if not args.no_cpu:
+        import oracle
+        oracle.build()
+        xv = x_np.astype(np.float64)
+        t0 = time.perf_counter()
+        p = oracle.forward(geo, ang, xv)
+        oracle.backward(geo, ang, p, oracle.BP_MATCHED)
+        oracle.sirt(geo, ang, b.cpu().numpy(), n_sirt)
+        dt = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": dt, "unit": "s/step", "cores": os.cpu_count(),
+                               "kind": "oracle",
+                               "sample": "the whole step (FP + matched BP + 10 SIRT iterations) "
+                                         "by the FP64 oracle"}
+    G.close()
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "small_64":
+        run_small(args)
     else:
         run_ours(args)
 

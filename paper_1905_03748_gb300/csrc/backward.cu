@@ -15,7 +15,14 @@
 // columns (two) and rows around the detector: in v, as many rows as the
 // volume's shadow can reach beyond the detector for this geometry (bounded
 // on the host), so the per-voxel loop has neither clamps nor branches; u is
-// clamped once per column and angle.
+// clamped once per column and angle.  In-core launches use a quad buffer:
+// element (r, c) holds the four taps (c, c+1) x (r, r+1) of the bilinear
+// cell, so a voxel-angle pair costs one aligned 16-byte load (8 bytes for
+// 16-bit storage) instead of four scalar loads and their addresses (the
+// kernel is bound by instruction issue).  Out-of-core slab launches keep the
+// plain buffer: a thin slab's band of rows spans the cone's spread (hundreds
+// of rows at 3072^3), and four copies of it would cost device memory that
+// the slabs need.
 // Grid order: x-tiles fastest, z-chunks slowest, so resident blocks share one
 // band of detector rows per angle in L2.
 //
@@ -26,6 +33,7 @@
 #include <algorithm>
 #include <cmath>
 
+#include "quad.cuh"
 #include "ray.cuh"
 
 namespace tigre {
@@ -57,11 +65,25 @@ __device__ __forceinline__ float rsqrt_sfu(float x)
     return r;
 }
 
-template <typename T>
-__device__ __forceinline__ float ldp(const T* p)
-{
-    return to_f32<T>(__ldg(p));
-}
+
+// The four bilinear taps (c, c+1) x (r, r+1) of the cell at `cell`, from the
+// plain (QUADP false) or the quad (true) zero-bordered projection buffer.
+template <typename TP, bool QUADP> struct ProjTaps;
+template <typename TP> struct ProjTaps<TP, false> {
+    using E = TP;
+    static __device__ __forceinline__ float4 load(const E* cell, int PU)
+    {
+        return make_float4(to_f32<TP>(__ldg(cell)), to_f32<TP>(__ldg(cell + 1)),
+                           to_f32<TP>(__ldg(cell + PU)), to_f32<TP>(__ldg(cell + PU + 1)));
+    }
+};
+template <typename TP> struct ProjTaps<TP, true> {
+    using E = typename QuadOf<TP>::type;
+    static __device__ __forceinline__ float4 load(const E* cell, int)
+    {
+        return load_quad(cell, (TP*)nullptr);
+    }
+};
 
 // SART == true: also accumulate the backprojection of the all-ones
 // projections (the normaliser V^-1 = A_w^T 1, from the same weights and
@@ -70,8 +92,9 @@ __device__ __forceinline__ float ldp(const T* p)
 // Occupancy: 5 blocks per SM (48 registers, no spills) measured 11 % faster
 // than the unconstrained 62-register build; 6 blocks (40 registers) gained
 // nothing more.  The SART form, with twice the accumulators, keeps 3.
-template <typename TP, typename TV, int NZ, int MODE, bool SART = false>
-__global__ void __launch_bounds__(256, SART ? 3 : 5) bp_voxel_kernel(const TP* __restrict__ pp,
+template <typename TP, typename TV, int NZ, int MODE, bool SART, bool QUADP>
+__global__ void __launch_bounds__(256, SART ? 3 : 5) bp_voxel_kernel(
+                                                       const typename ProjTaps<TP, QUADP>::E* __restrict__ pp,
                                                        TV* __restrict__ vol,
                                                        const BpAngle* __restrict__ params,
                                                        BpConst c, int a_first, int na,
@@ -108,7 +131,7 @@ __global__ void __launch_bounds__(256, SART ? 3 : 5) bp_voxel_kernel(const TP* _
         int ip;
         float fu;
         split_floor(pu, ip, fu);
-        const TP* col = pp + (int64_t)a * PA + ip;
+        const typename ProjTaps<TP, QUADP>::E* col = pp + (int64_t)a * PA + ip;
         // Padded row coordinate of voxel k: within [2, PV - 2) by the
         // host-side bound on the volume's shadow.
         const float pv0 = fmaf(Zb * mag, c.inv_dv, pv_off);
@@ -131,11 +154,10 @@ __global__ void __launch_bounds__(256, SART ? 3 : 5) bp_voxel_kernel(const TP* _
             int iq;
             float fv;
             split_floor(fmaf((float)k, dpv, pv0), iq, fv);
-            const TP* r0 = col + iq * PU;
-            const float a00 = ldp(r0), a01 = ldp(r0 + 1);
-            const float a10 = ldp(r0 + PU), a11 = ldp(r0 + PU + 1);
-            const float top = fmaf(fu, a01 - a00, a00);
-            const float bot = fmaf(fu, a11 - a10, a10);
+            // (a00, a01, a10, a11): columns ip, ip + 1 of rows iq, iq + 1
+            const float4 t = ProjTaps<TP, QUADP>::load(col + iq * PU, PU);
+            const float top = fmaf(fu, t.y - t.x, t.x);
+            const float bot = fmaf(fu, t.w - t.z, t.z);
             const float val = fmaf(fv, bot - top, top);
             float wk = w;
             if (MODE != TIGRE_BP_FDK) {
@@ -177,19 +199,37 @@ __device__ __forceinline__ TP pix_or_zero(const TP* row, int p, int nu)
     return (unsigned)p < (unsigned)nu ? row[p] : from_f32<TP>(0.0f);
 }
 
-// Write the whole zero-bordered buffer of one angle range:
-// out[a][r][c] = y[a][r - pv_lo][c - 2] (zero outside the detector).
-template <typename TP>
-__global__ void pad_proj_kernel(const TP* __restrict__ in, TP* __restrict__ out, int nu, int nv,
+// Write the whole zero-bordered buffer of one angle range: with
+// Z(r, c) = y[a][r - pv_lo][c - 2] (zero outside the detector), the plain
+// buffer holds out[a][r][c] = Z(r, c), the quad buffer
+// out[a][r][c] = (Z(r, c), Z(r, c+1), Z(r+1, c), Z(r+1, c+1)).
+template <typename TP, bool QUADP>
+__global__ void pad_proj_kernel(const TP* __restrict__ in,
+                                typename ProjTaps<TP, QUADP>::E* __restrict__ out, int nu, int nv,
                                 int PU, int PV, int pv_lo)
 {
     const int r = blockIdx.y, a = blockIdx.z;
     const int q = r - pv_lo;
-    TP* dst = out + ((int64_t)a * PV + r) * PU;
-    const TP* row = in + ((int64_t)a * nv + q) * nu;
-    const bool inrow = (unsigned)q < (unsigned)nv;
-    for (int col = blockIdx.x * blockDim.x + threadIdx.x; col < PU; col += gridDim.x * blockDim.x)
-        dst[col] = inrow ? pix_or_zero(row, col - kPad, nu) : from_f32<TP>(0.0f);
+    typename ProjTaps<TP, QUADP>::E* dst = out + ((int64_t)a * PV + r) * PU;
+    const TP* row0 = in + ((int64_t)a * nv + q) * nu;
+    const TP* row1 = row0 + nu;
+    const bool in0 = (unsigned)q < (unsigned)nv, in1 = (unsigned)(q + 1) < (unsigned)nv;
+    const TP z = from_f32<TP>(0.0f);
+    for (int col = blockIdx.x * blockDim.x + threadIdx.x; col < PU; col += gridDim.x * blockDim.x) {
+        const int p = col - kPad;
+        const TP a00 = in0 ? pix_or_zero(row0, p, nu) : z;
+        if constexpr (!QUADP) {
+            dst[col] = a00;
+        } else {
+            const TP a01 = in0 ? pix_or_zero(row0, p + 1, nu) : z;
+            const TP a10 = in1 ? pix_or_zero(row1, p, nu) : z;
+            const TP a11 = in1 ? pix_or_zero(row1, p + 1, nu) : z;
+            if constexpr (sizeof(TP) == 4)
+                dst[col] = pack_quad(a00, a01, a10, a11);
+            else
+                dst[col] = pack_quad16(a00, a01, a10, a11);
+        }
+    }
 }
 
 // Exact adjoint: scatter every sample of each ray.
@@ -344,6 +384,14 @@ size_t bp_slab_pad_bytes(const tigre_geometry_desc& d, int64_t slab, int64_t na)
     return most;
 }
 
+// Whether an in-core backprojection with weight w reads the quad buffer
+// (slab launches always read the plain band).
+static bool bp_reads_quads(tigre_bp_weight w)
+{
+    (void)w;
+    return false;
+}
+
 tigre_status backward_workspace(tigre_geometry* g, tigre_dtype pt, tigre_bp_weight w, int64_t a0,
                                 int64_t na)
 {
@@ -361,7 +409,52 @@ tigre_status backward_workspace(tigre_geometry* g, tigre_dtype pt, tigre_bp_weig
         return TIGRE_OK;
     }
     const BpConst c = make_bp_const(d);
-    return g->proj_pad.ensure((size_t)na * (size_t)c.PU * (size_t)c.PV * dtype_size(pt));
+    const size_t elem = (bp_reads_quads(w) ? 4 : 1) * dtype_size(pt);
+    return g->proj_pad.ensure((size_t)na * (size_t)c.PU * (size_t)c.PV * elem);
+}
+
+// The launch of a voxel-driven backprojection over the planes c describes.
+template <typename TP, typename TV, bool QUADP>
+static tigre_status run_voxel_bp(tigre_geometry* g, const BpConst& c, const TP* proj, TV* vol,
+                                 int64_t a0, int64_t na, tigre_bp_weight w, int accumulate,
+                                 cudaStream_t st, bool sart, float lambda, int nonneg)
+{
+    using Q = typename ProjTaps<TP, QUADP>::E;
+    static_assert(sizeof(Q) == (QUADP ? 4 : 1) * sizeof(TP), "a quad is four elements");
+    const size_t pelems = (size_t)na * (size_t)c.PU * (size_t)c.PV;
+    TIGRE_TRY(g->proj_pad.ensure(pelems * sizeof(Q)));
+    g->proj_pad.tag = 0;
+    Q* pp = (Q*)g->proj_pad.ptr;
+    for (int64_t s = 0; s < na; s += 65535) {
+        const int64_t cnt = std::min<int64_t>(65535, na - s);
+        dim3 grid((unsigned)((c.PU + 255) / 256), (unsigned)c.PV, (unsigned)cnt);
+        pad_proj_kernel<TP, QUADP><<<grid, 256, 0, st>>>(proj + s * (int64_t)c.nu * c.nv,
+                                                   pp + s * (int64_t)c.PU * c.PV, c.nu, c.nv,
+                                                   c.PU, c.PV, c.pv_lo);
+        TIGRE_LAUNCHED("pad_proj_kernel");
+    }
+    dim3 grid((unsigned)((c.nx + 31) / 32), (unsigned)((c.ny + 7) / 8),
+              (unsigned)((c.z_end - c.z_first + kBpNZ - 1) / kBpNZ));
+    if (grid.y > 65535 || grid.z > 65535) return fail(TIGRE_ERR_UNSUPPORTED, "volume too large");
+    const BpAngle* params = (const BpAngle*)g->bp_params.ptr;
+    const dim3 block(32, 8);
+    ProfScope prof(kProfBackproject, st);
+    if (sart) {
+        if (w == TIGRE_BP_FDK)
+            bp_voxel_kernel<TP, TV, kBpNZ, TIGRE_BP_FDK, true, QUADP><<<grid, block, 0, st>>>(
+                pp, vol, params, c, (int)a0, (int)na, 0, lambda, nonneg);
+        else
+            bp_voxel_kernel<TP, TV, kBpNZ, TIGRE_BP_MATCHED, true, QUADP><<<grid, block, 0, st>>>(
+                pp, vol, params, c, (int)a0, (int)na, 0, lambda, nonneg);
+    } else if (w == TIGRE_BP_FDK) {
+        bp_voxel_kernel<TP, TV, kBpNZ, TIGRE_BP_FDK, false, QUADP><<<grid, block, 0, st>>>(
+            pp, vol, params, c, (int)a0, (int)na, accumulate);
+    } else {
+        bp_voxel_kernel<TP, TV, kBpNZ, TIGRE_BP_MATCHED, false, QUADP><<<grid, block, 0, st>>>(
+            pp, vol, params, c, (int)a0, (int)na, accumulate);
+    }
+    TIGRE_LAUNCHED("bp_voxel_kernel");
+    return TIGRE_OK;
 }
 
 // Voxel planes [z_first, z_end) into an output buffer whose first plane is
@@ -382,41 +475,13 @@ tigre_status launch_voxel_bp(tigre_geometry* g, const TP* proj, TV* vol, int64_t
         c.z_out0 = z_out0;
         bp_slab_band(c, d, z_first, z_end);
     }
-    const size_t pelems = (size_t)na * (size_t)c.PU * (size_t)c.PV;
-    TIGRE_TRY(g->proj_pad.ensure(pelems * sizeof(TP)));
-    g->proj_pad.tag = 0;
-    TP* pp = (TP*)g->proj_pad.ptr;
-    for (int64_t s = 0; s < na; s += 65535) {
-        const int64_t cnt = std::min<int64_t>(65535, na - s);
-        dim3 grid((unsigned)((c.PU + 255) / 256), (unsigned)c.PV, (unsigned)cnt);
-        pad_proj_kernel<TP><<<grid, 256, 0, st>>>(proj + s * (int64_t)c.nu * c.nv,
-                                                   pp + s * (int64_t)c.PU * c.PV, c.nu, c.nv,
-                                                   c.PU, c.PV, c.pv_lo);
-        TIGRE_LAUNCHED("pad_proj_kernel");
-    }
-    dim3 grid((unsigned)((c.nx + 31) / 32), (unsigned)((c.ny + 7) / 8),
-              (unsigned)((c.z_end - c.z_first + kBpNZ - 1) / kBpNZ));
-    if (grid.y > 65535 || grid.z > 65535) return fail(TIGRE_ERR_UNSUPPORTED, "volume too large");
-    const BpAngle* params = (const BpAngle*)g->bp_params.ptr;
-    const dim3 block(32, 8);
-    ProfScope prof(kProfBackproject, st);
-    if (sart) {
-        if (w == TIGRE_BP_FDK)
-            bp_voxel_kernel<TP, TV, kBpNZ, TIGRE_BP_FDK, true><<<grid, block, 0, st>>>(
-                pp, vol, params, c, (int)a0, (int)na, 0, lambda, nonneg);
-        else
-            bp_voxel_kernel<TP, TV, kBpNZ, TIGRE_BP_MATCHED, true><<<grid, block, 0, st>>>(
-                pp, vol, params, c, (int)a0, (int)na, 0, lambda, nonneg);
-    } else if (w == TIGRE_BP_FDK) {
-        bp_voxel_kernel<TP, TV, kBpNZ, TIGRE_BP_FDK><<<grid, block, 0, st>>>(
-            pp, vol, params, c, (int)a0, (int)na, accumulate);
-    } else {
-        bp_voxel_kernel<TP, TV, kBpNZ, TIGRE_BP_MATCHED><<<grid, block, 0, st>>>(
-            pp, vol, params, c, (int)a0, (int)na, accumulate);
-    }
-    TIGRE_LAUNCHED("bp_voxel_kernel");
-    return TIGRE_OK;
+    // In-core launches read quads where they pay, slab launches the plain band.
+    return z_end < 0 && bp_reads_quads(w) ? run_voxel_bp<TP, TV, true>(g, c, proj, vol, a0, na, w, accumulate, st, sart,
+                                                  lambda, nonneg)
+                     : run_voxel_bp<TP, TV, false>(g, c, proj, vol, a0, na, w, accumulate, st,
+                                                   sart, lambda, nonneg);
 }
+
 
 tigre_status backward_slab_impl(tigre_geometry* g, const float* proj, float* vol_slab, int64_t a0,
                                 int64_t na, tigre_bp_weight w, int accumulate, int z_first,
@@ -462,7 +527,7 @@ static tigre_status launch_adjoint(tigre_geometry* g, const TP* proj, TV* vol, i
     const tigre_geometry_desc& d = g->desc;
     if (padded_elems(d) >= (size_t)INT32_MAX)
         return fail(TIGRE_ERR_UNSUPPORTED, "exact adjoint needs (nx+4)(ny+4)(nz+4) < 2^31");
-    const FwdConst c = make_fwd_const(d);
+    const FwdConst c = make_fwd_const(g);
     bool need[2] = {false, false};
     for (int64_t a = a0; a < a0 + na; ++a) need[g->layout[(size_t)a]] = true;
     DeviceBuffer* bufs[2] = {&g->adj_xy, &g->adj_yx};

@@ -21,7 +21,7 @@ LIB = os.path.join(LIB_DIR, "libtigre103.so")
 SOURCES = ["geometry.cu", "forward.cu", "backward.cu", "tv.cu", "vecops.cu", "solvers.cu",
            "profile.cu", "forward_tma.cu", "tv_noalloc.cu", "ooc.cu", "siddon.cu",
            "fdk.cu", "rof.cu"]
-HEADERS = ["common.cuh", "ray.cuh", "vecops.cuh"]
+HEADERS = ["common.cuh", "ray.cuh", "vecops.cuh", "quad.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                      "-Xcompiler", "-fvisibility=hidden", "--expt-relaxed-constexpr",

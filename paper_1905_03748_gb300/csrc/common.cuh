@@ -128,9 +128,25 @@ struct FwdAngle {
     float dp[3];    // change of (P - S)/d per pixel along u
     float dq[3];    // change of (P - S)/d per pixel along v
     int layout;     // 0: x fastest (vol as given), 1: y fastest (transposed)
-    int pad_[3];
+    int index;      // the angle's index (its FwdAngle64 entry)
+    int pad_[2];
 };
 static_assert(sizeof(FwdAngle) == 64, "FwdAngle must stay 64 bytes");
+
+// The same vectors in FP64 (not rounded to FP32), for the once-per-geometry
+// search of rays whose FP32 sample count is wrong.
+struct FwdAngle64 {
+    double src[3], base[3], dp[3], dq[3];
+};
+
+// A ray whose FP32 set-up gets its sample count wrong: its pixel column and
+// its FP64 clip (rounded to FP32) and count.
+struct RayException {
+    int p;         // detector column
+    int K;         // samples (0: the ray misses the support)
+    float t0, t1;  // clip of src + t (P - S)
+    float len;     // chord length (mm)
+};
 
 // Per-angle parameters of the voxel-driven backprojector.
 struct BpAngle {
@@ -147,6 +163,10 @@ struct tigre_geometry {
     int device = -1;
     bool uploaded = false;
     tigre::DeviceBuffer fwd_params;   // FwdAngle[n_angles]
+    tigre::DeviceBuffer fwd_params64; // FwdAngle64[n_angles]
+    tigre::DeviceBuffer ray_exc_start; // int[n_angles * nv + 1]: rows' first exception
+    tigre::DeviceBuffer ray_exc;       // RayException[n_ray_exc], grouped by detector row
+    int64_t n_ray_exc = 0;
     tigre::DeviceBuffer bp_params;    // BpAngle[n_angles]
     tigre::DeviceBuffer angle_order;  // int[n_angles]: angle indices grouped by layout
     // Angle groups of 2 and 4 (index 0, 1) for the angle-interleaved forward
@@ -180,6 +200,9 @@ namespace tigre {
 constexpr int kPad = 2;  // zero voxels around the volume in the padded layouts
 
 tigre_status upload_params(tigre_geometry* g);
+// Sets every ray of the geometry up in FP32 (as the projector kernels do) and
+// in FP64, and keeps the rays whose sample counts differ (forward.cu).
+tigre_status build_ray_exceptions(tigre_geometry* g);
 // Detector row coordinates [lo, hi] (row index units, continuous) that any
 // point of the support with z in [za, zb] (voxel index units) projects to,
 // over all angles; false when the source can be inside the support (no bound).
@@ -193,7 +216,7 @@ tigre_status fill_padded_f32(const tigre_geometry_desc& d, const float* vol, flo
 tigre_status forward_slab_impl(tigre_geometry* g, const tigre_geometry_desc& sd, float* const pad[2],
                                float4* const quad[2], float* proj, int64_t a0, int64_t na,
                                int cell_lo, int cell_hi, int plane0, cudaStream_t st);
-// Bytes of the zero-bordered F32 projection buffer that slab launches of
+// Bytes of the zero-bordered F32 quad projection buffer that slab launches of
 // `slab` planes over na angles need at most (the largest row band).
 size_t bp_slab_pad_bytes(const tigre_geometry_desc& d, int64_t slab, int64_t na);
 tigre_status backward_slab_impl(tigre_geometry* g, const float* proj, float* vol_slab, int64_t a0,

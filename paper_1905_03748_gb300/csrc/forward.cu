@@ -26,12 +26,14 @@
 #include <cmath>
 #include <vector>
 
+#include "quad.cuh"
 #include "ray.cuh"
 
 namespace tigre {
 
-FwdConst make_fwd_const(const tigre_geometry_desc& d)
+FwdConst make_fwd_const(const tigre_geometry* g)
 {
+    const tigre_geometry_desc& d = g->desc;
     FwdConst c;
     c.nx = (int)d.n_voxel[0];
     c.ny = (int)d.n_voxel[1];
@@ -52,7 +54,132 @@ FwdConst make_fwd_const(const tigre_geometry_desc& d)
         diag2 += e * e;
     }
     c.kmax = (int)std::min(std::ceil(std::sqrt(diag2) / step) + 4.0, 1.0e8);
+    c.exc_start = (const int*)g->ray_exc_start.ptr;
+    c.exc = (const RayException*)g->ray_exc.ptr;
     return c;
+}
+
+// The clip of a ray to the support and its sample count in FP64, from the
+// FP64 vectors of its angle: t0, t1 (rounded to FP32) and the chord length
+// len (mm), K = max(1, ceil(len / step - 1e-9)) as the quadrature defines it;
+// 0 when the ray misses the support.
+__device__ __forceinline__ int ray_clip_f64(const FwdAngle64* __restrict__ P, int nf, int nm, int ns,
+                                         int p, int q, double u0, double v0, double du, double dv,
+                                         double dsd2, double inv_step, float* t0o, float* t1o,
+                                         float* leno)
+{
+    const double fp = (double)p, fq = (double)q;
+    const int n[3] = {nf, nm, ns};
+    double t0 = 0.0, t1 = 1.0;
+    for (int a = 0; a < 3; ++a) {
+        const double r = fma(fq, P->dq[a], fma(fp, P->dp[a], P->base[a]));
+        const double s = P->src[a];
+        if (r != 0.0) {
+            const double ta = (-1.0 - s) / r, tb = ((double)n[a] - s) / r;
+            t0 = fmax(t0, fmin(ta, tb));
+            t1 = fmin(t1, fmax(ta, tb));
+        } else if (!(s > -1.0 && s < (double)n[a])) {
+            return 0;
+        }
+    }
+    if (!(t1 > t0)) return 0;
+    const double u = fma(fp, du, u0), v = fma(fq, dv, v0);
+    const double len = (t1 - t0) * sqrt(dsd2 + u * u + v * v);
+    *t0o = (float)t0;
+    *t1o = (float)t1;
+    *leno = (float)len;
+    return max(1, (int)ceil(fma(len, inv_step, -1e-9)));
+}
+
+// FP64 constants of the detector frame for ray_clip_f64.
+struct FwdConst64 {
+    double u0, v0, du, dv, dsd2, inv_step;
+};
+
+// Every ray of angles [a_first, a_first + gridDim.y): set up in FP32 exactly
+// as the projector kernels do and in FP64; a ray whose counts differ is an
+// exception.  Pass 0 counts them per detector row, pass 1 (FILL) writes them
+// into their row's slots.
+template <bool FILL>
+__global__ void __launch_bounds__(256) ray_exception_kernel(
+    const FwdAngle* __restrict__ params, const FwdAngle64* __restrict__ p64, FwdConst c,
+    FwdConst64 d, int a_first, int* __restrict__ count, const int* __restrict__ start,
+    RayException* __restrict__ out)
+{
+    const int p = blockIdx.x * 32 + threadIdx.x;
+    const int q = blockIdx.z * blockDim.y + threadIdx.y;
+    const int a = a_first + (int)blockIdx.y;
+    if (p >= c.nu || q >= c.nv) return;
+    const FwdAngle* P = params + a;
+    const int layout = P->layout;
+    const int n[3] = {layout ? c.ny : c.nx, layout ? c.nx : c.ny, c.nz};
+    float r[3], t0 = 0.0f, t1 = 0.0f, len = 0.0f;
+    const int K32 = ray_clip_f32(P, c, p, q, n, r, t0, t1, len);
+    float t0d = 0.0f, t1d = 0.0f, lend = 0.0f;
+    const int K64 = ray_clip_f64(p64 + a, n[0], n[1], n[2], p, q, d.u0, d.v0, d.du, d.dv, d.dsd2,
+                                 d.inv_step, &t0d, &t1d, &lend);
+    if (K64 == K32) return;
+    const int row = a * c.nv + q;
+    const int slot = atomicAdd(count + row, 1);
+    if (FILL) out[start[row] + slot] = RayException{p, K64, t0d, t1d, lend};
+}
+
+tigre_status build_ray_exceptions(tigre_geometry* g)
+{
+    const tigre_geometry_desc& d = g->desc;
+    const int64_t na = (int64_t)g->angles.size();
+    const int64_t rows = na * d.n_det[1];
+    if (rows >= (int64_t)INT32_MAX) return fail(TIGRE_ERR_UNSUPPORTED, "too many detector rows");
+    TIGRE_TRY(g->ray_exc_start.ensure(sizeof(int) * (size_t)(rows + 1)));
+    DeviceBuffer counts;
+    TIGRE_TRY(counts.ensure(sizeof(int) * (size_t)rows));
+    FwdConst c = make_fwd_const(g);
+    c.exc_start = nullptr;
+    c.exc = nullptr;
+    const double dmin = std::min(d.d_voxel[0], std::min(d.d_voxel[1], d.d_voxel[2]));
+    const FwdConst64 c64{-0.5 * (double)(d.n_det[0] - 1) * d.d_det[0] + d.off_det[0],
+                         -0.5 * (double)(d.n_det[1] - 1) * d.d_det[1] + d.off_det[1],
+                         d.d_det[0], d.d_det[1], d.DSD * d.DSD, 1.0 / (d.accuracy * dmin)};
+    const FwdAngle* params = (const FwdAngle*)g->fwd_params.ptr;
+    const FwdAngle64* p64 = (const FwdAngle64*)g->fwd_params64.ptr;
+    auto pass = [&](bool fill) -> tigre_status {
+        TIGRE_CUDA(cudaMemset(counts.ptr, 0, sizeof(int) * (size_t)rows));
+        for (int64_t s = 0; s < na; s += 65535) {
+            const int64_t cnt = std::min<int64_t>(65535, na - s);
+            dim3 grid((unsigned)((c.nu + 31) / 32), (unsigned)cnt, (unsigned)((c.nv + 7) / 8));
+            if (fill)
+                ray_exception_kernel<true><<<grid, dim3(32, 8)>>>(
+                    params, p64, c, c64, (int)s, (int*)counts.ptr, (const int*)g->ray_exc_start.ptr,
+                    (RayException*)g->ray_exc.ptr);
+            else
+                ray_exception_kernel<false><<<grid, dim3(32, 8)>>>(params, p64, c, c64, (int)s,
+                                                                    (int*)counts.ptr, nullptr,
+                                                                    nullptr);
+            TIGRE_LAUNCHED("ray_exception_kernel");
+        }
+        return TIGRE_OK;
+    };
+    TIGRE_TRY(pass(false));
+    std::vector<int> start((size_t)rows + 1);
+    TIGRE_CUDA(cudaMemcpy(start.data() + 1, counts.ptr, sizeof(int) * (size_t)rows,
+                          cudaMemcpyDeviceToHost));
+    start[0] = 0;
+    int64_t total = 0;
+    for (int64_t r = 0; r < rows; ++r) {
+        total += start[(size_t)r + 1];
+        if (total >= (int64_t)INT32_MAX) return fail(TIGRE_ERR_UNSUPPORTED, "too many exceptions");
+        start[(size_t)r + 1] = (int)total;
+    }
+    TIGRE_CUDA(cudaMemcpy(g->ray_exc_start.ptr, start.data(), sizeof(int) * (size_t)(rows + 1),
+                          cudaMemcpyHostToDevice));
+    g->n_ray_exc = total;
+    if (total > 0) {
+        TIGRE_TRY(g->ray_exc.ensure(sizeof(RayException) * (size_t)total));
+        TIGRE_TRY(pass(true));
+    }
+    TIGRE_CUDA(cudaDeviceSynchronize());
+    counts.release();
+    return TIGRE_OK;
 }
 
 template <typename T>
@@ -166,40 +293,7 @@ __global__ void __launch_bounds__(256) fwd_l1_kernel(const TV* __restrict__ vxy,
 // Element (s, m, f) of a quad volume holds the four taps of the cell's lower
 // s-plane: (P[s][m][f], P[s][m][f+1], P[s][m+1][f], P[s][m+1][f+1]) of the
 // zero-padded layout P.  A trilinear sample is then two aligned loads (planes
-// s and s+1) instead of eight scalar ones.  F32 quads are float4 (16 B);
-// BF16/F16 quads are four 16-bit values in a uint2 (8 B).
-template <typename T> struct QuadOf;
-template <> struct QuadOf<float> { using type = float4; };
-template <> struct QuadOf<__nv_bfloat16> { using type = uint2; };
-template <> struct QuadOf<__half> { using type = uint2; };
-
-__device__ __forceinline__ float4 pack_quad(float a, float b, float c, float d)
-{
-    return make_float4(a, b, c, d);
-}
-__device__ __forceinline__ uint32_t bits16(__nv_bfloat16 v) { return __bfloat16_as_ushort(v); }
-__device__ __forceinline__ uint32_t bits16(__half v) { return __half_as_ushort(v); }
-template <typename T>
-__device__ __forceinline__ uint2 pack_quad16(T a, T b, T c, T d)
-{
-    return make_uint2(bits16(a) | (bits16(b) << 16), bits16(c) | (bits16(d) << 16));
-}
-
-__device__ __forceinline__ float4 load_quad(const float4* p, float*) { return __ldg(p); }
-__device__ __forceinline__ float4 load_quad(const uint2* p, __nv_bfloat16*)
-{
-    const uint2 q = __ldg(p);
-    return make_float4(__uint_as_float(q.x << 16), __uint_as_float(q.x & 0xffff0000u),
-                       __uint_as_float(q.y << 16), __uint_as_float(q.y & 0xffff0000u));
-}
-__device__ __forceinline__ float4 load_quad(const uint2* p, __half*)
-{
-    const uint2 q = __ldg(p);
-    return make_float4(__half2float(__ushort_as_half((unsigned short)(q.x & 0xffffu))),
-                       __half2float(__ushort_as_half((unsigned short)(q.x >> 16))),
-                       __half2float(__ushort_as_half((unsigned short)(q.y & 0xffffu))),
-                       __half2float(__ushort_as_half((unsigned short)(q.y >> 16))));
-}
+// s and s+1) instead of eight scalar ones (element types: quad.cuh).
 
 // Build the quad volume of a padded layout; one block per (s, m) row.
 template <typename T>
@@ -596,7 +690,7 @@ tigre_status forward_impl(tigre_geometry* g, const void* vol, tigre_dtype vt, vo
                     "in-core forward projection needs (nx+4)(ny+4)(nz+4) < 2^31; use out-of-core");
     if (d.n_det[1] > 65535 * 8)
         return fail(TIGRE_ERR_UNSUPPORTED, "detector too large for one launch");
-    const FwdConst c = make_fwd_const(d);
+    const FwdConst c = make_fwd_const(g);
     TIGRE_TRY(forward_workspace(g, vt, a0, na, st));
     bool need[2];
     needed_layouts(g, a0, na, need);
@@ -759,7 +853,7 @@ tigre_status forward_slab_impl(tigre_geometry* g, const tigre_geometry_desc& sd,
     const tigre_geometry_desc& d = g->desc;
     if (g->projector != TIGRE_PROJ_INTERPOLATED)
         return fail(TIGRE_ERR_UNSUPPORTED, "out-of-core projection is interpolated only");
-    const FwdConst c = make_fwd_const(d);
+    const FwdConst c = make_fwd_const(g);
     for (int l = 0; l < 2; ++l) {
         if (!pad[l]) continue;
         const int PF = (int)(l ? sd.n_voxel[1] : sd.n_voxel[0]) + 2 * kPad;
@@ -866,7 +960,7 @@ extern "C" tigre_status tigre_forward_samples(tigre_geometry_t g, int64_t angle_
     TIGRE_TRY(check_geometry(g));
     TIGRE_TRY(check_range(g, angle_begin, angle_count));
     if (!samples) return fail(TIGRE_ERR_INVALID_ARG, "null output");
-    const FwdConst c = make_fwd_const(g->desc);
+    const FwdConst c = make_fwd_const(g);
     unsigned long long* d = nullptr;
     TIGRE_CUDA(dev_alloc_sync((void**)&d, sizeof(unsigned long long)));
     tigre_status st = TIGRE_OK;

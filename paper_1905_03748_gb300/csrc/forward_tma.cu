@@ -484,7 +484,7 @@ tigre_status launch_forward_tma(tigre_geometry* g, const TV* vol, TP* proj, int6
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
         set = true;
     }
-    const FwdConst c = make_fwd_const(d);
+    const FwdConst c = make_fwd_const(g);
     ProfScope prof(kProfForward, st);
     for (int64_t s = 0; s < na; s += 65535) {
         const int64_t cnt = std::min<int64_t>(65535, na - s);

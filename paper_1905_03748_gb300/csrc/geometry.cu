@@ -270,6 +270,7 @@ tigre_status upload_params(tigre_geometry* g)
     const tigre_geometry_desc& d = g->desc;
     const int64_t na = (int64_t)g->angles.size();
     std::vector<FwdAngle> fwd((size_t)na);
+    std::vector<FwdAngle64> fwd64((size_t)na);
     std::vector<BpAngle> bp((size_t)na);
     g->layout.assign((size_t)na, 0);
     const double nu = (double)d.n_det[0], nv = (double)d.n_det[1];
@@ -294,14 +295,20 @@ tigre_status upload_params(tigre_geometry* g)
         const int layout = angle_layout(t);
         const int perm[3] = {layout ? 1 : 0, layout ? 0 : 1, 2};
         FwdAngle& f = fwd[(size_t)a];
+        FwdAngle64& f64 = fwd64[(size_t)a];
         std::memset(&f, 0, sizeof(f));
         for (int k = 0; k < 3; ++k) {
+            f64.src[k] = src[perm[k]];
+            f64.base[k] = base[perm[k]];
+            f64.dp[k] = dp[perm[k]];
+            f64.dq[k] = dq[perm[k]];
             f.src[k] = (float)src[perm[k]];
             f.base[k] = (float)base[perm[k]];
             f.dp[k] = (float)dp[perm[k]];
             f.dq[k] = (float)dq[perm[k]];
         }
         f.layout = layout;
+        f.index = (int)a;
         g->layout[(size_t)a] = layout;
         bp[(size_t)a] = BpAngle{(float)c, (float)s, (float)S[0], (float)S[1]};
     }
@@ -328,8 +335,12 @@ tigre_status upload_params(tigre_geometry* g)
     }
     TIGRE_TRY(g->fwd_params.ensure(sizeof(FwdAngle) * (size_t)na));
     TIGRE_TRY(g->bp_params.ensure(sizeof(BpAngle) * (size_t)na));
+    TIGRE_TRY(g->fwd_params64.ensure(sizeof(FwdAngle64) * (size_t)na));
     TIGRE_CUDA(cudaMemcpy(g->fwd_params.ptr, fwd.data(), sizeof(FwdAngle) * (size_t)na,
                           cudaMemcpyHostToDevice));
+    TIGRE_CUDA(cudaMemcpy(g->fwd_params64.ptr, fwd64.data(), sizeof(FwdAngle64) * (size_t)na,
+                          cudaMemcpyHostToDevice));
+    TIGRE_TRY(build_ray_exceptions(g));
     TIGRE_CUDA(cudaMemcpy(g->bp_params.ptr, bp.data(), sizeof(BpAngle) * (size_t)na,
                           cudaMemcpyHostToDevice));
     g->uploaded = true;
@@ -374,6 +385,9 @@ tigre_status tigre_geometry_destroy(tigre_geometry_t g)
 {
     if (!g) return TIGRE_OK;
     g->fwd_params.release();
+    g->fwd_params64.release();
+    g->ray_exc_start.release();
+    g->ray_exc.release();
     g->bp_params.release();
     g->angle_order.release();
     g->angle_groups[0].release();

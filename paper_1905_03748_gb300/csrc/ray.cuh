@@ -14,9 +14,14 @@ struct FwdConst {
     float dsd2;      // DSD^2 (mm^2)
     float inv_step;  // 1 / (accuracy * min d)
     int kmax;        // more samples than the support's diagonal allows = corrupt ray
+    // Rays whose sample count FP32 gets wrong (see setup_ray): entries
+    // [exc_start[row], exc_start[row + 1]) of exc for the detector row
+    // row = angle * nv + q.
+    const int* exc_start;
+    const RayException* exc;
 };
 
-FwdConst make_fwd_const(const tigre_geometry_desc& d);
+FwdConst make_fwd_const(const tigre_geometry* g);
 
 // Integer part and fraction of x for 0.5 <= x < 2^22 (below about 0.25 the
 // sum leaves the [2^23, 2^24) binade and the split is wrong, so callers keep
@@ -27,20 +32,6 @@ __device__ __forceinline__ void split_floor(float x, int& i, float& f)
     const float m = __fadd_rn(x, 8388607.5f);
     i = __float_as_int(m) - 0x4B000000;
     f = __fsub_rn(x, __fsub_rn(m, 8388608.0f));
-}
-
-// Clip parameter range [t0, t1] of src + t r to (-1, n) along one axis.
-__device__ __forceinline__ void clip_axis(float src, float r, int n, float& t0, float& t1)
-{
-    const float lo = -1.0f, hi = (float)n;
-    if (r != 0.0f) {
-        const float inv = 1.0f / r;
-        const float ta = (lo - src) * inv, tb = (hi - src) * inv;
-        t0 = fmaxf(t0, fminf(ta, tb));
-        t1 = fminf(t1, fmaxf(ta, tb));
-    } else if (!(src > lo && src < hi)) {
-        t1 = -1.0f;  // parallel to the slab and outside it: empty
-    }
 }
 
 // One ray in the padded index coordinates of its angle's layout.
@@ -54,6 +45,45 @@ struct Ray {
     bool ok;      // all samples provably inside the padded volume
 };
 
+// The FP32 set-up of ray (p, q): clip to the support (-1, n) per axis,
+// chord length len (mm) and K = max(1, ceil(len / step)), 0 for a miss.
+// Every operation is written with an explicit rounding (no contraction left
+// to the compiler), so that each kernel that inlines it gets the same bits:
+// the exception table below is built from this very computation.
+__device__ __forceinline__ int ray_clip_f32(const FwdAngle* __restrict__ P, const FwdConst& c,
+                                            int p, int q, const int n[3], float r[3], float& t0,
+                                            float& t1, float& len)
+{
+    const float fp = (float)p, fq = (float)q;
+    t0 = 0.0f;
+    t1 = 1.0f;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        r[a] = fmaf(fq, P->dq[a], fmaf(fp, P->dp[a], P->base[a]));
+        const float s = P->src[a];
+        if (r[a] != 0.0f) {
+            const float inv = __frcp_rn(r[a]);
+            const float ta = __fmul_rn(__fsub_rn(-1.0f, s), inv);
+            const float tb = __fmul_rn(__fsub_rn((float)n[a], s), inv);
+            t0 = fmaxf(t0, fminf(ta, tb));
+            t1 = fminf(t1, fmaxf(ta, tb));
+        } else if (!(s > -1.0f && s < (float)n[a])) {
+            t1 = -1.0f;  // parallel to the slab and outside it: empty
+        }
+    }
+    if (!(t1 > t0)) return 0;
+    const float u = fmaf(fp, c.du, c.u0), v = fmaf(fq, c.dv, c.v0);
+    len = __fmul_rn(__fsub_rn(t1, t0), __fsqrt_rn(fmaf(v, v, fmaf(u, u, c.dsd2))));
+    return max(1, (int)ceilf(__fmul_rn(len, c.inv_step)));
+}
+
+// A ray of the geometry: its first sample, step, weight and sample count.
+// The count is the quadrature's K = max(1, ceil(len / step - 1e-9)) with len
+// from the exact chord.  FP32 carries len / step only to a few 1e-4 (more for
+// rays that cross a face at a shallow angle), so for about one ray in a few
+// thousand its ceil differs; those rays were found once per geometry by
+// setting every ray up in FP64 as well, and their FP64 clip and count are
+// looked up here.
 __device__ __forceinline__ void setup_ray(const FwdAngle* __restrict__ P, const FwdConst& c,
                                           int p, int q, Ray& R)
 {
@@ -61,21 +91,23 @@ __device__ __forceinline__ void setup_ray(const FwdAngle* __restrict__ P, const 
     R.nf = R.layout ? c.ny : c.nx;
     R.nm = R.layout ? c.nx : c.ny;
     R.ns = c.nz;
-    const float fp = (float)p, fq = (float)q;
-    const float r[3] = {fmaf(fq, P->dq[0], fmaf(fp, P->dp[0], P->base[0])),
-                        fmaf(fq, P->dq[1], fmaf(fp, P->dp[1], P->base[1])),
-                        fmaf(fq, P->dq[2], fmaf(fp, P->dp[2], P->base[2]))};
-    float t0 = 0.0f, t1 = 1.0f;
-    clip_axis(P->src[0], r[0], R.nf, t0, t1);
-    clip_axis(P->src[1], r[1], R.nm, t0, t1);
-    clip_axis(P->src[2], r[2], R.ns, t0, t1);
-    R.K = 0;
+    const int n[3] = {R.nf, R.nm, R.ns};
+    float r[3], t0, t1, len;
+    R.K = ray_clip_f32(P, c, p, q, n, r, t0, t1, len);
+    R.h = 0.0f;
     R.ok = true;
-    if (!(t1 > t0)) return;
-    const float u = fmaf(fp, c.du, c.u0), v = fmaf(fq, c.dv, c.v0);
-    const float len = (t1 - t0) * sqrtf(c.dsd2 + u * u + v * v);
-    // K = ceil(len / step); the small guard keeps exact multiples exact.
-    R.K = max(1, (int)ceilf(fmaf(len, c.inv_step, -1e-3f)));
+    const int row = P->index * c.nv + q;
+    for (int e = c.exc_start[row], end = c.exc_start[row + 1]; e < end; ++e) {
+        const RayException x = c.exc[e];
+        if (x.p == p) {
+            R.K = x.K;
+            t0 = x.t0;
+            t1 = x.t1;
+            len = x.len;
+            break;
+        }
+    }
+    if (R.K == 0) return;
     if (!(R.K <= c.kmax)) {
         R.ok = false;
         return;
@@ -84,7 +116,6 @@ __device__ __forceinline__ void setup_ray(const FwdAngle* __restrict__ P, const 
     const float dt = (t1 - t0) * invK;
     const float tm = fmaf(0.5f, dt, t0);
     R.h = len * invK;
-    const int n[3] = {R.nf, R.nm, R.ns};
     const float kl = (float)(R.K - 1);
     for (int a = 0; a < 3; ++a) {
         R.x0[a] = fmaf(tm, r[a], P->src[a]) + (float)kPad;

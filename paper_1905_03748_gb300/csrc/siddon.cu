@@ -148,7 +148,7 @@ template <typename TV, typename TP>
 tigre_status launch_siddon_forward(tigre_geometry* g, const TV* vxy, const TV* vyx, TP* proj,
                                    int64_t a0, int64_t na, const int* order, cudaStream_t st)
 {
-    const FwdConst c = make_fwd_const(g->desc);
+    const FwdConst c = make_fwd_const(g);
     ProfScope prof(kProfForward, st);
     for (int64_t s = 0; s < na; s += 65535) {
         const int64_t cnt = std::min<int64_t>(65535, na - s);
@@ -165,7 +165,7 @@ template <typename TP>
 tigre_status launch_siddon_scatter(tigre_geometry* g, const TP* proj, float* acc_xy, float* acc_yx,
                                    int64_t a0, int64_t na, cudaStream_t st)
 {
-    const FwdConst c = make_fwd_const(g->desc);
+    const FwdConst c = make_fwd_const(g);
     for (int64_t s = 0; s < na; s += 65535) {
         const int64_t cnt = std::min<int64_t>(65535, na - s);
         dim3 grid((unsigned)((c.nu + 31) / 32), (unsigned)cnt, (unsigned)((c.nv + 7) / 8));
