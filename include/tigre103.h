@@ -308,6 +308,38 @@ TIGRE_API tigre_status tigre_cgls_iterate(tigre_cgls_t state, int n_iter);
 TIGRE_API tigre_status tigre_cgls_history(tigre_cgls_t state, double* resid_hist, int n);
 TIGRE_API tigre_status tigre_cgls_end(tigre_cgls_t state);
 
+/* Batched CGLS (no counterpart in the paper, which reconstructs one volume at
+ * a time with the Sec. 3.2 CGLS; a service for reconstruction servers): batch
+ * problems that share the geometry handle and opts->storage, iterated
+ * together.  Each iteration projects the batch's search directions in ONE
+ * forward-projector launch and backprojects its residuals in ONE voxel-driven
+ * backprojector launch (the member index runs over the grid); inner
+ * products, norms, step lengths and vector updates are each member's own.
+ * Every member's x and residual history are bitwise those of tigre_cgls on
+ * that problem alone.
+ * begin: projs[i] (b) and vols[i] (x0, updated in place) are DEVICE buffers
+ *        in opts->storage, valid until end.  Flags: TIGRE_GRAPH (replay
+ *        captured iteration pairs; needs a non-default stream) and
+ *        TIGRE_X0_ZERO (x_i zeroed, r_i = b_i).  The handle must use the
+ *        interpolated projector and the automatic forward path; bp_weight
+ *        MATCHED or FDK.  Workspaces (owned by the batch, stream-ordered on
+ *        opts->cuda_stream): per member 4 iterate vectors, 2 padded and 2 quad
+ *        copies of the volume per layout, and a quad copy of the padded
+ *        projections.  Otherwise as tigre_cgls_begin; TIGRE_ERR_UNSUPPORTED for
+ *        other flags, projectors or weights.
+ * iterate: enqueues n_iter iterations of every member (no host sync).
+ * history: the first n residual norms of member member_index (synchronises).
+ * end:   releases the workspaces (stream-ordered) and the handle. */
+typedef struct tigre_cgls_batch* tigre_cgls_batch_t;
+TIGRE_API tigre_status tigre_cgls_batch_begin(tigre_geometry_t geo, int batch,
+                                              const void* const* projs, void* const* vols,
+                                              const tigre_solver_opts* opts,
+                                              tigre_cgls_batch_t* out);
+TIGRE_API tigre_status tigre_cgls_batch_iterate(tigre_cgls_batch_t state, int n_iter);
+TIGRE_API tigre_status tigre_cgls_batch_history(tigre_cgls_batch_t state, int member_index,
+                                                double* resid_hist, int n);
+TIGRE_API tigre_status tigre_cgls_batch_end(tigre_cgls_batch_t state);
+
 /* Checkpoint / resume of a stepwise CGLS (no counterpart in the paper; lets a
  * long reconstruction stop and continue, e.g. across job limits or when a
  * server preempts it).  save: copies the state's residual r (n_angles x nv x

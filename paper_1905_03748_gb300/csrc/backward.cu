@@ -32,6 +32,7 @@
 // forward projector, so a warp's atomics hit adjacent addresses).
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 
 #include "quad.cuh"
 #include "ray.cuh"
@@ -89,21 +90,49 @@ template <typename TP> struct ProjTaps<TP, true> {
 // projections (the normaliser V^-1 = A_w^T 1, from the same weights and
 // interpolation) and finish with vol += lambda * num / den (den > 1e-12),
 // clamped at zero when nonneg.
-// Occupancy: 5 blocks per SM (48 registers, no spills) measured 11 % faster
-// than the unconstrained 62-register build; 6 blocks (40 registers) gained
-// nothing more.  The SART form, with twice the accumulators, keeps 3.
+// Occupancy (512^3 x 360, one launch): plain buffer, 16 voxels per thread,
+// 5 blocks per SM (48 registers): matched 51.2 ms, FDK 46.5 ms.  Quad buffer:
+// matched 48.4 ms with 8 voxels per thread at 8 blocks per SM (62 ms with 16
+// at 5, 53.6 ms with 16 at 4); FDK 36.0 ms with 16 at 4 blocks (49 ms at 5,
+// 39.9 ms with 8 at 8).  The SART form, with twice the accumulators, keeps 3.
+template <int MODE, bool SART, bool QUADP>
+constexpr int bp_blocks_per_sm()
+{
+    return SART ? 3 : !QUADP ? 5 : MODE == TIGRE_BP_FDK ? 4 : 8;
+}
+template <int MODE, bool QUADP>
+constexpr int bp_voxels_per_thread()
+{
+    return QUADP && MODE != TIGRE_BP_FDK ? 8 : 16;
+}
+static_assert(bp_voxels_per_thread<TIGRE_BP_FDK, false>() <= kBpNZ &&
+                  bp_voxels_per_thread<TIGRE_BP_MATCHED, true>() <= kBpNZ,
+              "the row-band bounds assume chunks of at most kBpNZ planes");
+
+// Members of a batched launch: blockIdx.z = member * chunks + z chunk; member
+// i reads projections proj_stride elements and writes the volume vol_stride
+// voxels after member 0's.  The default is a single member.
+struct BpBatch {
+    int chunks = 1 << 30;
+    int64_t proj_stride = 0, vol_stride = 0;
+};
+
 template <typename TP, typename TV, int NZ, int MODE, bool SART, bool QUADP>
-__global__ void __launch_bounds__(256, SART ? 3 : 5) bp_voxel_kernel(
+__global__ void __launch_bounds__(256, (bp_blocks_per_sm<MODE, SART, QUADP>())) bp_voxel_kernel(
                                                        const typename ProjTaps<TP, QUADP>::E* __restrict__ pp,
                                                        TV* __restrict__ vol,
                                                        const BpAngle* __restrict__ params,
                                                        BpConst c, int a_first, int na,
                                                        int accumulate, float lambda = 0.0f,
-                                                       int nonneg = 0)
+                                                       int nonneg = 0,
+                                                       BpBatch bt = BpBatch{})
 {
+    const int member = (int)blockIdx.z / bt.chunks;
+    pp += member * bt.proj_stride;
+    vol += member * bt.vol_stride;
     const int x = blockIdx.x * 32 + threadIdx.x;
     const int y = blockIdx.y * 8 + threadIdx.y;
-    const int zb = c.z_first + blockIdx.z * NZ;
+    const int zb = c.z_first + ((int)blockIdx.z - member * bt.chunks) * NZ;
     if (x >= c.nx || y >= c.ny) return;
     const float X = fmaf((float)x, c.dx, c.x0);
     const float Y = fmaf((float)y, c.dy, c.y0);
@@ -385,11 +414,11 @@ size_t bp_slab_pad_bytes(const tigre_geometry_desc& d, int64_t slab, int64_t na)
 }
 
 // Whether an in-core backprojection with weight w reads the quad buffer
-// (slab launches always read the plain band).
+// (both voxel-driven weights do; slab launches and the SART update, whose
+// normaliser doubles the accumulators, read the plain buffer).
 static bool bp_reads_quads(tigre_bp_weight w)
 {
-    (void)w;
-    return false;
+    return w == TIGRE_BP_MATCHED || w == TIGRE_BP_FDK;
 }
 
 tigre_status backward_workspace(tigre_geometry* g, tigre_dtype pt, tigre_bp_weight w, int64_t a0,
@@ -417,42 +446,59 @@ tigre_status backward_workspace(tigre_geometry* g, tigre_dtype pt, tigre_bp_weig
 template <typename TP, typename TV, bool QUADP>
 static tigre_status run_voxel_bp(tigre_geometry* g, const BpConst& c, const TP* proj, TV* vol,
                                  int64_t a0, int64_t na, tigre_bp_weight w, int accumulate,
-                                 cudaStream_t st, bool sart, float lambda, int nonneg)
+                                 cudaStream_t st, bool sart, float lambda, int nonneg,
+                                 int batch = 1, void* ws = nullptr)
 {
     using Q = typename ProjTaps<TP, QUADP>::E;
     static_assert(sizeof(Q) == (QUADP ? 4 : 1) * sizeof(TP), "a quad is four elements");
     const size_t pelems = (size_t)na * (size_t)c.PU * (size_t)c.PV;
-    TIGRE_TRY(g->proj_pad.ensure(pelems * sizeof(Q)));
-    g->proj_pad.tag = 0;
-    Q* pp = (Q*)g->proj_pad.ptr;
-    for (int64_t s = 0; s < na; s += 65535) {
-        const int64_t cnt = std::min<int64_t>(65535, na - s);
+    Q* pp = (Q*)ws;
+    if (!pp) {
+        TIGRE_TRY(g->proj_pad.ensure(pelems * sizeof(Q)));
+        g->proj_pad.tag = 0;
+        pp = (Q*)g->proj_pad.ptr;
+    }
+    // a batch's projections are consecutive angle blocks of one long buffer
+    for (int64_t s = 0; s < na * batch; s += 65535) {
+        const int64_t cnt = std::min<int64_t>(65535, na * batch - s);
         dim3 grid((unsigned)((c.PU + 255) / 256), (unsigned)c.PV, (unsigned)cnt);
         pad_proj_kernel<TP, QUADP><<<grid, 256, 0, st>>>(proj + s * (int64_t)c.nu * c.nv,
                                                    pp + s * (int64_t)c.PU * c.PV, c.nu, c.nv,
                                                    c.PU, c.PV, c.pv_lo);
         TIGRE_LAUNCHED("pad_proj_kernel");
     }
-    dim3 grid((unsigned)((c.nx + 31) / 32), (unsigned)((c.ny + 7) / 8),
-              (unsigned)((c.z_end - c.z_first + kBpNZ - 1) / kBpNZ));
-    if (grid.y > 65535 || grid.z > 65535) return fail(TIGRE_ERR_UNSUPPORTED, "volume too large");
     const BpAngle* params = (const BpAngle*)g->bp_params.ptr;
     const dim3 block(32, 8);
     ProfScope prof(kProfBackproject, st);
-    if (sart) {
-        if (w == TIGRE_BP_FDK)
-            bp_voxel_kernel<TP, TV, kBpNZ, TIGRE_BP_FDK, true, QUADP><<<grid, block, 0, st>>>(
-                pp, vol, params, c, (int)a0, (int)na, 0, lambda, nonneg);
-        else
-            bp_voxel_kernel<TP, TV, kBpNZ, TIGRE_BP_MATCHED, true, QUADP><<<grid, block, 0, st>>>(
-                pp, vol, params, c, (int)a0, (int)na, 0, lambda, nonneg);
-    } else if (w == TIGRE_BP_FDK) {
-        bp_voxel_kernel<TP, TV, kBpNZ, TIGRE_BP_FDK, false, QUADP><<<grid, block, 0, st>>>(
-            pp, vol, params, c, (int)a0, (int)na, accumulate);
-    } else {
-        bp_voxel_kernel<TP, TV, kBpNZ, TIGRE_BP_MATCHED, false, QUADP><<<grid, block, 0, st>>>(
-            pp, vol, params, c, (int)a0, (int)na, accumulate);
-    }
+    // One kernel instance: MODE and SART fixed, NZ voxels per thread.
+    auto launch = [&](auto mode, auto sart_tag) -> tigre_status {
+        constexpr int M = decltype(mode)::value;
+        constexpr bool S = decltype(sart_tag)::value;
+        constexpr int NZ = bp_voxels_per_thread<M, QUADP>();
+        const int chunks = (c.z_end - c.z_first + NZ - 1) / NZ;
+        dim3 grid((unsigned)((c.nx + 31) / 32), (unsigned)((c.ny + 7) / 8),
+                  (unsigned)((int64_t)chunks * batch));
+        if (grid.y > 65535 || (int64_t)chunks * batch > 65535)
+            return fail(TIGRE_ERR_UNSUPPORTED, "volume too large");
+        BpBatch bt;
+        if (batch > 1) {
+            bt.chunks = chunks;
+            bt.proj_stride = (int64_t)pelems;
+            bt.vol_stride = (int64_t)c.nx * c.ny * c.nz;
+        }
+        bp_voxel_kernel<TP, TV, NZ, M, S, QUADP><<<grid, block, 0, st>>>(
+            pp, vol, params, c, (int)a0, (int)na, S ? 0 : accumulate, lambda, nonneg, bt);
+        return TIGRE_OK;
+    };
+    using Fdk = std::integral_constant<int, TIGRE_BP_FDK>;
+    using Matched = std::integral_constant<int, TIGRE_BP_MATCHED>;
+    tigre_status ls;
+    if (sart)
+        ls = w == TIGRE_BP_FDK ? launch(Fdk{}, std::true_type{}) : launch(Matched{}, std::true_type{});
+    else
+        ls = w == TIGRE_BP_FDK ? launch(Fdk{}, std::false_type{})
+                               : launch(Matched{}, std::false_type{});
+    TIGRE_TRY(ls);
     TIGRE_LAUNCHED("bp_voxel_kernel");
     return TIGRE_OK;
 }
@@ -476,12 +522,33 @@ tigre_status launch_voxel_bp(tigre_geometry* g, const TP* proj, TV* vol, int64_t
         bp_slab_band(c, d, z_first, z_end);
     }
     // In-core launches read quads where they pay, slab launches the plain band.
-    return z_end < 0 && bp_reads_quads(w) ? run_voxel_bp<TP, TV, true>(g, c, proj, vol, a0, na, w, accumulate, st, sart,
+    return z_end < 0 && !sart && bp_reads_quads(w) ? run_voxel_bp<TP, TV, true>(g, c, proj, vol, a0, na, w, accumulate, st, sart,
                                                   lambda, nonneg)
                      : run_voxel_bp<TP, TV, false>(g, c, proj, vol, a0, na, w, accumulate, st,
                                                    sart, lambda, nonneg);
 }
 
+
+size_t backward_batch_workspace_bytes(const tigre_geometry* g, tigre_dtype dt)
+{
+    const BpConst c = make_bp_const(g->desc);
+    return (size_t)g->angles.size() * (size_t)c.PU * (size_t)c.PV * 4 * dtype_size(dt);
+}
+
+tigre_status backward_batch_impl(tigre_geometry* g, const void* projs, void* vols, int batch,
+                                 tigre_dtype dt, tigre_bp_weight w, void* ws, cudaStream_t st)
+{
+    TIGRE_TRY(check_geometry(g));
+    if (!bp_reads_quads(w))
+        return fail(TIGRE_ERR_UNSUPPORTED, "batched backprojection: matched or FDK weights");
+    const BpConst c = make_bp_const(g->desc);
+    const int64_t na = (int64_t)g->angles.size();
+    return dispatch_dtype(dt, [&](auto tag) -> tigre_status {
+        using T = decltype(tag);
+        return run_voxel_bp<T, T, true>(g, c, (const T*)projs, (T*)vols, 0, na, w, 0, st, false,
+                                        0.0f, 0, batch, ws);
+    });
+}
 
 tigre_status backward_slab_impl(tigre_geometry* g, const float* proj, float* vol_slab, int64_t a0,
                                 int64_t na, tigre_bp_weight w, int accumulate, int z_first,

@@ -401,6 +401,14 @@ struct SlabRange {
     const int2* prange;
 };
 
+// Members of a batched launch: blockIdx.z = member * tiles + row tile; member
+// i's quad volumes start vol_stride quads and its projections proj_stride
+// elements after member 0's.  The default is a single member.
+struct FwdBatch {
+    int tiles = 1 << 30;
+    int64_t vol_stride = 0, proj_stride = 0;
+};
+
 // First k in [0, K] whose z cell satisfies pred (pred monotone along the ray).
 template <typename P>
 __device__ __forceinline__ int first_k(int K, P pred)
@@ -452,19 +460,26 @@ __device__ __forceinline__ void cut_axis(const Ray& R, int ax, int lo, int hi, i
 // Occupancy: 6 blocks per SM (40 registers) hides more gather latency than
 // the unconstrained 44-register build (5 blocks): 136 vs 144 ms per 512^3 x
 // 360 projection; 7 blocks spill.
+// With a Batch, several volumes of the same geometry are projected in one
+// launch (blockIdx.z runs over member 0's row tiles, then member 1's, ...).
 template <typename TV, typename TP, bool SLAB = false, bool PAIR = false, int AG = 1>
 __global__ void __launch_bounds__(256, 6) fwd_quad_kernel(
     const typename QuadOf<TV>::type* __restrict__ qxy,
     const typename QuadOf<TV>::type* __restrict__ qyx, TP* __restrict__ proj,
     const FwdAngle* __restrict__ params, FwdConst c, int a_first, const int* __restrict__ order,
-    SlabRange sr)
+    SlabRange sr, FwdBatch bt = FwdBatch{})
 {
     static_assert(AG == 1 || (!SLAB && !PAIR), "angle groups: in-core single-sample march only");
     using Q = typename QuadOf<TV>::type;
     constexpr int CW = 32 / AG;  // detector columns per warp
     const unsigned full = 0xffffffffu;
+    const int member = (int)blockIdx.z / bt.tiles;
+    const int tile = (int)blockIdx.z - member * bt.tiles;
+    qxy += member * bt.vol_stride;
+    qyx += member * bt.vol_stride;
+    proj += member * bt.proj_stride;
     const int p = blockIdx.x * CW + (AG == 1 ? (int)threadIdx.x : (int)threadIdx.x % CW);
-    const int q = (SLAB ? sr.q0 : 0) + (int)(blockIdx.z * blockDim.y + threadIdx.y);
+    const int q = (SLAB ? sr.q0 : 0) + tile * (int)blockDim.y + (int)threadIdx.y;
     const int a = AG > 1  ? order[blockIdx.y * AG + threadIdx.x / CW]
                   : order ? order[blockIdx.y]
                           : (int)blockIdx.y;
@@ -753,7 +768,7 @@ tigre_status forward_impl(tigre_geometry* g, const void* vol, tigre_dtype vt, vo
                 kern<<<grid, dim3(32, 8), 0, st>>>(
                     (const Q*)g->vol_qxy.ptr, (const Q*)g->vol_qyx.ptr, (TP*)proj,
                     (const FwdAngle*)g->fwd_params.ptr, c, 0, (const int*)g->angle_groups[gi].ptr,
-                    SlabRange{0, 0, 0, 0, 0, 0, 0, 0, nullptr});
+                    SlabRange{0, 0, 0, 0, 0, 0, 0, 0, nullptr}, FwdBatch{});
                 TIGRE_LAUNCHED("fwd_quad_kernel");
                 return TIGRE_OK;
             }
@@ -767,7 +782,7 @@ tigre_status forward_impl(tigre_geometry* g, const void* vol, tigre_dtype vt, vo
                     kern<<<grid, dim3(32, 8), 0, st>>>(
                         (const Q*)g->vol_qxy.ptr, (const Q*)g->vol_qyx.ptr,
                         (TP*)proj + s * (int64_t)c.nu * c.nv, (const FwdAngle*)g->fwd_params.ptr,
-                        c, (int)(a0 + s), order, SlabRange{0, 0, 0, 0, 0, 0, 0, 0, nullptr});
+                        c, (int)(a0 + s), order, SlabRange{0, 0, 0, 0, 0, 0, 0, 0, nullptr}, FwdBatch{});
                     TIGRE_LAUNCHED("fwd_quad_kernel");
                 }
                 return TIGRE_OK;
@@ -784,6 +799,61 @@ tigre_status forward_impl(tigre_geometry* g, const void* vol, tigre_dtype vt, vo
             }
             return TIGRE_OK;
         });
+    });
+}
+
+tigre_status forward_batch_impl(tigre_geometry* g, const void* vols, void* projs, int batch,
+                                 tigre_dtype dt, void* const pad[2], void* const quad[2],
+                                 cudaStream_t st)
+{
+    TIGRE_TRY(check_geometry(g));
+    const tigre_geometry_desc& d = g->desc;
+    const int64_t na = (int64_t)g->angles.size();
+    if (g->projector != TIGRE_PROJ_INTERPOLATED || g->fwd_path != 0)
+        return fail(TIGRE_ERR_UNSUPPORTED, "batched projection: interpolated projector, automatic path");
+    if (padded_elems(d) >= (size_t)INT32_MAX || na > 65535)
+        return fail(TIGRE_ERR_UNSUPPORTED, "batched projection: volume or angle count too large");
+    const FwdConst c = make_fwd_const(g);
+    const int tiles = (c.nv + 7) / 8;
+    if ((int64_t)tiles * batch > 65535) return fail(TIGRE_ERR_UNSUPPORTED, "batch too large");
+    bool need[2];
+    needed_layouts(g, 0, na, need);
+    const int64_t nvox = d.n_voxel[0] * d.n_voxel[1] * d.n_voxel[2];
+    const int64_t pe = (int64_t)padded_elems(d);
+    return dispatch_dtype(dt, [&](auto tag) -> tigre_status {
+        using T = decltype(tag);
+        using Q = typename QuadOf<T>::type;
+        for (int i = 0; i < batch; ++i)
+            for (int l = 0; l < 2; ++l) {
+                if (!need[l]) continue;
+                T* pl = (T*)pad[l] + i * pe;
+                TIGRE_TRY(fill_padded<T>(d, (const T*)vols + i * nvox, pl, l, st));
+                const int PF = (int)(l ? d.n_voxel[1] : d.n_voxel[0]) + 2 * kPad;
+                const int PM = (int)(l ? d.n_voxel[0] : d.n_voxel[1]) + 2 * kPad;
+                const int64_t rows = (int64_t)PM * (d.n_voxel[2] + 2 * kPad);
+                quad_kernel<T><<<(unsigned)rows, 128, 0, st>>>(pl, (Q*)quad[l] + i * pe, PF, PM, rows);
+                TIGRE_LAUNCHED("quad_kernel");
+            }
+        FwdBatch bt;
+        bt.tiles = tiles;
+        bt.vol_stride = pe;
+        bt.proj_stride = na * c.nu * c.nv;
+        ProfScope prof(kProfForward, st);
+        // the automatic path of forward_impl for a full-range projection
+        if (g->auto_angle_group == 2) {
+            dim3 grid((unsigned)((c.nu + 15) / 16), (unsigned)g->n_groups[0], (unsigned)(tiles * batch));
+            fwd_quad_kernel<T, T, false, false, 2><<<grid, dim3(32, 8), 0, st>>>(
+                (const Q*)quad[0], (const Q*)quad[1], (T*)projs, (const FwdAngle*)g->fwd_params.ptr,
+                c, 0, (const int*)g->angle_groups[0].ptr, SlabRange{0, 0, 0, 0, 0, 0, 0, 0, nullptr},
+                bt);
+        } else {
+            dim3 grid((unsigned)((c.nu + 31) / 32), (unsigned)na, (unsigned)(tiles * batch));
+            fwd_quad_kernel<T, T, false, false><<<grid, dim3(32, 8), 0, st>>>(
+                (const Q*)quad[0], (const Q*)quad[1], (T*)projs, (const FwdAngle*)g->fwd_params.ptr,
+                c, 0, (const int*)g->angle_order.ptr, SlabRange{0, 0, 0, 0, 0, 0, 0, 0, nullptr}, bt);
+        }
+        TIGRE_LAUNCHED("fwd_quad_kernel(batch)");
+        return TIGRE_OK;
     });
 }
 
@@ -902,7 +972,7 @@ tigre_status forward_slab_impl(tigre_geometry* g, const tigre_geometry_desc& sd,
                           (unsigned)((q_hi - q_lo + 7) / 8));
                 kern<<<grid, dim3(32, 8), 0, st>>>(
                     quad[0], quad[1], proj + s * (int64_t)c.nu * c.nv,
-                    (const FwdAngle*)g->fwd_params.ptr, c, (int)(a0 + s), nullptr, sr);
+                    (const FwdAngle*)g->fwd_params.ptr, c, (int)(a0 + s), nullptr, sr, FwdBatch{});
                 TIGRE_LAUNCHED("fwd_quad_kernel(slab)");
             }
         }

@@ -461,8 +461,9 @@ size_t placement1_workspace(const tigre_geometry* g, int64_t slab, const bool ne
     const int64_t plane = d.n_voxel[0] * d.n_voxel[1];
     const int64_t nslab = (d.n_voxel[2] + slab - 1) / slab;
     const size_t fwd = sizeof(float) * (size_t)(2 * plane * (slab + 1)) + FwdSlabs::bytes(d, slab, need);
-    // the backprojection's two slab buffers, or the direction update's two
-    const size_t bwd = sizeof(float) * (size_t)(2 * plane * slab) +
+    // the backprojection's projection band (kept by the handle afterwards)
+    // with its two slab buffers, or with the direction update's two pairs
+    const size_t bwd = sizeof(float) * (size_t)(4 * plane * slab) +
                        bp_slab_pad_bytes(d, slab, (int64_t)g->angles.size());
     return std::max(fwd, bwd) + sizeof(double) * (size_t)(nslab + 2 * kRedBlocks + kScalarSlots);
 }
@@ -540,29 +541,46 @@ static tigre_status cgls_host_vectors(tigre_geometry* g, const float* b_host, fl
     double* qq = sc + kRedBlocks;       // [2]
     double* rr = sc + kRedBlocks + 2;   // [2]
     double* gam = sc + kRedBlocks + 4;  // gamma (host-set)
-    // x += alpha p and p = s + beta p, slab by slab through the device, in
-    // two slab buffers that exist only for the pass (the backprojection's
-    // footprint): p and x in, x out; then s in where x was, p out.
+    // x += alpha p and p = s + beta p, slab by slab through the device: p and
+    // x in, x out; then s in where x was, p out.  Consecutive slabs alternate
+    // between two streams, each with its own pair of slab buffers (they exist
+    // only for the pass), so one slab's host copies overlap the other's
+    // copies and kernels; the two copy directions run on separate engines.
     auto update = [&](float alpha, float beta) -> tigre_status {
         Bufs U;
-        float *up, *uv;
-        TIGRE_TRY(U.alloc(&up, (size_t)(plane * slab)));
-        TIGRE_TRY(U.alloc(&uv, (size_t)(plane * slab)));
+        Streams side[2];
+        float *up[2], *uv[2];
+        for (int k = 0; k < 2; ++k) {
+            TIGRE_TRY(side[k].init());
+            TIGRE_TRY(U.alloc(&up[k], (size_t)(plane * slab)));
+            TIGRE_TRY(U.alloc(&uv[k], (size_t)(plane * slab)));
+        }
+        // both start after the work queued on st (which wrote s, p and x)
+        TIGRE_CUDA(cudaEventRecord(side[0].ev[0], st));
+        for (int k = 0; k < 2; ++k) TIGRE_CUDA(cudaStreamWaitEvent(side[k].copy, side[0].ev[0], 0));
         const dim3 grid(4 * 152), block(256);
-        for (int64_t z0 = 0; z0 < nz; z0 += slab) {
+        int64_t i = 0;
+        for (int64_t z0 = 0; z0 < nz; z0 += slab, ++i) {
             const int64_t n = plane * std::min(slab, nz - z0), off = plane * z0;
             const size_t bytes = sizeof(float) * (size_t)n;
-            TIGRE_CUDA(cudaMemcpyAsync(up, hp + off, bytes, cudaMemcpyHostToDevice, st));
-            TIGRE_CUDA(cudaMemcpyAsync(uv, x_host + off, bytes, cudaMemcpyHostToDevice, st));
-            cgls_slab_axpy_kernel<<<grid, block, 0, st>>>(uv, up, n, alpha);
+            cudaStream_t ss = side[i & 1].copy;
+            float* P = up[i & 1];
+            float* V = uv[i & 1];
+            TIGRE_CUDA(cudaMemcpyAsync(P, hp + off, bytes, cudaMemcpyHostToDevice, ss));
+            TIGRE_CUDA(cudaMemcpyAsync(V, x_host + off, bytes, cudaMemcpyHostToDevice, ss));
+            cgls_slab_axpy_kernel<<<grid, block, 0, ss>>>(V, P, n, alpha);
             TIGRE_LAUNCHED("cgls_slab_axpy_kernel");
-            TIGRE_CUDA(cudaMemcpyAsync(x_host + off, uv, bytes, cudaMemcpyDeviceToHost, st));
-            TIGRE_CUDA(cudaMemcpyAsync(uv, hs + off, bytes, cudaMemcpyHostToDevice, st));
-            cgls_slab_xpay_kernel<<<grid, block, 0, st>>>(up, uv, n, beta);
+            TIGRE_CUDA(cudaMemcpyAsync(x_host + off, V, bytes, cudaMemcpyDeviceToHost, ss));
+            TIGRE_CUDA(cudaMemcpyAsync(V, hs + off, bytes, cudaMemcpyHostToDevice, ss));
+            cgls_slab_xpay_kernel<<<grid, block, 0, ss>>>(P, V, n, beta);
             TIGRE_LAUNCHED("cgls_slab_xpay_kernel");
-            TIGRE_CUDA(cudaMemcpyAsync(hp + off, up, bytes, cudaMemcpyDeviceToHost, st));
+            TIGRE_CUDA(cudaMemcpyAsync(hp + off, P, bytes, cudaMemcpyDeviceToHost, ss));
         }
-        // the next projection reads p from host memory on its own stream
+        // st continues after both; the next projection reads p from host memory
+        for (int k = 0; k < 2; ++k) {
+            TIGRE_CUDA(cudaEventRecord(side[k].ev[1], side[k].copy));
+            TIGRE_CUDA(cudaStreamWaitEvent(st, side[k].ev[1], 0));
+        }
         TIGRE_CUDA(cudaStreamSynchronize(st));
         return TIGRE_OK;
     };

@@ -615,3 +615,267 @@ tigre_status tigre_cgls_end(tigre_cgls_t S)
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- batched CGLS
+// B reconstructions of one geometry and storage type, iterated together: each
+// iteration projects the B search directions in one forward launch and
+// backprojects the B residuals in one voxel-driven launch; the inner
+// products, norms, step lengths and vector updates are each member's own
+// (the kernels of the single-problem CGLS, FP64 scalars in per-member device
+// slots).  Every member's iterates are therefore those of tigre_cgls on its
+// problem alone, bit for bit.
+struct tigre_cgls_batch {
+    tigre_geometry* g = nullptr;
+    tigre_bp_weight bw = TIGRE_BP_MATCHED;
+    cudaStream_t st = nullptr;
+    int B = 0;
+    int64_t nvox = 0, m = 0, na = 0, pe = 0;
+    tigre_dtype dt = TIGRE_F32;
+    std::vector<const void*> b;  // caller's projections, one per member
+    std::vector<void*> x;        // caller's volumes, one per member
+    void *r = nullptr, *q = nullptr, *p = nullptr, *s = nullptr;  // B consecutive vectors each
+    void* pad[2] = {nullptr, nullptr};   // forward workspaces, B padded volumes per layout
+    void* quad[2] = {nullptr, nullptr};
+    void* bpws = nullptr;                // backprojection workspace
+    double* sc = nullptr;                // B scalar areas
+    double* hist = nullptr;              // B histories of hist_cap residuals
+    int* counter = nullptr;              // B device counters
+    int hist_cap = 0, done = 0, cur = 0;
+    bool graph = false;
+    cudaGraphExec_t exec[2] = {};
+};
+
+namespace tigre {
+namespace {
+
+using Batch = tigre_cgls_batch;
+
+size_t batch_scalar_count() { return Scalars::count(4); }
+Scalars batch_scalars(const Batch* S, int i) { return Scalars{S->sc + (size_t)i * batch_scalar_count()}; }
+const unsigned char* member(const void* base, int64_t count, size_t elem, int i)
+{
+    return (const unsigned char*)base + (size_t)i * (size_t)count * elem;
+}
+unsigned char* member(void* base, int64_t count, size_t elem, int i)
+{
+    return (unsigned char*)base + (size_t)i * (size_t)count * elem;
+}
+
+void batch_release(Batch* S)
+{
+    for (cudaGraphExec_t e : S->exec)
+        if (e) cudaGraphExecDestroy(e);
+    for (void* ptr : {S->r, S->q, S->p, S->s, S->pad[0], S->pad[1], S->quad[0], S->quad[1],
+                      S->bpws, (void*)S->sc, (void*)S->hist, (void*)S->counter})
+        if (ptr) dev_free(ptr, S->st);
+    delete S;
+    handle_destroyed();
+}
+
+// x_i += alpha_i p_i, r_i -= alpha_i q_i (with ||r_i||), recorded; the first
+// half of an iteration after the batched projection q = A p.
+tigre_status batch_step(Batch* S)
+{
+    const size_t e = dtype_size(S->dt);
+    const int c = S->cur;
+    TIGRE_TRY(forward_batch_impl(S->g, S->p, S->q, S->B, S->dt, S->pad, S->quad, S->st));
+    for (int i = 0; i < S->B; ++i) {
+        const Scalars sc = batch_scalars(S, i);
+        const void* pi = member(S->p, S->nvox, e, i);
+        const void* qi = member(S->q, S->m, e, i);
+        TIGRE_TRY(dot_f64_dt(S->dt, qi, qi, S->m, sc.partials(), sc.slot(2), S->st));
+        TIGRE_TRY(axpy_ratio_dt(S->dt, S->x[(size_t)i], pi, S->nvox, sc.slot(c), sc.slot(2), 1.0f,
+                                S->st));
+        TIGRE_TRY(axpy_ratio_norm_dt(S->dt, member(S->r, S->m, e, i), qi, S->m, sc.slot(c),
+                                     sc.slot(2), -1.0f, sc.partials(), sc.slot(3), S->st));
+        TIGRE_TRY(record_dscalar(S->hist + (size_t)i * S->hist_cap, S->hist_cap, S->counter + i,
+                                 sc.slot(3) + 1, S->st));
+    }
+    TIGRE_TRY(backward_batch_impl(S->g, S->r, S->s, S->B, S->dt, S->bw, S->bpws, S->st));
+    for (int i = 0; i < S->B; ++i) {
+        const Scalars sc = batch_scalars(S, i);
+        const void* si = member(S->s, S->nvox, e, i);
+        TIGRE_TRY(dot_f64_dt(S->dt, si, si, S->nvox, sc.partials(), sc.slot(1 - c), S->st));
+        TIGRE_TRY(xpay_ratio_dt(S->dt, member(S->p, S->nvox, e, i), si, S->nvox, sc.slot(1 - c),
+                                sc.slot(c), S->st));
+    }
+    S->cur = 1 - c;
+    S->done += 1;
+    return TIGRE_OK;
+}
+
+tigre_status batch_capture(Batch* S, cudaGraphExec_t* out)
+{
+    const int done0 = S->done, cur0 = S->cur;
+    TIGRE_CUDA(cudaStreamBeginCapture(S->st, cudaStreamCaptureModeThreadLocal));
+    tigre_status st = batch_step(S);
+    if (st == TIGRE_OK) st = batch_step(S);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(S->st, &graph);
+    S->done = done0;
+    S->cur = cur0;
+    if (st != TIGRE_OK || e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return st != TIGRE_OK ? st : cuda_fail(e, "cudaStreamEndCapture(cgls batch)");
+    }
+    const cudaError_t ei = cudaGraphInstantiate(out, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) return cuda_fail(ei, "cudaGraphInstantiate(cgls batch)");
+    return TIGRE_OK;
+}
+
+tigre_status batch_init(Batch* S, int hist_cap, bool x0_zero)
+{
+    const tigre_geometry_desc& d = S->g->desc;
+    const size_t e = dtype_size(S->dt);
+    const size_t B = (size_t)S->B;
+    TIGRE_TRY(dalloc((unsigned char**)&S->r, B * (size_t)S->m * e, S->st));
+    TIGRE_TRY(dalloc((unsigned char**)&S->q, B * (size_t)S->m * e, S->st));
+    TIGRE_TRY(dalloc((unsigned char**)&S->p, B * (size_t)S->nvox * e, S->st));
+    TIGRE_TRY(dalloc((unsigned char**)&S->s, B * (size_t)S->nvox * e, S->st));
+    bool need[2] = {false, false};
+    for (int l : S->g->layout) need[l] = true;
+    for (int l = 0; l < 2; ++l) {
+        if (!need[l]) continue;
+        TIGRE_TRY(dalloc((unsigned char**)&S->pad[l], B * (size_t)S->pe * e, S->st));
+        TIGRE_TRY(dalloc((unsigned char**)&S->quad[l], B * (size_t)S->pe * 4 * e, S->st));
+        // the zero borders; every projection rewrites the interiors only
+        TIGRE_CUDA(cudaMemsetAsync(S->pad[l], 0, B * (size_t)S->pe * e, S->st));
+    }
+    TIGRE_TRY(dalloc((unsigned char**)&S->bpws, B * backward_batch_workspace_bytes(S->g, S->dt),
+                     S->st));
+    TIGRE_TRY(dalloc(&S->sc, B * batch_scalar_count(), S->st));
+    S->hist_cap = std::max(hist_cap, 16);
+    TIGRE_TRY(dalloc(&S->hist, B * (size_t)S->hist_cap, S->st));
+    TIGRE_TRY(dalloc(&S->counter, B, S->st));
+    TIGRE_CUDA(cudaMemsetAsync(S->counter, 0, sizeof(int) * B, S->st));
+    (void)d;
+    // r = b - A x0 (r = b from a zero start), p = A^T r, gamma = ||p||^2
+    if (x0_zero) {
+        for (int i = 0; i < S->B; ++i)
+            TIGRE_CUDA(cudaMemsetAsync(S->x[(size_t)i], 0, e * (size_t)S->nvox, S->st));
+        TIGRE_CUDA(cudaMemsetAsync(S->q, 0, B * (size_t)S->m * e, S->st));
+    } else {
+        for (int i = 0; i < S->B; ++i)
+            TIGRE_CUDA(cudaMemcpyAsync(member(S->p, S->nvox, e, i), S->x[(size_t)i],
+                                       e * (size_t)S->nvox, cudaMemcpyDeviceToDevice, S->st));
+        TIGRE_TRY(forward_batch_impl(S->g, S->p, S->q, S->B, S->dt, S->pad, S->quad, S->st));
+    }
+    for (int i = 0; i < S->B; ++i) {
+        const Scalars sc = batch_scalars(S, i);
+        TIGRE_TRY(weighted_residual_dt(S->dt, S->b[(size_t)i], member(S->q, S->m, e, i), nullptr,
+                                       member(S->r, S->m, e, i), S->m, sc.partials(), sc.slot(3),
+                                       S->st));
+    }
+    TIGRE_TRY(backward_batch_impl(S->g, S->r, S->p, S->B, S->dt, S->bw, S->bpws, S->st));
+    for (int i = 0; i < S->B; ++i) {
+        const Scalars sc = batch_scalars(S, i);
+        const void* pi = member(S->p, S->nvox, e, i);
+        TIGRE_TRY(dot_f64_dt(S->dt, pi, pi, S->nvox, sc.partials(), sc.slot(0), S->st));
+    }
+    S->cur = 0;
+    return TIGRE_OK;
+}
+
+}  // namespace
+}  // namespace tigre
+
+extern "C" {
+
+tigre_status tigre_cgls_batch_begin(tigre_geometry_t geo, int batch, const void* const* projs,
+                                    void* const* vols, const tigre_solver_opts* opts,
+                                    tigre_cgls_batch_t* out)
+{
+    using namespace tigre;
+    if (!out) return fail(TIGRE_ERR_INVALID_ARG, "null output handle pointer");
+    *out = nullptr;
+    if (batch < 1 || !projs || !vols) return fail(TIGRE_ERR_INVALID_ARG, "need batch >= 1 and buffers");
+    for (int i = 0; i < batch; ++i)
+        if (!projs[i] || !vols[i]) return fail(TIGRE_ERR_INVALID_ARG, "null projection or volume");
+    TIGRE_TRY(check_geometry(geo));
+    TIGRE_TRY(check_opts(geo, opts, projs[0], vols[0]));
+    if (opts->flags & ~(TIGRE_GRAPH | TIGRE_X0_ZERO))
+        return fail(TIGRE_ERR_UNSUPPORTED, "batched CGLS: device buffers, in core");
+    if (opts->bp_weight == TIGRE_BP_EXACT_ADJOINT)
+        return fail(TIGRE_ERR_UNSUPPORTED, "batched CGLS: voxel-driven backprojection");
+    if (geo->projector != TIGRE_PROJ_INTERPOLATED || geo->fwd_path != 0)
+        return fail(TIGRE_ERR_UNSUPPORTED, "batched CGLS: interpolated projector, automatic path");
+    Batch* S = new (std::nothrow) Batch();
+    if (!S) return fail(TIGRE_ERR_OOM, "host allocation failed");
+    handle_created();
+    S->g = geo;
+    S->bw = opts->bp_weight;
+    S->graph = (opts->flags & TIGRE_GRAPH) && opts->cuda_stream != nullptr;
+    S->st = (cudaStream_t)opts->cuda_stream;
+    S->B = batch;
+    S->nvox = n_vox(geo);
+    S->na = (int64_t)geo->angles.size();
+    S->m = n_pix(geo) * S->na;
+    S->pe = (int64_t)padded_elems(geo->desc);
+    S->dt = opts->storage;
+    S->b.assign(projs, projs + batch);
+    S->x.assign(vols, vols + batch);
+    const tigre_status st = batch_init(S, opts->n_iter, (opts->flags & TIGRE_X0_ZERO) != 0);
+    if (st != TIGRE_OK) {
+        batch_release(S);
+        return st;
+    }
+    *out = S;
+    return TIGRE_OK;
+}
+
+tigre_status tigre_cgls_batch_iterate(tigre_cgls_batch_t S, int n_iter)
+{
+    using namespace tigre;
+    if (!S || n_iter < 0) return fail(TIGRE_ERR_INVALID_ARG, "null batch or n_iter < 0");
+    if (S->done + n_iter > S->hist_cap) {
+        // grow every member's history (stream-ordered, outside any capture)
+        int cap = S->hist_cap;
+        while (S->done + n_iter > cap) cap *= 2;
+        double* nh = nullptr;
+        TIGRE_TRY(dalloc(&nh, (size_t)S->B * (size_t)cap, S->st));
+        for (int i = 0; i < S->B; ++i)
+            TIGRE_CUDA(cudaMemcpyAsync(nh + (size_t)i * cap, S->hist + (size_t)i * S->hist_cap,
+                                       sizeof(double) * (size_t)S->hist_cap,
+                                       cudaMemcpyDeviceToDevice, S->st));
+        dev_free(S->hist, S->st);
+        S->hist = nh;
+        S->hist_cap = cap;
+        for (cudaGraphExec_t& e : S->exec)
+            if (e) {
+                cudaGraphExecDestroy(e);
+                e = nullptr;
+            }
+    }
+    int left = n_iter;
+    if (S->graph) {
+        while (left >= 2) {
+            cudaGraphExec_t& e = S->exec[S->cur];
+            if (!e) TIGRE_TRY(batch_capture(S, &e));
+            TIGRE_CUDA(cudaGraphLaunch(e, S->st));
+            S->done += 2;
+            left -= 2;
+        }
+    }
+    for (; left > 0; --left) TIGRE_TRY(batch_step(S));
+    return TIGRE_OK;
+}
+
+tigre_status tigre_cgls_batch_history(tigre_cgls_batch_t S, int member_index, double* resid_hist,
+                                      int n)
+{
+    using namespace tigre;
+    if (!S || member_index < 0 || member_index >= S->B || n < 0 || n > S->done ||
+        (n > 0 && !resid_hist))
+        return fail(TIGRE_ERR_INVALID_ARG, "history: need a member and 0 <= n <= iterations done");
+    return finish_history(S->hist + (size_t)member_index * S->hist_cap, resid_hist, n, S->st);
+}
+
+tigre_status tigre_cgls_batch_end(tigre_cgls_batch_t S)
+{
+    if (S) tigre::batch_release(S);
+    return TIGRE_OK;
+}
+
+}  // extern "C"

@@ -2,15 +2,18 @@
 
 Requests (geometry, angles, projections, iteration count) arrive over time.
 The scheduler keeps up to `max_slots` reconstructions resident on the GPU at
-once, each with its own stream, geometry handle and CGLS state (iterates stay
-in HBM from admission to completion).  A request is admitted, in arrival
-order, as soon as a slot is free and its HBM footprint fits the remaining
-budget; it does not wait for the requests already running to finish.  Every
-scheduler tick enqueues the next iterations of every resident request on its
-stream (as replays of a captured CUDA graph of two CGLS iterations), so
-different requests' projections and backprojections overlap on the device.
-Finished requests are detected with events, copied back, and their slot and
-memory returned to the pool.
+once (iterates stay in HBM from admission to completion).  A request is
+admitted, in arrival order, as soon as a slot is free and its HBM footprint
+fits the remaining budget; it does not wait for the requests already running
+to finish.  Requests queued behind it with the same geometry, angles,
+storage type and iteration count join it, up to `max_batch`: the group runs
+as one batched CGLS (tigre_cgls_batch_*), whose every iteration projects the
+whole group in one forward launch and backprojects it in one backprojection
+launch, captured with the group's vector updates in one CUDA graph of two
+iterations.  Each group has its own stream and geometry handle; every
+scheduler tick enqueues the next iterations of every resident group, so
+different groups' launches overlap on the device.  Finished groups are
+detected with events, copied back, and their slots and memory returned.
 
 `run_plain` is the one-at-a-time reference path: each request is solved
 alone with tigre_cgls, in arrival order.
@@ -52,16 +55,20 @@ class Result:
 
 
 def footprint_bytes(geo: dict, n_angles: int, elem: int = 4) -> int:
-    """HBM needed by one resident CGLS reconstruction stored in elem-byte
-    values: x, p, s (volume-sized), b, r, q (projection-sized), the forward
+    """HBM one member of a batched CGLS keeps resident, in elem-byte values:
+    x, p, s (volume-sized), b, r, q (projection-sized), the forward
     projector's two padded layouts and their quad copies (5 padded volumes
-    each), the backprojector's padded projections, plus 64 MiB of slack."""
+    each), the backprojector's quad copy of the zero-bordered projections
+    (4 values per pixel; two border columns a side, and the rows the volume's
+    shadow reaches beyond the detector, taken as 10 % + 8), plus 64 MiB of
+    slack."""
     nx, ny, nz = geo["n_voxel"]
     nu, nv = geo["n_det"]
     vol = elem * nx * ny * nz
     padded = elem * (nx + 4) * (ny + 4) * (nz + 4)
     proj = elem * nu * nv * n_angles
-    return 3 * vol + 4 * proj + 10 * padded + (64 << 20)
+    proj_quads = 4 * elem * n_angles * (nu + 4) * (nv + nv // 10 + 8)
+    return 3 * vol + 3 * proj + proj_quads + 10 * padded + (64 << 20)
 
 
 _STORAGE = (torch.float32, torch.bfloat16, torch.float16)
@@ -73,6 +80,15 @@ def storage_dtype(req: Request) -> torch.dtype:
 
 def request_bytes(req: Request) -> int:
     return footprint_bytes(req.geo, len(req.angles), storage_dtype(req).itemsize)
+
+
+def batch_key(req: Request) -> tuple:
+    """Requests with equal keys can share one batched CGLS: same geometry,
+    angles, storage type and iteration count."""
+    geo = tuple(sorted((k, tuple(v) if isinstance(v, (list, tuple)) else v)
+                       for k, v in req.geo.items()))
+    ang = np.ascontiguousarray(req.angles, dtype=np.float64).tobytes()
+    return geo, ang, storage_dtype(req), req.n_iter
 
 
 def work_estimate(req: Request) -> float:
@@ -88,42 +104,72 @@ def admit(queue: list[Request], n_active: int, used: int, max_slots: int, budget
     resident).  fifo keeps arrival order (a large request at the head waits
     and holds the ones behind it); sjf first sorts the queue by estimated
     work."""
+    return [g[0] for g in admit_groups(queue, n_active, used, max_slots, budget, policy, 1)]
+
+
+def admit_groups(queue: list[Request], n_active: int, used: int, max_slots: int, budget: int,
+                 policy: str = "fifo", max_batch: int = 1) -> list[list[Request]]:
+    """As `admit`, in groups: each admitted request (the head of the queue in
+    turn) takes along the requests queued behind it with its batch_key, up to
+    max_batch per group, while slots (one per request) and HBM remain."""
     if policy == "sjf":
         queue.sort(key=lambda r: (work_estimate(r), r.arrival, r.rid))
-    out: list[Request] = []
-    while queue and n_active + len(out) < max_slots:
+    out: list[list[Request]] = []
+    n = n_active
+    while queue and n < max_slots:
         need = request_bytes(queue[0])
-        if used + need > budget and n_active + len(out) > 0:
+        if used + need > budget and n > 0:
             break
-        out.append(queue.pop(0))
+        head = queue.pop(0)
+        group = [head]
         used += need
+        n += 1
+        key = batch_key(head)
+        i = 0
+        while len(group) < max_batch and i < len(queue) and n < max_slots:
+            r = queue[i]
+            if batch_key(r) == key and used + request_bytes(r) <= budget:
+                group.append(queue.pop(i))
+                used += request_bytes(r)
+                n += 1
+            else:
+                i += 1
+        out.append(group)
     return out
 
 
 @dataclass
 class _Slot:
-    req: Request
+    reqs: list
     G: tigre.Geometry
     stream: torch.cuda.Stream
-    b: torch.Tensor
-    x: torch.Tensor
+    b: list
+    x: list
     state: object
     issued: int
     admitted: float
     done_event: torch.cuda.Event = field(default_factory=lambda: torch.cuda.Event())
     bytes: int = 0
 
+    @property
+    def n_iter(self) -> int:
+        return self.reqs[0].n_iter
+
 
 class Server:
     def __init__(self, max_slots: int = 8, hbm_budget: int | None = None, graph: bool = True,
-                 iters_per_tick: int = 2, device: int = 0, policy: str = "fifo"):
+                 iters_per_tick: int = 2, device: int = 0, policy: str = "fifo",
+                 max_batch: int = 4):
         """policy: "fifo" admits in arrival order; "sjf" admits the queued
         request with the least estimated work (voxels x angles x iterations)
         first, which shortens the typical latency when big and small
-        reconstructions are mixed."""
+        reconstructions are mixed.  max_batch: the most requests of one
+        batch key run as one batched CGLS (1: every request alone)."""
         if policy not in ("fifo", "sjf"):
             raise ValueError("policy must be 'fifo' or 'sjf'")
         self.policy = policy
+        self.max_batch = max(1, int(max_batch))
+        self.groups: list[list[int]] = []  # request ids of every group admitted, in order
         self.max_slots = max_slots
         self.graph = graph
         self.iters_per_tick = max(1, iters_per_tick)
@@ -133,23 +179,29 @@ class Server:
             hbm_budget = int(0.8 * free)
         self.hbm_budget = hbm_budget
 
-    def _admit(self, req: Request, now: float) -> _Slot:
+    def _admit(self, group: list[Request], now: float) -> _Slot:
         stream = torch.cuda.Stream(device=self.device)
+        head = group[0]
+        self.groups.append([r.rid for r in group])
         with torch.cuda.stream(stream):
-            G = tigre.Geometry(req.geo, req.angles)
-            dt = storage_dtype(req)
-            b = req.proj.to(self.device, dtype=dt, non_blocking=True)
-            x = torch.empty(G.vol_shape, device=self.device, dtype=dt)  # zeroed by the library
-            state = tigre.tigre_cgls_begin(G.handle, b, x, n_iter_hint=req.n_iter,
-                                           stream=stream, graph=self.graph, x0_zero=True)
-        return _Slot(req, G, stream, b, x, state, 0, now, bytes=request_bytes(req))
+            G = tigre.Geometry(head.geo, head.angles)
+            dt = storage_dtype(head)
+            bs = [r.proj.to(self.device, dtype=dt, non_blocking=True) for r in group]
+            # zeroed by the library (zero start: r = b, no projection of x0)
+            xs = [torch.empty(G.vol_shape, device=self.device, dtype=dt) for _ in group]
+            state = tigre.tigre_cgls_batch_begin(G.handle, bs, xs, n_iter_hint=head.n_iter,
+                                                 stream=stream, graph=self.graph, x0_zero=True)
+        return _Slot(group, G, stream, bs, xs, state, 0, now,
+                     bytes=sum(request_bytes(r) for r in group))
 
-    def _finish(self, s: _Slot, now: float) -> Result:
-        resid = tigre.tigre_cgls_history(s.state, s.req.n_iter)  # syncs the slot's stream
-        x = s.x.float().cpu()
-        tigre.tigre_cgls_end(s.state)
+    def _finish(self, s: _Slot, now: float) -> list[Result]:
+        out = []
+        for i, r in enumerate(s.reqs):
+            resid = tigre.tigre_cgls_batch_history(s.state, i, r.n_iter)  # syncs the stream
+            out.append(Result(r.rid, s.x[i].float().cpu(), resid, r.arrival, s.admitted, now))
+        tigre.tigre_cgls_batch_end(s.state)
         s.G.close()
-        return Result(s.req.rid, x, resid, s.req.arrival, s.admitted, now)
+        return out
 
     def run(self, requests: list[Request], realtime: bool = True) -> list[Result]:
         """Serve requests (arrival offsets in seconds) and return results in
@@ -165,33 +217,34 @@ class Server:
             while pending and (pending[0].arrival <= now or not realtime):
                 queue.append(pending.pop(0))
             # Admission as slots and memory free up (arrival order, or least
-            # work first).
-            for req in admit(queue, len(active), used, self.max_slots, self.hbm_budget,
-                             self.policy):
-                slot = self._admit(req, time.perf_counter() - t0)
+            # work first), same-key requests grouped into one batch.
+            n_active = sum(len(s.reqs) for s in active)
+            for group in admit_groups(queue, n_active, used, self.max_slots, self.hbm_budget,
+                                      self.policy, self.max_batch):
+                slot = self._admit(group, time.perf_counter() - t0)
                 used += slot.bytes
                 active.append(slot)
-            # One tick of work for every resident reconstruction.
+            # One tick of work for every resident group.
             for s in active:
-                if s.issued < s.req.n_iter:
-                    n = min(self.iters_per_tick, s.req.n_iter - s.issued)
+                if s.issued < s.n_iter:
+                    n = min(self.iters_per_tick, s.n_iter - s.issued)
                     with torch.cuda.stream(s.stream):
-                        tigre.tigre_cgls_iterate(s.state, n)
+                        tigre.tigre_cgls_batch_iterate(s.state, n)
                     s.issued += n
-                    if s.issued == s.req.n_iter:
+                    if s.issued == s.n_iter:
                         s.done_event.record(s.stream)
-            # Retire finished reconstructions.
+            # Retire finished groups.
             still = []
             for s in active:
-                if s.issued == s.req.n_iter and s.done_event.query():
-                    results.append(self._finish(s, time.perf_counter() - t0))
+                if s.issued == s.n_iter and s.done_event.query():
+                    results.extend(self._finish(s, time.perf_counter() - t0))
                     used -= s.bytes
                 else:
                     still.append(s)
             active = still
             if not active and not queue and pending and realtime:
                 time.sleep(max(0.0, pending[0].arrival - (time.perf_counter() - t0)))
-            elif active and all(s.issued == s.req.n_iter for s in active):
+            elif active and all(s.issued == s.n_iter for s in active):
                 time.sleep(0.0005)
         return results
 

@@ -34,7 +34,9 @@ EXPORTED = ["tigre_geometry_create", "tigre_geometry_destroy", "tigre_forward", 
             "tigre_tv_step", "tigre_tv_step_noalloc", "tigre_solver_opts_default", "tigre_sirt",
             "tigre_sart",
             "tigre_cgls", "tigre_cgls_begin", "tigre_cgls_iterate", "tigre_cgls_history",
-            "tigre_cgls_end", "tigre_cgls_save", "tigre_cgls_resume", "tigre_forward_samples", "tigre_forward_ooc", "tigre_backward_ooc",
+            "tigre_cgls_end", "tigre_cgls_batch_begin", "tigre_cgls_batch_iterate",
+            "tigre_cgls_batch_history", "tigre_cgls_batch_end", "tigre_cgls_save",
+            "tigre_cgls_resume", "tigre_forward_samples", "tigre_forward_ooc", "tigre_backward_ooc",
             "tigre_cgls_ooc_plan", "tigre_geometry_set_forward_path", "tigre_forward_angle_groups",
             "tigre_cgls_ooc_plan_desc",
             "tigre_geometry_set_projector", "tigre_fdk", "tigre_rof_denoise",
@@ -82,6 +84,11 @@ _sigs = {
     "tigre_cgls_iterate": [_P, ctypes.c_int],
     "tigre_cgls_history": [_P, _P, ctypes.c_int],
     "tigre_cgls_end": [_P],
+    "tigre_cgls_batch_begin": [_P, ctypes.c_int, _P, _P, ctypes.POINTER(tigre_solver_opts),
+                               ctypes.POINTER(_P)],
+    "tigre_cgls_batch_iterate": [_P, ctypes.c_int],
+    "tigre_cgls_batch_history": [_P, ctypes.c_int, _P, ctypes.c_int],
+    "tigre_cgls_batch_end": [_P],
     "tigre_cgls_save": [_P, _P, ctypes.c_size_t, _P, ctypes.c_size_t,
                         ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)],
     "tigre_cgls_resume": [_P, _P, _P, _P, ctypes.c_size_t, _P, ctypes.c_size_t, ctypes.c_double,
@@ -360,6 +367,52 @@ def tigre_cgls_history(state, n: int) -> np.ndarray:
 
 def tigre_cgls_end(state) -> None:
     _check(_lib.tigre_cgls_end(state))
+
+
+def tigre_cgls_batch_begin(handle, projs, vols, n_iter_hint=16, bp_weight="matched", stream=None,
+                           graph=False, x0_zero=False):
+    """Batched CGLS: len(projs) problems on one geometry handle, iterated
+    together (one forward and one backprojection launch per iteration for
+    the whole batch).  projs[i] (b) and vols[i] (x0, updated in place) are
+    CUDA tensors of one storage dtype; every member's result is bitwise that
+    of tigre_cgls on its problem alone."""
+    if len(projs) != len(vols) or not projs:
+        raise ValueError("need as many volumes as projection sets, at least one")
+    o = _opts(n_iter_hint, stream, bp_weight=bp_weight)
+    if graph:
+        o.flags |= TIGRE_GRAPH
+    if x0_zero:
+        o.flags |= TIGRE_X0_ZERO
+    pps, vps, dts = [], [], set()
+    for pr, vo in zip(projs, vols):
+        pp, pt = _dev(pr, "proj")
+        vp, vt = _dev(vo, "vol")
+        pps.append(pp.value)
+        vps.append(vp.value)
+        dts.update((pt, vt))
+    if len(dts) != 1:
+        raise TypeError("all projections and volumes must share one storage dtype")
+    o.storage = dts.pop()
+    parr = (_P * len(pps))(*pps)
+    varr = (_P * len(vps))(*vps)
+    s = ctypes.c_void_p()
+    _check(_lib.tigre_cgls_batch_begin(handle, len(pps), ctypes.cast(parr, _P),
+                                       ctypes.cast(varr, _P), ctypes.byref(o), ctypes.byref(s)))
+    return s
+
+
+def tigre_cgls_batch_iterate(state, n_iter: int) -> None:
+    _check(_lib.tigre_cgls_batch_iterate(state, int(n_iter)))
+
+
+def tigre_cgls_batch_history(state, member: int, n: int) -> np.ndarray:
+    h = np.zeros(max(n, 1), dtype=np.float64)
+    _check(_lib.tigre_cgls_batch_history(state, int(member), h.ctypes.data_as(_P), int(n)))
+    return h[:n]
+
+
+def tigre_cgls_batch_end(state) -> None:
+    _check(_lib.tigre_cgls_batch_end(state))
 
 
 def tigre_cgls_save(state, r_host: torch.Tensor, p_host: torch.Tensor) -> tuple:

@@ -69,3 +69,32 @@ def test_each_request_same_alone_and_in_the_mix(tigre, budget_mb):
         np.testing.assert_array_equal(r.resid, alone[r.rid].resid)
     stats = serving.latency_stats(mixed)
     assert stats["p99_s"] >= stats["p50_s"] > 0
+
+
+def test_batched_groups_same_alone_and_in_the_mix(tigre):
+    """Requests that share geometry, angles, storage type and iteration count
+    are served as batched CGLS groups (one forward and one backprojection
+    launch per iteration for the group); each result is bitwise its problem
+    solved alone."""
+    from paper_1905_03748_gb300 import serving
+    keys = [(synth.cube_geometry(32, 48, fov_mm=64.0), synth.angles(30)),
+            (synth.cube_geometry(24, 40, fov_mm=64.0), synth.angles(18) + 0.1)]
+    reqs = []
+    for i in range(8):
+        geo, ang = keys[i % 2]
+        n = geo["n_voxel"][0]
+        vol = synth.voxelize(synth.random_ellipsoids(n, 64.0 / n, 5, seed=200 + i,
+                                                     r_vox=(60, 200)),
+                             geo["n_voxel"], geo["d_voxel"])
+        b = projections(tigre, geo, ang, vol)
+        if i == 5:  # a BF16 request: a key of its own
+            b = b.to(torch.bfloat16)
+        reqs.append(serving.Request(i, geo, ang, b.pin_memory(), n_iter=6, arrival=0.0))
+    alone = {r.rid: r for r in serving.run_plain(reqs, realtime=False)}
+    server = serving.Server(max_slots=8, graph=True, iters_per_tick=2, max_batch=3)
+    mixed = server.run(reqs, realtime=False)
+    assert sorted(r.rid for r in mixed) == list(range(8))
+    assert max(len(g) for g in server.groups) == 3 and [5] in server.groups
+    for r in mixed:
+        assert torch.equal(r.x, alone[r.rid].x), r.rid
+        np.testing.assert_array_equal(r.resid, alone[r.rid].resid)

@@ -22,9 +22,10 @@ def request(serving, rid, n, na=30, dtype=torch.float32, arrival=0.0, n_iter=15)
 
 def test_footprint_counts_six_vectors_layouts_and_slack(serving):
     geo, ang = synth.workload("small_64")
-    # x, p, s: 3 x 64^3; b, r, q + padded projections: 4 x 100 x 128^2;
-    # two padded layouts and their quad copies: 10 x 68^3; 64 MiB slack
-    want = 4 * (3 * 64 ** 3 + 4 * 100 * 128 ** 2 + 10 * 68 ** 3) + (64 << 20)
+    # x, p, s: 3 x 64^3; b, r, q: 3 x 100 x 128^2; the backprojector's quad
+    # projections: 4 x 100 x (128 + 4) x (128 + 12 + 8); two padded layouts
+    # and their quad copies: 10 x 68^3; 64 MiB slack
+    want = 4 * (3 * 64 ** 3 + 3 * 100 * 128 ** 2 + 4 * 100 * 132 * 148 + 10 * 68 ** 3) + (64 << 20)
     assert serving.footprint_bytes(geo, len(ang)) == want
     assert serving.footprint_bytes(geo, len(ang), 2) == want // 2 + (32 << 20)
 
@@ -92,3 +93,34 @@ def test_latency_summary(serving):
     assert st["p99_s"] > 9.0 and st["mean_s"] == pytest.approx(1.9)
     assert st["makespan_s"] == pytest.approx(19.0)
     assert st["throughput_req_s"] == pytest.approx(10 / 19.0)
+
+
+def test_batch_key_separates_what_cannot_share_a_batch(serving):
+    a = request(serving, 0, 16)
+    assert serving.batch_key(a) == serving.batch_key(request(serving, 1, 16, arrival=3.0))
+    assert serving.batch_key(a) != serving.batch_key(request(serving, 2, 24))
+    assert serving.batch_key(a) != serving.batch_key(request(serving, 3, 16, na=31))
+    assert serving.batch_key(a) != serving.batch_key(request(serving, 4, 16, dtype=torch.bfloat16))
+    assert serving.batch_key(a) != serving.batch_key(request(serving, 5, 16, n_iter=14))
+
+
+def test_groups_take_same_key_requests_from_behind_the_head(serving):
+    sizes = [16, 24, 16, 16, 24, 16, 16]
+    reqs = [request(serving, i, n) for i, n in enumerate(sizes)]
+    q = list(reqs)
+    got = serving.admit_groups(q, 0, 0, 8, 10 ** 12, "fifo", 3)
+    # head 0 takes 2 and 3 (max 3 per group); head 1 takes 4; head 5 takes 6
+    assert [[r.rid for r in g] for g in got] == [[0, 2, 3], [1, 4], [5, 6]] and q == []
+    # slots count requests: 4 slots stop inside the second group
+    q = list(reqs)
+    got = serving.admit_groups(q, 0, 0, 4, 10 ** 12, "fifo", 3)
+    assert [[r.rid for r in g] for g in got] == [[0, 2, 3], [1]]
+    assert [r.rid for r in q] == [4, 5, 6]
+    # one member per group is plain admission
+    q = list(reqs)
+    assert [[r.rid for r in g] for g in serving.admit_groups(q, 0, 0, 2, 10 ** 12)] == [[0], [1]]
+    # the budget stops followers too
+    q = list(reqs)
+    one = serving.request_bytes(reqs[0])
+    got = serving.admit_groups(q, 0, 0, 8, 2 * one, "fifo", 4)
+    assert [[r.rid for r in g] for g in got] == [[0, 2]]
