@@ -27,8 +27,10 @@
  * Forward projection: the trilinear interpolant of the volume (zero outside,
  * i.e. virtual zero voxels at index -1 and n) is integrated along the ray
  * source -> pixel centre by the midpoint rule: the ray is clipped to the
- * support [-1, n] per axis, K = ceil(len / (accuracy * min d)) samples of
- * step h = len / K at the midpoints; proj = h * sum f(sample), mm x density.
+ * support [-1, n] per axis, K = max(1, ceil(len / (accuracy * min d) - 1e-9))
+ * samples of step h = len / K at the midpoints (K as computed in FP64 for every
+ * ray: rays whose FP32 set-up would round K differently are found once, when
+ * the handle is created); proj = h * sum f(sample), mm x density.
  *
  * Backprojection (voxel-driven): for each voxel centre X and angle, s =
  * X.(cos t, sin t, 0); the line source->X meets the detector at
@@ -323,8 +325,8 @@ TIGRE_API tigre_status tigre_cgls_end(tigre_cgls_t state);
  *        TIGRE_X0_ZERO (x_i zeroed, r_i = b_i).  The handle must use the
  *        interpolated projector and the automatic forward path; bp_weight
  *        MATCHED or FDK.  Workspaces (owned by the batch, stream-ordered on
- *        opts->cuda_stream): per member 4 iterate vectors, 2 padded and 2 quad
- *        copies of the volume per layout, and a quad copy of the padded
+ *        opts->cuda_stream): per member 4 iterate vectors, a quad copy of the
+ *        zero-bordered volume per layout (4 values per voxel), and a quad copy of the padded
  *        projections.  Otherwise as tigre_cgls_begin; TIGRE_ERR_UNSUPPORTED for
  *        other flags, projectors or weights.
  * iterate: enqueues n_iter iterations of every member (no host sync).

@@ -90,23 +90,26 @@ template <typename TP> struct ProjTaps<TP, true> {
 // projections (the normaliser V^-1 = A_w^T 1, from the same weights and
 // interpolation) and finish with vol += lambda * num / den (den > 1e-12),
 // clamped at zero when nonneg.
-// Occupancy (512^3 x 360, one launch): plain buffer, 16 voxels per thread,
-// 5 blocks per SM (48 registers): matched 51.2 ms, FDK 46.5 ms.  Quad buffer:
-// matched 48.4 ms with 8 voxels per thread at 8 blocks per SM (62 ms with 16
-// at 5, 53.6 ms with 16 at 4); FDK 36.0 ms with 16 at 4 blocks (49 ms at 5,
-// 39.9 ms with 8 at 8).  The SART form, with twice the accumulators, keeps 3.
+// Shape (512^3 x 360, one launch).  Plain buffer, 16 voxels per thread at 5
+// blocks per SM (48 registers): matched 51.2 ms, FDK 46.5 ms.  Quad buffer,
+// matched: 12 voxels at 6 blocks 44.7 ms (8 at 8: 48.1 with spills; 10 at 7:
+// 45.8; 16 at 5: 61.9; 4 at 8: 53.8); FDK: 16 voxels at 4 blocks 36.0 ms (8 at
+// 8: 39.9; 16 at 5: 49.0).  SART form (twice the accumulators): plain 16 at 3
+// blocks 74.2 ms per SIRT pass over 360 angles and 88.1 per OS-SART sweep of
+// 20-angle subsets; quads with 8 voxels at 6 blocks 65.5 and 66.2 ms.
 template <int MODE, bool SART, bool QUADP>
 constexpr int bp_blocks_per_sm()
 {
-    return SART ? 3 : !QUADP ? 5 : MODE == TIGRE_BP_FDK ? 4 : 8;
+    return !QUADP ? (SART ? 3 : 5) : SART ? 6 : MODE == TIGRE_BP_FDK ? 4 : 6;
 }
-template <int MODE, bool QUADP>
+template <int MODE, bool SART, bool QUADP>
 constexpr int bp_voxels_per_thread()
 {
-    return QUADP && MODE != TIGRE_BP_FDK ? 8 : 16;
+    return !QUADP ? 16 : SART ? 8 : MODE == TIGRE_BP_FDK ? 16 : 12;
 }
-static_assert(bp_voxels_per_thread<TIGRE_BP_FDK, false>() <= kBpNZ &&
-                  bp_voxels_per_thread<TIGRE_BP_MATCHED, true>() <= kBpNZ,
+static_assert(bp_voxels_per_thread<TIGRE_BP_FDK, false, false>() <= kBpNZ &&
+                  bp_voxels_per_thread<TIGRE_BP_MATCHED, false, true>() <= kBpNZ &&
+                  bp_voxels_per_thread<TIGRE_BP_FDK, false, true>() <= kBpNZ,
               "the row-band bounds assume chunks of at most kBpNZ planes");
 
 // Members of a batched launch: blockIdx.z = member * chunks + z chunk; member
@@ -414,8 +417,8 @@ size_t bp_slab_pad_bytes(const tigre_geometry_desc& d, int64_t slab, int64_t na)
 }
 
 // Whether an in-core backprojection with weight w reads the quad buffer
-// (both voxel-driven weights do; slab launches and the SART update, whose
-// normaliser doubles the accumulators, read the plain buffer).
+// (both voxel-driven weights do, the SART update included; out-of-core slab
+// launches read the plain band).
 static bool bp_reads_quads(tigre_bp_weight w)
 {
     return w == TIGRE_BP_MATCHED || w == TIGRE_BP_FDK;
@@ -474,7 +477,7 @@ static tigre_status run_voxel_bp(tigre_geometry* g, const BpConst& c, const TP* 
     auto launch = [&](auto mode, auto sart_tag) -> tigre_status {
         constexpr int M = decltype(mode)::value;
         constexpr bool S = decltype(sart_tag)::value;
-        constexpr int NZ = bp_voxels_per_thread<M, QUADP>();
+        constexpr int NZ = bp_voxels_per_thread<M, S, QUADP>();
         const int chunks = (c.z_end - c.z_first + NZ - 1) / NZ;
         dim3 grid((unsigned)((c.nx + 31) / 32), (unsigned)((c.ny + 7) / 8),
                   (unsigned)((int64_t)chunks * batch));
@@ -522,7 +525,7 @@ tigre_status launch_voxel_bp(tigre_geometry* g, const TP* proj, TV* vol, int64_t
         bp_slab_band(c, d, z_first, z_end);
     }
     // In-core launches read quads where they pay, slab launches the plain band.
-    return z_end < 0 && !sart && bp_reads_quads(w) ? run_voxel_bp<TP, TV, true>(g, c, proj, vol, a0, na, w, accumulate, st, sart,
+    return z_end < 0 && bp_reads_quads(w) ? run_voxel_bp<TP, TV, true>(g, c, proj, vol, a0, na, w, accumulate, st, sart,
                                                   lambda, nonneg)
                      : run_voxel_bp<TP, TV, false>(g, c, proj, vol, a0, na, w, accumulate, st,
                                                    sart, lambda, nonneg);

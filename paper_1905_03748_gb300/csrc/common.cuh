@@ -258,15 +258,14 @@ tigre_status backward_workspace(tigre_geometry* g, tigre_dtype pt, tigre_bp_weig
 std::vector<uint64_t> workspace_signature(const tigre_geometry* g);
 // Several reconstructions of one geometry in one launch each (the batched
 // CGLS): `batch` volumes (contiguous, storage dt) projected over all angles
-// into `batch` consecutive projection sets, through the caller's padded and
-// quad workspaces (batch x padded_elems elements of dt, and of quads, per
-// layout; borders zeroed by the caller); and the voxel-driven backprojection
+// into `batch` consecutive projection sets, through the caller's quad
+// workspaces (batch x padded_elems quads of dt per layout the angles use);
+// and the voxel-driven backprojection
 // of `batch` projection sets into `batch` volumes through a workspace of
 // batch x backward_batch_workspace_bytes.  Each member's numbers are the
 // single-volume operators' bit for bit.
 tigre_status forward_batch_impl(tigre_geometry* g, const void* vols, void* projs, int batch,
-                                 tigre_dtype dt, void* const pad[2], void* const quad[2],
-                                 cudaStream_t st);
+                                 tigre_dtype dt, void* const quad[2], cudaStream_t st);
 size_t backward_batch_workspace_bytes(const tigre_geometry* g, tigre_dtype dt);
 tigre_status backward_batch_impl(tigre_geometry* g, const void* projs, void* vols, int batch,
                                  tigre_dtype dt, tigre_bp_weight w, void* ws, cudaStream_t st);

@@ -295,6 +295,69 @@ __global__ void __launch_bounds__(256) fwd_l1_kernel(const TV* __restrict__ vxy,
 // zero-padded layout P.  A trilinear sample is then two aligned loads (planes
 // s and s+1) instead of eight scalar ones (element types: quad.cuh).
 
+// Build the quad volume of one layout straight from the caller's volume (no
+// padded copy): with P(s, m, f) the zero-bordered layout (vol[s-2][m-2][f-2]
+// for layout 0, x fastest; vol[s-2][f-2][m-2] for layout 1, y fastest; zero
+// outside), element (s, m, f) = (P(s,m,f), P(s,m,f+1), P(s,m+1,f),
+// P(s,m+1,f+1)).  A block makes a 32 x 32 tile of one plane from a 33 x 33
+// tile of P staged in shared memory, read along x (coalesced) in either
+// layout; blockIdx = (f tile, m tile, s).
+template <typename T>
+__global__ void __launch_bounds__(256) quad_from_vol_kernel(const T* __restrict__ vol,
+                                                            typename QuadOf<T>::type* __restrict__ out,
+                                                            int nx, int ny, int nz, int layout)
+{
+    __shared__ T tile[33][33];
+    const int PF = (layout ? ny : nx) + 2 * kPad, PM = (layout ? nx : ny) + 2 * kPad;
+    const int f0 = blockIdx.x * 32, m0 = blockIdx.y * 32, s = blockIdx.z;
+    const int z = s - kPad;
+    const T zero = from_f32<T>(0.0f);
+    const bool zin = (unsigned)z < (unsigned)nz;
+    const T* plane = vol + (int64_t)(zin ? z : 0) * nx * ny;
+    // tile[i][j] = P(s, m0 + i, f0 + j), i, j in [0, 33)
+    for (int k = threadIdx.y * 32 + threadIdx.x; k < 33 * 33; k += 256) {
+        int i, j;
+        if (layout == 0) {  // consecutive threads: consecutive f = x
+            i = k / 33;
+            j = k - i * 33;
+        } else {            // consecutive threads: consecutive m = x
+            j = k / 33;
+            i = k - j * 33;
+        }
+        const int m = m0 + i - kPad, f = f0 + j - kPad;
+        const int x = layout ? m : f, y = layout ? f : m;
+        tile[i][j] = (zin && (unsigned)x < (unsigned)nx && (unsigned)y < (unsigned)ny)
+                         ? plane[(int64_t)y * nx + x]
+                         : zero;
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += blockDim.y) {
+        const int m = m0 + i, f = f0 + threadIdx.x;
+        if (m >= PM || f >= PF) continue;
+        // P beyond the padded layout (f + 1 == PF or m + 1 == PM) is zero too
+        const T a = tile[i][threadIdx.x], b = tile[i][threadIdx.x + 1];
+        const T c = tile[i + 1][threadIdx.x], d = tile[i + 1][threadIdx.x + 1];
+        typename QuadOf<T>::type* o = out + ((int64_t)s * PM + m) * PF + f;
+        if constexpr (sizeof(T) == 4)
+            *o = pack_quad(a, b, c, d);
+        else
+            *o = pack_quad16(a, b, c, d);
+    }
+}
+
+template <typename T>
+tigre_status build_quads(const tigre_geometry_desc& d, const T* vol, typename QuadOf<T>::type* out,
+                         int layout, cudaStream_t st)
+{
+    const int nx = (int)d.n_voxel[0], ny = (int)d.n_voxel[1], nz = (int)d.n_voxel[2];
+    const int PF = (layout ? ny : nx) + 2 * kPad, PM = (layout ? nx : ny) + 2 * kPad;
+    if (nz + 2 * kPad > 65535) return fail(TIGRE_ERR_UNSUPPORTED, "volume too deep for one launch");
+    dim3 grid((unsigned)((PF + 31) / 32), (unsigned)((PM + 31) / 32), (unsigned)(nz + 2 * kPad));
+    quad_from_vol_kernel<T><<<grid, dim3(32, 8), 0, st>>>(vol, out, nx, ny, nz, layout);
+    TIGRE_LAUNCHED("quad_from_vol_kernel");
+    return TIGRE_OK;
+}
+
 // Build the quad volume of a padded layout; one block per (s, m) row.
 template <typename T>
 __global__ void quad_kernel(const T* __restrict__ pad, typename QuadOf<T>::type* __restrict__ out,
@@ -685,9 +748,12 @@ tigre_status forward_workspace(tigre_geometry* g, tigre_dtype vt, int64_t a0, in
     DeviceBuffer* qbufs[2] = {&g->vol_qxy, &g->vol_qyx};
     for (int l = 0; l < 2; ++l) {
         if (!need[l]) continue;
-        TIGRE_TRY(ensure_padded(*bufs[l], d, dtype_size(vt), l, st));
-        // a quad holds four elements of the storage type
-        if (use_quad) TIGRE_TRY(qbufs[l]->ensure(padded_elems(d) * 4 * dtype_size(vt)));
+        // the quad paths build their quads from the volume itself; the
+        // scalar and Siddon paths read the zero-bordered layouts
+        if (use_quad)
+            TIGRE_TRY(qbufs[l]->ensure(padded_elems(d) * 4 * dtype_size(vt)));  // 4 elements
+        else
+            TIGRE_TRY(ensure_padded(*bufs[l], d, dtype_size(vt), l, st));
     }
     return TIGRE_OK;
 }
@@ -738,15 +804,10 @@ tigre_status forward_impl(tigre_geometry* g, const void* vol, tigre_dtype vt, vo
         static_assert(sizeof(Q) == 4 * sizeof(TV), "a quad is four elements");
         for (int l = 0; l < 2; ++l) {
             if (!need[l]) continue;
-            TIGRE_TRY(fill_padded<TV>(d, (const TV*)vol, (TV*)bufs[l]->ptr, l, st));
-            if (use_quad) {
-                const int PF = (int)(l ? d.n_voxel[1] : d.n_voxel[0]) + 2 * kPad;
-                const int PM = (int)(l ? d.n_voxel[0] : d.n_voxel[1]) + 2 * kPad;
-                const int64_t rows = (int64_t)PM * (d.n_voxel[2] + 2 * kPad);
-                quad_kernel<TV><<<(unsigned)rows, 128, 0, st>>>((const TV*)bufs[l]->ptr,
-                                                                (Q*)qbufs[l]->ptr, PF, PM, rows);
-                TIGRE_LAUNCHED("quad_kernel");
-            }
+            if (use_quad)
+                TIGRE_TRY(build_quads<TV>(d, (const TV*)vol, (Q*)qbufs[l]->ptr, l, st));
+            else
+                TIGRE_TRY(fill_padded<TV>(d, (const TV*)vol, (TV*)bufs[l]->ptr, l, st));
         }
         return dispatch_dtype(pt, [&](auto ptag) -> tigre_status {
             using TP = decltype(ptag);
@@ -803,8 +864,7 @@ tigre_status forward_impl(tigre_geometry* g, const void* vol, tigre_dtype vt, vo
 }
 
 tigre_status forward_batch_impl(tigre_geometry* g, const void* vols, void* projs, int batch,
-                                 tigre_dtype dt, void* const pad[2], void* const quad[2],
-                                 cudaStream_t st)
+                                 tigre_dtype dt, void* const quad[2], cudaStream_t st)
 {
     TIGRE_TRY(check_geometry(g));
     const tigre_geometry_desc& d = g->desc;
@@ -824,16 +884,10 @@ tigre_status forward_batch_impl(tigre_geometry* g, const void* vols, void* projs
         using T = decltype(tag);
         using Q = typename QuadOf<T>::type;
         for (int i = 0; i < batch; ++i)
-            for (int l = 0; l < 2; ++l) {
-                if (!need[l]) continue;
-                T* pl = (T*)pad[l] + i * pe;
-                TIGRE_TRY(fill_padded<T>(d, (const T*)vols + i * nvox, pl, l, st));
-                const int PF = (int)(l ? d.n_voxel[1] : d.n_voxel[0]) + 2 * kPad;
-                const int PM = (int)(l ? d.n_voxel[0] : d.n_voxel[1]) + 2 * kPad;
-                const int64_t rows = (int64_t)PM * (d.n_voxel[2] + 2 * kPad);
-                quad_kernel<T><<<(unsigned)rows, 128, 0, st>>>(pl, (Q*)quad[l] + i * pe, PF, PM, rows);
-                TIGRE_LAUNCHED("quad_kernel");
-            }
+            for (int l = 0; l < 2; ++l)
+                if (need[l])
+                    TIGRE_TRY(build_quads<T>(d, (const T*)vols + i * nvox, (Q*)quad[l] + i * pe, l,
+                                             st));
         FwdBatch bt;
         bt.tiles = tiles;
         bt.vol_stride = pe;

@@ -634,8 +634,7 @@ struct tigre_cgls_batch {
     std::vector<const void*> b;  // caller's projections, one per member
     std::vector<void*> x;        // caller's volumes, one per member
     void *r = nullptr, *q = nullptr, *p = nullptr, *s = nullptr;  // B consecutive vectors each
-    void* pad[2] = {nullptr, nullptr};   // forward workspaces, B padded volumes per layout
-    void* quad[2] = {nullptr, nullptr};
+    void* quad[2] = {nullptr, nullptr};  // forward workspaces, B quad volumes per layout
     void* bpws = nullptr;                // backprojection workspace
     double* sc = nullptr;                // B scalar areas
     double* hist = nullptr;              // B histories of hist_cap residuals
@@ -665,8 +664,8 @@ void batch_release(Batch* S)
 {
     for (cudaGraphExec_t e : S->exec)
         if (e) cudaGraphExecDestroy(e);
-    for (void* ptr : {S->r, S->q, S->p, S->s, S->pad[0], S->pad[1], S->quad[0], S->quad[1],
-                      S->bpws, (void*)S->sc, (void*)S->hist, (void*)S->counter})
+    for (void* ptr : {S->r, S->q, S->p, S->s, S->quad[0], S->quad[1], S->bpws, (void*)S->sc,
+                      (void*)S->hist, (void*)S->counter})
         if (ptr) dev_free(ptr, S->st);
     delete S;
     handle_destroyed();
@@ -678,7 +677,7 @@ tigre_status batch_step(Batch* S)
 {
     const size_t e = dtype_size(S->dt);
     const int c = S->cur;
-    TIGRE_TRY(forward_batch_impl(S->g, S->p, S->q, S->B, S->dt, S->pad, S->quad, S->st));
+    TIGRE_TRY(forward_batch_impl(S->g, S->p, S->q, S->B, S->dt, S->quad, S->st));
     for (int i = 0; i < S->B; ++i) {
         const Scalars sc = batch_scalars(S, i);
         const void* pi = member(S->p, S->nvox, e, i);
@@ -736,13 +735,8 @@ tigre_status batch_init(Batch* S, int hist_cap, bool x0_zero)
     TIGRE_TRY(dalloc((unsigned char**)&S->s, B * (size_t)S->nvox * e, S->st));
     bool need[2] = {false, false};
     for (int l : S->g->layout) need[l] = true;
-    for (int l = 0; l < 2; ++l) {
-        if (!need[l]) continue;
-        TIGRE_TRY(dalloc((unsigned char**)&S->pad[l], B * (size_t)S->pe * e, S->st));
-        TIGRE_TRY(dalloc((unsigned char**)&S->quad[l], B * (size_t)S->pe * 4 * e, S->st));
-        // the zero borders; every projection rewrites the interiors only
-        TIGRE_CUDA(cudaMemsetAsync(S->pad[l], 0, B * (size_t)S->pe * e, S->st));
-    }
+    for (int l = 0; l < 2; ++l)
+        if (need[l]) TIGRE_TRY(dalloc((unsigned char**)&S->quad[l], B * (size_t)S->pe * 4 * e, S->st));
     TIGRE_TRY(dalloc((unsigned char**)&S->bpws, B * backward_batch_workspace_bytes(S->g, S->dt),
                      S->st));
     TIGRE_TRY(dalloc(&S->sc, B * batch_scalar_count(), S->st));
@@ -760,7 +754,7 @@ tigre_status batch_init(Batch* S, int hist_cap, bool x0_zero)
         for (int i = 0; i < S->B; ++i)
             TIGRE_CUDA(cudaMemcpyAsync(member(S->p, S->nvox, e, i), S->x[(size_t)i],
                                        e * (size_t)S->nvox, cudaMemcpyDeviceToDevice, S->st));
-        TIGRE_TRY(forward_batch_impl(S->g, S->p, S->q, S->B, S->dt, S->pad, S->quad, S->st));
+        TIGRE_TRY(forward_batch_impl(S->g, S->p, S->q, S->B, S->dt, S->quad, S->st));
     }
     for (int i = 0; i < S->B; ++i) {
         const Scalars sc = batch_scalars(S, i);

@@ -57,8 +57,8 @@ class Result:
 def footprint_bytes(geo: dict, n_angles: int, elem: int = 4) -> int:
     """HBM one member of a batched CGLS keeps resident, in elem-byte values:
     x, p, s (volume-sized), b, r, q (projection-sized), the forward
-    projector's two padded layouts and their quad copies (5 padded volumes
-    each), the backprojector's quad copy of the zero-bordered projections
+    projector's quad copies of the two zero-bordered layouts (4 padded
+    volumes each), the backprojector's quad copy of the zero-bordered projections
     (4 values per pixel; two border columns a side, and the rows the volume's
     shadow reaches beyond the detector, taken as 10 % + 8), plus 64 MiB of
     slack."""
@@ -68,7 +68,7 @@ def footprint_bytes(geo: dict, n_angles: int, elem: int = 4) -> int:
     padded = elem * (nx + 4) * (ny + 4) * (nz + 4)
     proj = elem * nu * nv * n_angles
     proj_quads = 4 * elem * n_angles * (nu + 4) * (nv + nv // 10 + 8)
-    return 3 * vol + 3 * proj + proj_quads + 10 * padded + (64 << 20)
+    return 3 * vol + 3 * proj + proj_quads + 8 * padded + (64 << 20)
 
 
 _STORAGE = (torch.float32, torch.bfloat16, torch.float16)
