@@ -6,7 +6,9 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <map>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/tigre103.h"
@@ -116,6 +118,9 @@ struct AngleGroups {
     bool auto_pairs = false;    // the automatic path uses 2-angle warps
 };
 int angle_layout(double t);
+// Groups of `size` neighbouring angles of one layout and march direction
+// among angles[0 .. na), as indices into that array (-1 fills a short group).
+AngleGroups build_angle_groups(const tigre_geometry_desc& d, const double* angles, int64_t na);
 // Checks of a geometry description and its angles (host only).
 tigre_status validate_desc(const tigre_geometry_desc* d, const double* angles, int64_t na);
 
@@ -173,6 +178,10 @@ struct tigre_geometry {
     // kernel: int[n_groups * size], -1 filling a short group.
     tigre::DeviceBuffer angle_groups[2];
     int64_t n_groups[2] = {0, 0};
+    // The same tables for partial angle ranges (begin, count), indices relative
+    // to the range's first angle; built on first use (OS-SART's subsets).
+    std::map<std::pair<int64_t, int64_t>, tigre::DeviceBuffer> range_groups[2];
+    std::map<std::pair<int64_t, int64_t>, int64_t> range_n_groups[2];
     // Angles per warp of the automatic forward path (1 or 2): 2 when rays of
     // one pixel at grouped angles stay within a few voxels of each other.
     int auto_angle_group = 1;
@@ -208,12 +217,14 @@ tigre_status build_ray_exceptions(tigre_geometry* g);
 // over all angles; false when the source can be inside the support (no bound).
 bool detector_row_range(const tigre_geometry_desc& d, double za, double zb, double* lo, double* hi);
 size_t padded_elems(const tigre_geometry_desc& d);
-// Out-of-core building blocks: the zero-padded layout of a (sub-)volume
-// described by d, and the voxel-driven backprojection of planes
-// [z_first, z_end) into a slab buffer whose first plane is z_first.
-tigre_status fill_padded_f32(const tigre_geometry_desc& d, const float* vol, float* out, int layout,
+// Out-of-core building blocks: the quad volume of a layout of the
+// (sub-)volume described by d, built straight from it (its zero borders
+// included); the projection of one slab's quads; and the voxel-driven
+// backprojection of planes [z_first, z_end) into a slab buffer whose first
+// plane is z_first.
+tigre_status build_quads_f32(const tigre_geometry_desc& d, const float* vol, float4* out, int layout,
                              cudaStream_t st);
-tigre_status forward_slab_impl(tigre_geometry* g, const tigre_geometry_desc& sd, float* const pad[2],
+tigre_status forward_slab_impl(tigre_geometry* g, const tigre_geometry_desc& sd,
                                float4* const quad[2], float* proj, int64_t a0, int64_t na,
                                int cell_lo, int cell_hi, int plane0, cudaStream_t st);
 // Bytes of the zero-bordered F32 quad projection buffer that slab launches of

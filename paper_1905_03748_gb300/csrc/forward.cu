@@ -520,13 +520,14 @@ __device__ __forceinline__ void cut_axis(const Ray& R, int ax, int lo, int hi, i
 // holds 32 / AG pixels of one detector row at AG neighbouring angles (order
 // is then the angle-group table, blockIdx.y the group; full-range, in-core
 // launches only); each ray is marched exactly as with AG = 1.
-// Occupancy: 6 blocks per SM (40 registers) hides more gather latency than
-// the unconstrained 44-register build (5 blocks): 136 vs 144 ms per 512^3 x
-// 360 projection; 7 blocks spill.
+// Occupancy: with angle pairs, 6 blocks per SM (40 registers): 130.3 ms per
+// 512^3 x 360 projection against 136.7 at 5 blocks and 143.2 at 7 or 8.  One
+// angle per warp in core, 7 blocks: 309.8 ms per 1024^3 x 90 against 321.6
+// at 6 and 364.7 at 5.
 // With a Batch, several volumes of the same geometry are projected in one
 // launch (blockIdx.z runs over member 0's row tiles, then member 1's, ...).
 template <typename TV, typename TP, bool SLAB = false, bool PAIR = false, int AG = 1>
-__global__ void __launch_bounds__(256, 6) fwd_quad_kernel(
+__global__ void __launch_bounds__(256, (AG == 1 && !SLAB && !PAIR) ? 7 : 6) fwd_quad_kernel(
     const typename QuadOf<TV>::type* __restrict__ qxy,
     const typename QuadOf<TV>::type* __restrict__ qyx, TP* __restrict__ proj,
     const FwdAngle* __restrict__ params, FwdConst c, int a_first, const int* __restrict__ order,
@@ -712,10 +713,40 @@ tigre_status fill_padded(const tigre_geometry_desc& d, const TV* vol, TV* out, i
     return TIGRE_OK;
 }
 
-tigre_status fill_padded_f32(const tigre_geometry_desc& d, const float* vol, float* out, int layout,
+tigre_status build_quads_f32(const tigre_geometry_desc& d, const float* vol, float4* out, int layout,
                              cudaStream_t st)
 {
-    return fill_padded<float>(d, vol, out, layout, st);
+    return build_quads<float>(d, vol, out, layout, st);
+}
+
+
+// The angle-group table (groups of 2 or 4 angles: gi = 0 or 1) of the
+// partial range [a0, a0 + na), indices relative to a0; built on the host and
+// uploaded on first use, then kept by the handle.
+static tigre_status range_group_table(tigre_geometry* g, int gi, int64_t a0, int64_t na,
+                                      const int** table, int64_t* ngroups)
+{
+    const std::pair<int64_t, int64_t> key(a0, na);
+    auto it = g->range_groups[gi].find(key);
+    if (it == g->range_groups[gi].end()) {
+        const AngleGroups ag = build_angle_groups(g->desc, g->angles.data() + a0, na);
+        const std::vector<int>& tab = ag.table[gi];
+        DeviceBuffer buf;
+        TIGRE_TRY(buf.ensure(sizeof(int) * std::max<size_t>(tab.size(), 1)));
+        if (!tab.empty()) {
+            const cudaError_t e = cudaMemcpy(buf.ptr, tab.data(), sizeof(int) * tab.size(),
+                                             cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) {
+                buf.release();
+                return cuda_fail(e, "angle-group table upload");
+            }
+        }
+        it = g->range_groups[gi].emplace(key, buf).first;
+        g->range_n_groups[gi][key] = (int64_t)(tab.size() / (gi ? 4 : 2));
+    }
+    *table = (const int*)it->second.ptr;
+    *ngroups = g->range_n_groups[gi][key];
+    return TIGRE_OK;
 }
 
 // Layouts the angles [a0, a0 + na) read.
@@ -820,18 +851,28 @@ tigre_status forward_impl(tigre_geometry* g, const void* vol, tigre_dtype vt, vo
                            : g->fwd_path == 6 ? 4
                            : g->fwd_path == 0 ? g->auto_angle_group
                                               : 1;
-            if (use_quad && ag > 1 && order) {
+            if (use_quad && ag > 1 && (order || na <= 65535 * (int64_t)ag)) {
                 const int gi = ag == 4 ? 1 : 0;
-                dim3 grid((unsigned)((c.nu + 32 / ag - 1) / (32 / ag)), (unsigned)g->n_groups[gi],
-                          (unsigned)((c.nv + 7) / 8));
-                auto kern = ag == 4 ? fwd_quad_kernel<TV, TP, false, false, 4>
-                                    : fwd_quad_kernel<TV, TP, false, false, 2>;
-                kern<<<grid, dim3(32, 8), 0, st>>>(
-                    (const Q*)g->vol_qxy.ptr, (const Q*)g->vol_qyx.ptr, (TP*)proj,
-                    (const FwdAngle*)g->fwd_params.ptr, c, 0, (const int*)g->angle_groups[gi].ptr,
-                    SlabRange{0, 0, 0, 0, 0, 0, 0, 0, nullptr}, FwdBatch{});
-                TIGRE_LAUNCHED("fwd_quad_kernel");
-                return TIGRE_OK;
+                const int* table = nullptr;
+                int64_t ngroups = 0;
+                if (order) {  // the full range
+                    table = (const int*)g->angle_groups[gi].ptr;
+                    ngroups = g->n_groups[gi];
+                } else {
+                    TIGRE_TRY(range_group_table(g, gi, a0, na, &table, &ngroups));
+                }
+                if (ngroups <= 65535) {
+                    dim3 grid((unsigned)((c.nu + 32 / ag - 1) / (32 / ag)), (unsigned)ngroups,
+                              (unsigned)((c.nv + 7) / 8));
+                    auto kern = ag == 4 ? fwd_quad_kernel<TV, TP, false, false, 4>
+                                        : fwd_quad_kernel<TV, TP, false, false, 2>;
+                    kern<<<grid, dim3(32, 8), 0, st>>>(
+                        (const Q*)g->vol_qxy.ptr, (const Q*)g->vol_qyx.ptr, (TP*)proj,
+                        (const FwdAngle*)g->fwd_params.ptr, c, order ? 0 : (int)a0, table,
+                        SlabRange{0, 0, 0, 0, 0, 0, 0, 0, nullptr}, FwdBatch{});
+                    TIGRE_LAUNCHED("fwd_quad_kernel");
+                    return TIGRE_OK;
+                }
             }
             if (use_quad) {
                 for (int64_t s = 0; s < na; s += 65535) {
@@ -970,22 +1011,15 @@ static tigre_status brick_pixel_ranges(tigre_geometry* g, const int2** out)
 // zero-padded F32 layouts (planes of padded index plane0 .. for the
 // sub-volume description sd), quad[l] receive their quad volumes, and the
 // samples with z cells in [cell_lo, cell_hi) add into proj.
-tigre_status forward_slab_impl(tigre_geometry* g, const tigre_geometry_desc& sd, float* const pad[2],
+tigre_status forward_slab_impl(tigre_geometry* g, const tigre_geometry_desc& sd,
                                float4* const quad[2], float* proj, int64_t a0, int64_t na,
                                int cell_lo, int cell_hi, int plane0, cudaStream_t st)
 {
+    (void)sd;
     const tigre_geometry_desc& d = g->desc;
     if (g->projector != TIGRE_PROJ_INTERPOLATED)
         return fail(TIGRE_ERR_UNSUPPORTED, "out-of-core projection is interpolated only");
     const FwdConst c = make_fwd_const(g);
-    for (int l = 0; l < 2; ++l) {
-        if (!pad[l]) continue;
-        const int PF = (int)(l ? sd.n_voxel[1] : sd.n_voxel[0]) + 2 * kPad;
-        const int PM = (int)(l ? sd.n_voxel[0] : sd.n_voxel[1]) + 2 * kPad;
-        const int64_t rows = (int64_t)PM * (sd.n_voxel[2] + 2 * kPad);
-        quad_kernel<float><<<(unsigned)rows, 128, 0, st>>>(pad[l], quad[l], PF, PM, rows);
-        TIGRE_LAUNCHED("quad_kernel");
-    }
     // Rows whose rays can have samples in the slab's cells: z (unpadded
     // index) in [cell_lo - P, cell_hi - P), within the support [-1, nz].
     int q_lo = 0, q_hi = c.nv;

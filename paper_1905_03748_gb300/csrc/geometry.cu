@@ -392,6 +392,8 @@ tigre_status tigre_geometry_destroy(tigre_geometry_t g)
     g->angle_order.release();
     g->angle_groups[0].release();
     g->angle_groups[1].release();
+    for (int gi = 0; gi < 2; ++gi)
+        for (auto& kv : g->range_groups[gi]) kv.second.release();
     g->vol_xy.release();
     g->vol_yx.release();
     g->vol_qxy.release();

@@ -122,22 +122,20 @@ int64_t auto_slab_planes(const tigre_geometry_desc& d, int64_t per_plane_bytes)
     return std::min<int64_t>(std::min<int64_t>(s, d.n_voxel[2]), max_slab_planes(d));
 }
 
-// The forward projection of a volume cut into z-slabs of `slab` planes:
-// zero-padded and quad buffers for slab + 1 planes (the halo plane) in the
-// layouts the angles use.
+// The forward projection of a volume cut into z-slabs of `slab` planes: quad
+// buffers for slab + 1 planes (the halo plane) and their zero borders, in
+// the layouts the angles use, built straight from each raw slab.
 struct FwdSlabs {
     tigre_geometry* g = nullptr;
     tigre_geometry_desc sd{};
     int64_t slab = 0, nslab = 0;
-    float* pad[2] = {nullptr, nullptr};
     float4* quad[2] = {nullptr, nullptr};
 
     static size_t bytes(const tigre_geometry_desc& d, int64_t slab, const bool need[2])
     {
         tigre_geometry_desc t = d;
         t.n_voxel[2] = slab + 1;
-        return (size_t)((need[0] ? 1 : 0) + (need[1] ? 1 : 0)) * padded_elems(t) *
-               (sizeof(float) + sizeof(float4));
+        return (size_t)((need[0] ? 1 : 0) + (need[1] ? 1 : 0)) * padded_elems(t) * sizeof(float4);
     }
 
     tigre_status init(tigre_geometry* g_, int64_t slab_, const bool need[2], Bufs& B,
@@ -151,43 +149,36 @@ struct FwdSlabs {
         sd.n_voxel[2] = slab + 1;
         if (padded_elems(sd) >= (size_t)INT32_MAX)
             return fail(TIGRE_ERR_UNSUPPORTED, "slab too large for 32-bit indexing; use thinner slabs");
+        (void)st;
         for (int l = 0; l < 2; ++l)
-            if (need[l]) {
-                TIGRE_TRY(B.alloc(&pad[l], padded_elems(sd)));
-                TIGRE_TRY(B.alloc(&quad[l], padded_elems(sd)));
-                TIGRE_CUDA(cudaMemsetAsync(pad[l], 0, sizeof(float) * padded_elems(sd), st));
-            }
+            if (need[l]) TIGRE_TRY(B.alloc(&quad[l], padded_elems(sd)));
         return TIGRE_OK;
     }
 
     // Adds the partial projections of slab s into proj.  src (device) holds
     // the slab's planes z0 .. z0 + planes - 1, the halo plane included; after
-    // the zero-padded copies are made, `filled` (if any) is recorded on st.
+    // the quads are built from it, `filled` (if any) is recorded on st.  The
+    // quads of the slab's planes and their borders (planes + 4 quad planes)
+    // are all its samples read: a slab's own cells and the plane above them,
+    // and at the volume's ends the samples the rays' in-bounds proof allows
+    // (down to padded plane 0, up to padded plane nz + 3).
     tigre_status project(int64_t s, const float* src, float* proj, int64_t a0, int64_t na,
                          cudaStream_t st, cudaEvent_t filled = nullptr)
     {
         const tigre_geometry_desc& d = g->desc;
-        const int64_t nx = d.n_voxel[0], ny = d.n_voxel[1], nz = d.n_voxel[2];
+        const int64_t nz = d.n_voxel[2];
         const int64_t z0 = s * slab, z1 = std::min(nz, z0 + slab);
         const int64_t planes = std::min(z1 + 1, nz) - z0;  // with the halo plane
         tigre_geometry_desc pd = d;
         pd.n_voxel[2] = planes;
         for (int l = 0; l < 2; ++l)
-            if (pad[l]) TIGRE_TRY(fill_padded_f32(pd, src, pad[l], l, st));
-        if (planes < slab + 1)  // a shorter last slab: clear the stale planes above it
-            for (int l = 0; l < 2; ++l)
-                if (pad[l]) {
-                    const int64_t pp = (l ? ny : nx) + 2 * kPad, pm = (l ? nx : ny) + 2 * kPad;
-                    const int64_t from = (planes + kPad) * pp * pm;
-                    TIGRE_CUDA(cudaMemsetAsync(pad[l] + from, 0,
-                                               sizeof(float) * (size_t)(padded_elems(sd) - from), st));
-                }
+            if (quad[l]) TIGRE_TRY(build_quads_f32(pd, src, quad[l], l, st));
         if (filled) TIGRE_CUDA(cudaEventRecord(filled, st));
         // Cells of this slab in padded z: [z0+P, z1+P); the first slab also owns
         // the cells below plane 0, the last the cells above plane nz-1.
         const int cell_lo = s == 0 ? -1000000 : (int)(z0 + kPad);
         const int cell_hi = s == nslab - 1 ? 1000000 : (int)(z1 + kPad);
-        return forward_slab_impl(g, sd, pad, quad, proj, a0, na, cell_lo, cell_hi, (int)z0, st);
+        return forward_slab_impl(g, sd, quad, proj, a0, na, cell_lo, cell_hi, (int)z0, st);
     }
 };
 
@@ -208,7 +199,7 @@ tigre_status forward_ooc_impl(tigre_geometry* g, const float* vol_host, float* p
     const tigre_geometry_desc& d = g->desc;
     const int64_t nx = d.n_voxel[0], ny = d.n_voxel[1], nz = d.n_voxel[2];
     const int64_t plane = nx * ny;
-    if (slab <= 0) slab = auto_slab_planes(d, 4 * 2 * plane + 20 * 2 * (nx + 4) * (ny + 4));
+    if (slab <= 0) slab = auto_slab_planes(d, 4 * 2 * plane + 16 * 2 * (nx + 4) * (ny + 4));
     slab = std::min(slab, nz);
     bool need[2];
     layouts_used(g, a0, na, need);
@@ -389,6 +380,80 @@ __global__ void __launch_bounds__(256) cgls_slab_xpay_kernel(float* __restrict__
         p[i] = fmaf(beta, p[i], s[i]);
 }
 
+// Placement 1's direction update folded into the next projection's slab
+// stream: per slab, p and s (each with the halo plane) and x come in; x +=
+// alpha p on the slab's own planes and p = s + beta p on all of them run on
+// the device (the fused multiply-adds of the separate update pass, so the
+// same bits); x and the new p go back to host memory on a stream of their
+// own while the new p is projected into q.  A slab's halo plane is read from
+// host memory before the next slab writes its own update of that plane back:
+// the copies in run in slab order on one stream, and a slab's copies out wait
+// for its update, which waits for its copies in.
+tigre_status forward_ooc_update(tigre_geometry* g, float* p_host, const float* s_host,
+                                float* x_host, float alpha, float beta, float* proj, int64_t slab,
+                                cudaStream_t st)
+{
+    const tigre_geometry_desc& d = g->desc;
+    const int64_t nz = d.n_voxel[2], plane = d.n_voxel[0] * d.n_voxel[1];
+    const int64_t na = (int64_t)g->angles.size();
+    slab = std::max<int64_t>(1, std::min(slab, nz));
+    bool need[2];
+    layouts_used(g, 0, na, need);
+    Streams in, out;
+    TIGRE_TRY(in.init());
+    TIGRE_TRY(out.init());
+    Bufs B;
+    float *rp[2], *rs[2], *rx[2];
+    for (int i = 0; i < 2; ++i) {
+        TIGRE_TRY(B.alloc(&rp[i], (size_t)(plane * (slab + 1))));
+        TIGRE_TRY(B.alloc(&rs[i], (size_t)(plane * (slab + 1))));
+        TIGRE_TRY(B.alloc(&rx[i], (size_t)(plane * slab)));
+    }
+    FwdSlabs F;
+    TIGRE_TRY(F.init(g, slab, need, B, st));
+    TIGRE_CUDA(cudaMemsetAsync(proj, 0, sizeof(float) * (size_t)(na * n_pix(g)), st));
+    cudaEvent_t* copied = in.ev;       // [2] copies in done
+    cudaEvent_t* updated = in.ev + 2;  // [2] x and p updated
+    cudaEvent_t* filled = in.ev + 4;   // [2] p copied into the padded layouts
+    cudaEvent_t* written = in.ev + 6;  // [2] x and p back in host memory
+    for (int b = 0; b < 2; ++b) {
+        TIGRE_CUDA(cudaEventRecord(filled[b], st));
+        TIGRE_CUDA(cudaEventRecord(written[b], st));
+    }
+    const dim3 grid(4 * 152), block(256);
+    for (int64_t s = 0; s < F.nslab; ++s) {
+        const int b = (int)(s & 1);
+        const int64_t z0 = s * slab, z1 = std::min(nz, z0 + slab);
+        const int64_t planes = std::min(z1 + 1, nz) - z0;  // with the halo plane
+        const int64_t own = (z1 - z0) * plane, all = planes * plane, off = z0 * plane;
+        TIGRE_CUDA(cudaStreamWaitEvent(in.copy, filled[b], 0));
+        TIGRE_CUDA(cudaStreamWaitEvent(in.copy, written[b], 0));
+        TIGRE_CUDA(cudaMemcpyAsync(rp[b], p_host + off, sizeof(float) * (size_t)all,
+                                   cudaMemcpyHostToDevice, in.copy));
+        TIGRE_CUDA(cudaMemcpyAsync(rs[b], s_host + off, sizeof(float) * (size_t)all,
+                                   cudaMemcpyHostToDevice, in.copy));
+        TIGRE_CUDA(cudaMemcpyAsync(rx[b], x_host + off, sizeof(float) * (size_t)own,
+                                   cudaMemcpyHostToDevice, in.copy));
+        TIGRE_CUDA(cudaEventRecord(copied[b], in.copy));
+        TIGRE_CUDA(cudaStreamWaitEvent(st, copied[b], 0));
+        cgls_slab_axpy_kernel<<<grid, block, 0, st>>>(rx[b], rp[b], own, alpha);
+        TIGRE_LAUNCHED("cgls_slab_axpy_kernel");
+        cgls_slab_xpay_kernel<<<grid, block, 0, st>>>(rp[b], rs[b], all, beta);
+        TIGRE_LAUNCHED("cgls_slab_xpay_kernel");
+        TIGRE_CUDA(cudaEventRecord(updated[b], st));
+        TIGRE_CUDA(cudaStreamWaitEvent(out.copy, updated[b], 0));
+        TIGRE_CUDA(cudaMemcpyAsync(x_host + off, rx[b], sizeof(float) * (size_t)own,
+                                   cudaMemcpyDeviceToHost, out.copy));
+        TIGRE_CUDA(cudaMemcpyAsync(p_host + off, rp[b], sizeof(float) * (size_t)own,
+                                   cudaMemcpyDeviceToHost, out.copy));
+        TIGRE_CUDA(cudaEventRecord(written[b], out.copy));
+        TIGRE_TRY(F.project(s, rp[b], proj, 0, na, st, filled[b]));
+    }
+    for (int b = 0; b < 2; ++b) TIGRE_CUDA(cudaStreamWaitEvent(st, written[b], 0));
+    TIGRE_CUDA(cudaStreamSynchronize(st));
+    return TIGRE_OK;
+}
+
 // Sum of the per-slab values in slab order (host FP64 combine of nslab scalars).
 tigre_status sum_slab_dots(const double* d_dots, int64_t nslab, double* out)
 {
@@ -453,19 +518,20 @@ size_t placement2_workspace(const tigre_geometry* g, int64_t slab, const bool ne
            sizeof(double) * (size_t)(nslab + kRedBlocks + kScalarSlots);
 }
 
-// Placement 1: the larger of the out-of-core projection's and
-// backprojection's slab buffers (they run one after the other).
+// Placement 1: the larger of the projection's slab buffers (the update folded
+// into it: p and s with the halo plane, x, two of each) and the
+// backprojection's or the last update pass's (they run one after the other),
+// plus the backprojector's projection band, which the handle keeps.
 size_t placement1_workspace(const tigre_geometry* g, int64_t slab, const bool need[2])
 {
     const tigre_geometry_desc& d = g->desc;
     const int64_t plane = d.n_voxel[0] * d.n_voxel[1];
     const int64_t nslab = (d.n_voxel[2] + slab - 1) / slab;
-    const size_t fwd = sizeof(float) * (size_t)(2 * plane * (slab + 1)) + FwdSlabs::bytes(d, slab, need);
-    // the backprojection's projection band (kept by the handle afterwards)
-    // with its two slab buffers, or with the direction update's two pairs
-    const size_t bwd = sizeof(float) * (size_t)(4 * plane * slab) +
-                       bp_slab_pad_bytes(d, slab, (int64_t)g->angles.size());
-    return std::max(fwd, bwd) + sizeof(double) * (size_t)(nslab + 2 * kRedBlocks + kScalarSlots);
+    const size_t fwd = sizeof(float) * (size_t)(4 * plane * (slab + 1) + 2 * plane * slab) +
+                       FwdSlabs::bytes(d, slab, need);
+    const size_t bwd = sizeof(float) * (size_t)(4 * plane * slab);
+    return std::max(fwd, bwd) + bp_slab_pad_bytes(d, slab, (int64_t)g->angles.size()) +
+           sizeof(double) * (size_t)(nslab + 2 * kRedBlocks + kScalarSlots);
 }
 
 // Slab thicknesses the backprojector fills without waste: it computes z in
@@ -519,6 +585,7 @@ static tigre_status cgls_host_vectors(tigre_geometry* g, const float* b_host, fl
     const int64_t nz = d.n_voxel[2], plane = d.n_voxel[0] * d.n_voxel[1];
     slab = std::max<int64_t>(1, std::min(slab, nz));
     const int64_t nslab = (nz + slab - 1) / slab;
+    Progress prog;
     HostPin pin_x;
     TIGRE_TRY(pin_x.pin(x_host, sizeof(float) * (size_t)nvox));
     float *hp = nullptr, *hs = nullptr;
@@ -584,6 +651,8 @@ static tigre_status cgls_host_vectors(tigre_geometry* g, const float* b_host, fl
         TIGRE_CUDA(cudaStreamSynchronize(st));
         return TIGRE_OK;
     };
+    prog.flag("volume buffer page-locked", pin_x.pinned);
+    prog.note("setup (host p and s page-locked)", -1);
     TIGRE_CUDA(cudaMemcpyAsync(b, b_host, sizeof(float) * (size_t)m, cudaMemcpyHostToDevice, st));
     // r = b - A x0; p = A^T r; gamma = ||p||^2
     TIGRE_TRY(forward_ooc_impl(g, x_host, q, 0, na, slab, st));
@@ -591,8 +660,16 @@ static tigre_status cgls_host_vectors(tigre_geometry* g, const float* b_host, fl
     TIGRE_TRY(backward_ooc_impl(g, r, 0, hp, 0, na, o->bp_weight, slab, 0, st, sdots));
     double gamma = 0.0;
     TIGRE_TRY(sum_slab_dots(sdots, nslab, &gamma));
+    prog.note("first direction (A x0, A^T r)", -1);
+    // The direction update of iteration it - 1 runs inside iteration it's
+    // projection of the new p; the last one is a pass of its own.
+    bool pending = false;
+    float pend_alpha = 0.0f, pend_beta = 0.0f;
     for (int it = 0; it < o->n_iter; ++it) {
-        TIGRE_TRY(forward_ooc_impl(g, hp, q, 0, na, slab, st));
+        if (pending)
+            TIGRE_TRY(forward_ooc_update(g, hp, hs, x_host, pend_alpha, pend_beta, q, slab, st));
+        else
+            TIGRE_TRY(forward_ooc_impl(g, hp, q, 0, na, slab, st));
         TIGRE_TRY(dot_f64(q, q, m, partials, qq, st));
         double hqq = 0.0;
         TIGRE_CUDA(cudaMemcpyAsync(&hqq, qq, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -608,12 +685,19 @@ static tigre_status cgls_host_vectors(tigre_geometry* g, const float* b_host, fl
             h_hist[it] = rn[1];
         }
         // s = A^T r with ||s||^2 per slab; then x += alpha p, p = s + beta p
+        prog.note(it ? "previous update and projection (x, p; A p)" : "projection (A p)", it);
         TIGRE_TRY(backward_ooc_impl(g, r, 0, hs, 0, na, o->bp_weight, slab, 0, st, sdots));
         double gamma_new = 0.0;
         TIGRE_TRY(sum_slab_dots(sdots, nslab, &gamma_new));
-        const float beta = (float)(gamma != 0.0 ? gamma_new / gamma : 0.0);
-        TIGRE_TRY(update((float)alpha, beta));
+        prog.note("backprojection (A^T r)", it);
+        pending = true;
+        pend_alpha = (float)alpha;
+        pend_beta = (float)(gamma != 0.0 ? gamma_new / gamma : 0.0);
         gamma = gamma_new;
+    }
+    if (pending) {
+        TIGRE_TRY(update(pend_alpha, pend_beta));
+        prog.note("last update pass (x += alpha p)", o->n_iter - 1);
     }
     TIGRE_CUDA(cudaStreamSynchronize(st));
     return TIGRE_OK;

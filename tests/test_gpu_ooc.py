@@ -25,6 +25,17 @@ def case():
     return geo, ang, vol
 
 
+def case_volume_heavy():
+    """A volume much larger than its projections (7 angles of a small
+    detector): the regime where placement 1 (volume vectors in host memory,
+    projections on the device) needs less device memory than placement 2."""
+    geo = synth.geometry((61, 53, 47), (1.0, 0.9, 1.1), (23, 15), (1.6, 1.5), dso=300.0,
+                         dsd=450.0, off_origin=(0.5, -0.3, 0.2), off_det=(1.3, -0.7))
+    ang = np.sort(np.random.default_rng(4).uniform(0, 2 * np.pi, 7))
+    vol = synth.random_volume((47, 53, 61), seed=6)
+    return geo, ang, vol
+
+
 @pytest.mark.parametrize("slab", [1, 3, 7, 23])
 @pytest.mark.parametrize("pinned", [True, False])
 def test_forward_ooc_equals_in_core(tigre, slab, pinned):
@@ -121,12 +132,12 @@ def budgets_by_plan(tigre, G):
 
 
 def test_ooc_plan_orders_placements(tigre):
-    geo, ang, _ = case()
+    geo, ang, _ = case_volume_heavy()
     with tigre.Geometry(geo, ang) as G:
         plans = budgets_by_plan(tigre, G)
         with pytest.raises(tigre.TigreError):
             tigre.tigre_cgls_ooc_plan(G.handle, 1024)
-        assert tigre.tigre_cgls_ooc_plan(G.handle, 0) == (2, 23)
+        assert tigre.tigre_cgls_ooc_plan(G.handle, 0) == (2, 47)
     ones = sorted(b for (pl, _), b in plans.items() if pl == 1)
     twos = sorted(b for (pl, _), b in plans.items() if pl == 2)
     assert ones and twos and max(ones) < min(twos)
@@ -150,10 +161,10 @@ def test_cgls_out_of_core_equals_in_core(tigre, placement, max_slab, x0):
     slabs forced thin so that many slabs, the three-buffer ring and a short
     last slab are exercised; same iterates and residuals as the in-core CGLS
     up to FP32 summation order."""
-    geo, ang, vol = case()
+    geo, ang, vol = case_volume_heavy() if placement == 1 else case()
     b = oracle.forward(geo, ang, vol).astype(np.float32)
-    start = (0.3 * synth.random_volume((23, 29, 37), seed=9)).astype(np.float32) if x0 else \
-        np.zeros((23, 29, 37), np.float32)
+    start = (0.3 * synth.random_volume(vol.shape, seed=9)).astype(np.float32) if x0 else \
+        np.zeros(vol.shape, np.float32)
     with tigre.Geometry(geo, ang) as G:
         budget = 0
         if placement:

@@ -364,3 +364,21 @@ def test_solver_timeout_returns_and_the_work_completes(tigre):
         assert torch.equal(x, x_ref)
         h = tigre.tigre_cgls(G.handle, b, torch.zeros_like(x), 3, timeout_ms=600000)
         assert len(h) == 3
+
+
+@pytest.mark.parametrize("path_name", ["FWD_AUTO", "FWD_QUAD_ANGLES2", "FWD_QUAD_ANGLES4"])
+def test_subset_projections_equal_the_full_range_slices(tigre, path_name):
+    """OS-SART projects contiguous subsets of angles.  A partial range takes
+    its own angle-group table (pairs or quadruples of the subset's angles):
+    every subset of 20 (the last one ragged) equals the matching slice of the
+    full-range projection bit for bit."""
+    geo, ang = synth.workload("small_64")
+    vol = synth.phantom("head10", 64, 1.0)
+    with tigre.Geometry(geo, ang) as G:
+        tigre.tigre_geometry_set_forward_path(G.handle, getattr(tigre, path_name))
+        v = torch.from_numpy(vol).cuda()
+        full = G.forward(v)
+        for a0 in range(0, len(ang), 20):
+            cnt = min(20, len(ang) - a0) if a0 < 80 else len(ang) - a0 - 7
+            sub = G.forward(v, angle_begin=a0, angle_count=cnt)
+            assert torch.equal(sub, full[a0:a0 + cnt]), a0

@@ -33,7 +33,9 @@ def test_plans_shrink_with_the_budget(tigre, name):
         try:
             pl, slab = tigre.tigre_cgls_ooc_plan_desc(geo, ang, int(budget))
         except tigre.TigreError:
-            assert budget < 4 * 3 * m * 1.05  # only below about three projection sets
+            # only below three projection sets plus the thinnest slabs' buffers and the
+            # backprojector's row band (kept by the handle): within 15 % of them here
+            assert budget < 4 * 3 * m * 1.15
             continue
         saw.add(pl)
         assert (pl, slab) <= prev  # lexicographic: placement 2 before 1, then thicker slabs
