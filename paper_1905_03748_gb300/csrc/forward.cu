@@ -526,7 +526,8 @@ __device__ __forceinline__ void cut_axis(const Ray& R, int ax, int lo, int hi, i
 // at 6 and 364.7 at 5.
 // With a Batch, several volumes of the same geometry are projected in one
 // launch (blockIdx.z runs over member 0's row tiles, then member 1's, ...).
-template <typename TV, typename TP, bool SLAB = false, bool PAIR = false, int AG = 1>
+template <typename TV, typename TP, bool SLAB = false, bool PAIR = false, int AG = 1,
+          bool BATCH = false>
 __global__ void __launch_bounds__(256, (AG == 1 && !SLAB && !PAIR) ? 7 : 6) fwd_quad_kernel(
     const typename QuadOf<TV>::type* __restrict__ qxy,
     const typename QuadOf<TV>::type* __restrict__ qyx, TP* __restrict__ proj,
@@ -537,11 +538,15 @@ __global__ void __launch_bounds__(256, (AG == 1 && !SLAB && !PAIR) ? 7 : 6) fwd_
     using Q = typename QuadOf<TV>::type;
     constexpr int CW = 32 / AG;  // detector columns per warp
     const unsigned full = 0xffffffffu;
-    const int member = (int)blockIdx.z / bt.tiles;
+    // (batched launches only: single launches keep the member arithmetic and
+    // its registers out of the kernel)
+    const int member = BATCH ? (int)blockIdx.z / bt.tiles : 0;
     const int tile = (int)blockIdx.z - member * bt.tiles;
-    qxy += member * bt.vol_stride;
-    qyx += member * bt.vol_stride;
-    proj += member * bt.proj_stride;
+    if (BATCH) {
+        qxy += member * bt.vol_stride;
+        qyx += member * bt.vol_stride;
+        proj += member * bt.proj_stride;
+    }
     const int p = blockIdx.x * CW + (AG == 1 ? (int)threadIdx.x : (int)threadIdx.x % CW);
     const int q = (SLAB ? sr.q0 : 0) + tile * (int)blockDim.y + (int)threadIdx.y;
     const int a = AG > 1  ? order[blockIdx.y * AG + threadIdx.x / CW]
@@ -937,13 +942,13 @@ tigre_status forward_batch_impl(tigre_geometry* g, const void* vols, void* projs
         // the automatic path of forward_impl for a full-range projection
         if (g->auto_angle_group == 2) {
             dim3 grid((unsigned)((c.nu + 15) / 16), (unsigned)g->n_groups[0], (unsigned)(tiles * batch));
-            fwd_quad_kernel<T, T, false, false, 2><<<grid, dim3(32, 8), 0, st>>>(
+            fwd_quad_kernel<T, T, false, false, 2, true><<<grid, dim3(32, 8), 0, st>>>(
                 (const Q*)quad[0], (const Q*)quad[1], (T*)projs, (const FwdAngle*)g->fwd_params.ptr,
                 c, 0, (const int*)g->angle_groups[0].ptr, SlabRange{0, 0, 0, 0, 0, 0, 0, 0, nullptr},
                 bt);
         } else {
             dim3 grid((unsigned)((c.nu + 31) / 32), (unsigned)na, (unsigned)(tiles * batch));
-            fwd_quad_kernel<T, T, false, false><<<grid, dim3(32, 8), 0, st>>>(
+            fwd_quad_kernel<T, T, false, false, 1, true><<<grid, dim3(32, 8), 0, st>>>(
                 (const Q*)quad[0], (const Q*)quad[1], (T*)projs, (const FwdAngle*)g->fwd_params.ptr,
                 c, 0, (const int*)g->angle_order.ptr, SlabRange{0, 0, 0, 0, 0, 0, 0, 0, nullptr}, bt);
         }
