@@ -24,6 +24,7 @@
 //  * floor() without conversion instructions (split_floor).
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 #include <vector>
 
 #include "quad.cuh"
@@ -203,12 +204,8 @@ __device__ __forceinline__ float tri_sample(const TV* __restrict__ vol, const Ra
     const float v010 = ld(b + PF), v110 = ld(b + PF + 1);
     const float v001 = ld(b + PFM), v101 = ld(b + PFM + 1);
     const float v011 = ld(b + PFM + PF), v111 = ld(b + PFM + PF + 1);
-    const float c00 = fmaf(af, v100 - v000, v000);
-    const float c10 = fmaf(af, v110 - v010, v010);
-    const float c01 = fmaf(af, v101 - v001, v001);
-    const float c11 = fmaf(af, v111 - v011, v011);
-    const float c0 = fmaf(am, c10 - c00, c00);
-    const float c1 = fmaf(am, c11 - c01, c01);
+    const float c0 = bilinear_value(bilinear_coefficients(v000, v100, v010, v110), af, am);
+    const float c1 = bilinear_value(bilinear_coefficients(v001, v101, v011, v111), af, am);
     return fmaf(as, c1 - c0, c0);
 }
 
@@ -294,6 +291,19 @@ __global__ void __launch_bounds__(256) fwd_l1_kernel(const TV* __restrict__ vxy,
 // s-plane: (P[s][m][f], P[s][m][f+1], P[s][m+1][f], P[s][m+1][f+1]) of the
 // zero-padded layout P.  A trilinear sample is then two aligned loads (planes
 // s and s+1) instead of eight scalar ones (element types: quad.cuh).
+//
+// F32 elements hold the cell's bilinear coefficients (bilinear_coefficients)
+// instead of its taps, so a plane's bilinear value is three FMAs
+// (bilinear_value).  16-bit elements hold the taps (a coefficient stored in 16
+// bits would be rounded again); their coefficients are formed after the load,
+// in the same FP32 operations, as the scalar kernels form theirs.
+__device__ __forceinline__ float4 load_fquad(const float4* p, float*) { return __ldg(p); }
+template <typename T16>
+__device__ __forceinline__ float4 load_fquad(const uint2* p, T16* t)
+{
+    const float4 v = load_quad(p, t);
+    return bilinear_coefficients(v.x, v.y, v.z, v.w);
+}
 
 // Build the quad volume of one layout straight from the caller's volume (no
 // padded copy): with P(s, m, f) the zero-bordered layout (vol[s-2][m-2][f-2]
@@ -339,7 +349,7 @@ __global__ void __launch_bounds__(256) quad_from_vol_kernel(const T* __restrict_
         const T c = tile[i + 1][threadIdx.x], d = tile[i + 1][threadIdx.x + 1];
         typename QuadOf<T>::type* o = out + ((int64_t)s * PM + m) * PF + f;
         if constexpr (sizeof(T) == 4)
-            *o = pack_quad(a, b, c, d);
+            *o = bilinear_coefficients(a, b, c, d);
         else
             *o = pack_quad16(a, b, c, d);
     }
@@ -358,94 +368,64 @@ tigre_status build_quads(const tigre_geometry_desc& d, const T* vol, typename Qu
     return TIGRE_OK;
 }
 
-// Build the quad volume of a padded layout; one block per (s, m) row.
-template <typename T>
-__global__ void quad_kernel(const T* __restrict__ pad, typename QuadOf<T>::type* __restrict__ out,
-                            int PF, int PM, int64_t rows)
+// Bias of a quad element index built from split_bits parts: the three
+// splits' 0x4B000000 and the slab's first plane, modulo 2^32.
+__host__ __device__ __forceinline__ uint32_t quad_index_bias(int PF, int PFM, int s_off)
 {
-    const int64_t r = blockIdx.x;
-    if (r >= rows) return;
-    const int m = (int)(r % PM);
-    const T* row = pad + r * PF;
-    const bool has_m1 = m + 1 < PM;
-    for (int f = threadIdx.x; f < PF; f += blockDim.x) {
-        const bool has_f1 = f + 1 < PF;
-        const T z = from_f32<T>(0.0f);
-        const T a = row[f];
-        const T b = has_f1 ? row[f + 1] : z;
-        const T c = has_m1 ? row[PF + f] : z;
-        const T d = (has_m1 && has_f1) ? row[PF + f + 1] : z;
-        if constexpr (sizeof(T) == 4)
-            out[r * PF + f] = pack_quad(a, b, c, d);
-        else
-            out[r * PF + f] = pack_quad16(a, b, c, d);
-    }
+    return 0x4B000000u * (uint32_t)(PFM + PF + 1) + (uint32_t)s_off * (uint32_t)PFM;
 }
 
+// Trilinear sample kf of a ray from the quad volume qv; ym = x0[1] + kf d[1]
+// (the march's depth coordinate, which the caller has already formed).
 template <typename TV>
 __device__ __forceinline__ float tri_sample_quad(const typename QuadOf<TV>::type* __restrict__ qv,
-                                                 const Ray& R, float kf, int PF, int PFM,
-                                                 int s_off = 0)
+                                                 const Ray& R, float kf, float ym, int PF, int PFM,
+                                                 uint32_t bias)
 {
-    int i_f, i_m, i_s;
+    uint32_t b_f, b_m, b_s;
     float af, am, as;
-    split_floor(fmaf(kf, R.d[0], R.x0[0]), i_f, af);
-    split_floor(fmaf(kf, R.d[1], R.x0[1]), i_m, am);
-    split_floor(fmaf(kf, R.d[2], R.x0[2]), i_s, as);
-    const typename QuadOf<TV>::type* b = qv + ((i_s - s_off) * PFM + i_m * PF + i_f);
-    const float4 lo = load_quad(b, (TV*)nullptr);        // plane s: v000 v100 v010 v110
-    const float4 hi = load_quad(b + PFM, (TV*)nullptr);  // plane s+1: v001 v101 v011 v111
-    const float c00 = fmaf(af, lo.y - lo.x, lo.x);
-    const float c10 = fmaf(af, lo.w - lo.z, lo.z);
-    const float c01 = fmaf(af, hi.y - hi.x, hi.x);
-    const float c11 = fmaf(af, hi.w - hi.z, hi.z);
-    const float c0 = fmaf(am, c10 - c00, c00);
-    const float c1 = fmaf(am, c11 - c01, c01);
+    split_bits(fmaf(kf, R.d[0], R.x0[0]), b_f, af);
+    split_bits(ym, b_m, am);
+    split_bits(fmaf(kf, R.d[2], R.x0[2]), b_s, as);
+    const uint32_t e = b_s * (uint32_t)PFM + b_m * (uint32_t)PF + b_f - bias;
+    const typename QuadOf<TV>::type* b = qv + e;
+    const float c0 = bilinear_value(load_fquad(b, (TV*)nullptr), af, am);        // plane s
+    const float c1 = bilinear_value(load_fquad(b + PFM, (TV*)nullptr), af, am);  // plane s+1
     return fmaf(as, c1 - c0, c0);
 }
 
-// Samples k and k + 1 of a ray (kf = k), added to acc in that order when t0
-// (resp. t1) holds.  Both samples' loads are issued before either
-// interpolation, so four gathers are in flight per thread; a sample not taken
-// reads the volume's first element and adds nothing, so the sum is bitwise
-// the one-sample-at-a-time sum.
+// Samples k and k + 1 of a ray (kf = k, depth coordinates ym0 and ym1), added
+// to acc in that order when t0 (resp. t1) holds.  Both samples' loads are
+// issued before either interpolation, so four gathers are in flight per
+// thread; a sample not taken reads the volume's first element and adds
+// nothing, so the sum is bitwise the one-sample-at-a-time sum.
 template <typename TV>
 __device__ __forceinline__ void tri_pair_quad(const typename QuadOf<TV>::type* __restrict__ qv,
-                                              const Ray& R, float kf, int PF, int PFM, int s_off,
-                                              bool t0, bool t1, float& acc)
+                                              const Ray& R, float kf, float ym0, float ym1, int PF,
+                                              int PFM, uint32_t bias, bool t0, bool t1, float& acc)
 {
     using Q = typename QuadOf<TV>::type;
-    int f0, m0, z0, f1, m1, z1;
+    uint32_t f0, m0, z0, f1, m1, z1;
     float af0, am0, as0, af1, am1, as1;
     const float kf1 = kf + 1.0f;
-    split_floor(fmaf(kf, R.d[0], R.x0[0]), f0, af0);
-    split_floor(fmaf(kf, R.d[1], R.x0[1]), m0, am0);
-    split_floor(fmaf(kf, R.d[2], R.x0[2]), z0, as0);
-    split_floor(fmaf(kf1, R.d[0], R.x0[0]), f1, af1);
-    split_floor(fmaf(kf1, R.d[1], R.x0[1]), m1, am1);
-    split_floor(fmaf(kf1, R.d[2], R.x0[2]), z1, as1);
-    const Q* b0 = t0 ? qv + ((z0 - s_off) * PFM + m0 * PF + f0) : qv;
-    const Q* b1 = t1 ? qv + ((z1 - s_off) * PFM + m1 * PF + f1) : qv;
-    const float4 lo0 = load_quad(b0, (TV*)nullptr);
-    const float4 hi0 = load_quad(b0 + PFM, (TV*)nullptr);
-    const float4 lo1 = load_quad(b1, (TV*)nullptr);
-    const float4 hi1 = load_quad(b1 + PFM, (TV*)nullptr);
+    split_bits(fmaf(kf, R.d[0], R.x0[0]), f0, af0);
+    split_bits(ym0, m0, am0);
+    split_bits(fmaf(kf, R.d[2], R.x0[2]), z0, as0);
+    split_bits(fmaf(kf1, R.d[0], R.x0[0]), f1, af1);
+    split_bits(ym1, m1, am1);
+    split_bits(fmaf(kf1, R.d[2], R.x0[2]), z1, as1);
+    const Q* b0 = t0 ? qv + (z0 * (uint32_t)PFM + m0 * (uint32_t)PF + f0 - bias) : qv;
+    const Q* b1 = t1 ? qv + (z1 * (uint32_t)PFM + m1 * (uint32_t)PF + f1 - bias) : qv;
+    const float4 lo0 = load_fquad(b0, (TV*)nullptr);
+    const float4 hi0 = load_fquad(b0 + PFM, (TV*)nullptr);
+    const float4 lo1 = load_fquad(b1, (TV*)nullptr);
+    const float4 hi1 = load_fquad(b1 + PFM, (TV*)nullptr);
     {
-        const float c00 = fmaf(af0, lo0.y - lo0.x, lo0.x);
-        const float c10 = fmaf(af0, lo0.w - lo0.z, lo0.z);
-        const float c01 = fmaf(af0, hi0.y - hi0.x, hi0.x);
-        const float c11 = fmaf(af0, hi0.w - hi0.z, hi0.z);
-        const float c0 = fmaf(am0, c10 - c00, c00);
-        const float c1 = fmaf(am0, c11 - c01, c01);
+        const float c0 = bilinear_value(lo0, af0, am0), c1 = bilinear_value(hi0, af0, am0);
         if (t0) acc += fmaf(as0, c1 - c0, c0);
     }
     {
-        const float c00 = fmaf(af1, lo1.y - lo1.x, lo1.x);
-        const float c10 = fmaf(af1, lo1.w - lo1.z, lo1.z);
-        const float c01 = fmaf(af1, hi1.y - hi1.x, hi1.x);
-        const float c11 = fmaf(af1, hi1.w - hi1.z, hi1.z);
-        const float c0 = fmaf(am1, c10 - c00, c00);
-        const float c1 = fmaf(am1, c11 - c01, c01);
+        const float c0 = bilinear_value(lo1, af1, am1), c1 = bilinear_value(hi1, af1, am1);
         if (t1) acc += fmaf(as1, c1 - c0, c0);
     }
 }
@@ -520,15 +500,15 @@ __device__ __forceinline__ void cut_axis(const Ray& R, int ax, int lo, int hi, i
 // holds 32 / AG pixels of one detector row at AG neighbouring angles (order
 // is then the angle-group table, blockIdx.y the group; full-range, in-core
 // launches only); each ray is marched exactly as with AG = 1.
-// Occupancy: with angle pairs, 6 blocks per SM (40 registers): 130.3 ms per
+// Occupancy: 6 blocks per SM (40 registers).  With angle pairs: 130.3 ms per
 // 512^3 x 360 projection against 136.7 at 5 blocks and 143.2 at 7 or 8.  One
-// angle per warp in core, 7 blocks: 309.8 ms per 1024^3 x 90 against 321.6
-// at 6 and 364.7 at 5.
+// angle per warp in core: 308.0 ms per 1024^3 x 90 against 312.6 at 7 (32
+// registers, spilling in the march loop).
 // With a Batch, several volumes of the same geometry are projected in one
 // launch (blockIdx.z runs over member 0's row tiles, then member 1's, ...).
 template <typename TV, typename TP, bool SLAB = false, bool PAIR = false, int AG = 1,
           bool BATCH = false>
-__global__ void __launch_bounds__(256, (AG == 1 && !SLAB && !PAIR) ? 7 : 6) fwd_quad_kernel(
+__global__ void __launch_bounds__(256, 6) fwd_quad_kernel(
     const typename QuadOf<TV>::type* __restrict__ qxy,
     const typename QuadOf<TV>::type* __restrict__ qyx, TP* __restrict__ proj,
     const FwdAngle* __restrict__ params, FwdConst c, int a_first, const int* __restrict__ order,
@@ -547,9 +527,16 @@ __global__ void __launch_bounds__(256, (AG == 1 && !SLAB && !PAIR) ? 7 : 6) fwd_
         qyx += member * bt.vol_stride;
         proj += member * bt.proj_stride;
     }
-    const int p = blockIdx.x * CW + (AG == 1 ? (int)threadIdx.x : (int)threadIdx.x % CW);
+    // Each 16-lane half of a warp holds 8 pixels of two neighbouring angles
+    // (pairs: lane = 2 * pixel + angle; groups of 4: lanes 8j..8j+7 hold angle
+    // j).  A 128-bit warp load is served a half-warp at a time, and 8 pixels of
+    // two neighbouring angles touch fewer 128-byte lines than 16 pixels of one
+    // angle do.
+    const int lane_p = AG == 2 ? (int)threadIdx.x >> 1 : (int)threadIdx.x % CW;
+    const int lane_a = AG == 2 ? (int)threadIdx.x & 1 : (int)threadIdx.x / CW;
+    const int p = blockIdx.x * CW + (AG == 1 ? (int)threadIdx.x : lane_p);
     const int q = (SLAB ? sr.q0 : 0) + tile * (int)blockDim.y + (int)threadIdx.y;
-    const int a = AG > 1  ? order[blockIdx.y * AG + threadIdx.x / CW]
+    const int a = AG > 1  ? order[blockIdx.y * AG + lane_a]
                   : order ? order[blockIdx.y]
                           : (int)blockIdx.y;
     if (SLAB && sr.prange) {  // uniform per block: all its rays miss the brick
@@ -583,7 +570,9 @@ __global__ void __launch_bounds__(256, (AG == 1 && !SLAB && !PAIR) ? 7 : 6) fwd_
     if (act) {
         const unsigned pos = __ballot_sync(full, active && R.d[1] > 0.0f);
         const unsigned neg = __ballot_sync(full, active && R.d[1] < 0.0f);
-        int k = kb;
+        const uint32_t bias = quad_index_bias(PF, PFM, s_off);
+        // sample counters in float (exact: K < 2^24)
+        const float kef = (float)ke;
         float kf = (float)kb;
         if (pos == act || neg == act) {
             const float sgn = pos == act ? 1.0f : -1.0f;
@@ -601,30 +590,46 @@ __global__ void __launch_bounds__(256, (AG == 1 && !SLAB && !PAIR) ? 7 : 6) fwd_
             }
             const float ns = (Y1 - Y0) / D;
             const int nslab = ns < (float)(2 * kmax + 64) ? (int)ns + 1 : 0;
+            // sgn * ym is the depth coordinate fmaf(kf, dy, y0) (the sign
+            // flip is exact), and ym feeds the sample's m split
             if (PAIR) {
                 const float D2 = 2.0f * D;
-                for (int j = 1; j <= (nslab + 1) / 2; ++j) {
-                    const float bound = fmaf((float)j, D2, Y0);
-                    const bool t0 = k < ke && fmaf(kf, dy, y0) < bound;
-                    const bool t1 = t0 && k + 1 < ke && fmaf(kf + 1.0f, dy, y0) < bound;
-                    if (__any_sync(full, t0)) tri_pair_quad<TV>(vol, R, kf, PF, PFM, s_off, t0, t1, acc);
-                    const int took = (int)t0 + (int)t1;
-                    k += took;
-                    kf += (float)took;
+                const float nj = (float)((nslab + 1) / 2);
+                for (float jf = 1.0f; jf <= nj; jf += 1.0f) {
+                    const float bound = fmaf(jf, D2, Y0);
+                    const float ym0 = fmaf(kf, R.d[1], R.x0[1]);
+                    const float ym1 = fmaf(kf + 1.0f, R.d[1], R.x0[1]);
+                    const bool t0 = kf < kef && sgn * ym0 < bound;
+                    const bool t1 = t0 && kf + 1.0f < kef && sgn * ym1 < bound;
+                    if (__any_sync(full, t0))
+                        tri_pair_quad<TV>(vol, R, kf, ym0, ym1, PF, PFM, bias, t0, t1, acc);
+                    kf += (float)((int)t0 + (int)t1);
                 }
             } else {
-                for (int j = 1; j <= nslab; ++j) {
-                    const float bound = fmaf((float)j, D, Y0);
-                    if (k < ke && fmaf(kf, dy, y0) < bound) {
-                        acc += tri_sample_quad<TV>(vol, R, kf, PF, PFM, s_off);
-                        ++k;
-                        kf += 1.0f;
+                // one loop per march direction: for sgn = -1 the test
+                // -ym < bound is ym > -bound, with -bound = fmaf(jf, -D, -Y0)
+                // exactly
+                const float nj = (float)nslab;
+                auto march = [&](auto neg) {
+                    constexpr bool NEG = decltype(neg)::value;
+                    const float Ds = NEG ? -D : D, Ys = NEG ? -Y0 : Y0;
+                    for (float jf = 1.0f; jf <= nj; jf += 1.0f) {
+                        const float bound = fmaf(jf, Ds, Ys);
+                        const float ym = fmaf(kf, R.d[1], R.x0[1]);
+                        if (kf < kef && (NEG ? ym > bound : ym < bound)) {
+                            acc += tri_sample_quad<TV>(vol, R, kf, ym, PF, PFM, bias);
+                            kf += 1.0f;
+                        }
                     }
-                }
+                };
+                if (sgn > 0.0f)
+                    march(std::false_type{});
+                else
+                    march(std::true_type{});
             }
         }
-        for (; active && k < ke; ++k, kf += 1.0f)
-            acc += tri_sample_quad<TV>(vol, R, kf, PF, PFM, s_off);
+        for (; active && kf < kef; kf += 1.0f)
+            acc += tri_sample_quad<TV>(vol, R, kf, fmaf(kf, R.d[1], R.x0[1]), PF, PFM, bias);
     }
     if (!inside) return;
     TP* o = proj + ((int64_t)a * c.nv + q) * c.nu + p;

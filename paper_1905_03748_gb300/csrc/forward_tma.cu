@@ -294,12 +294,10 @@ __global__ void __launch_bounds__(256) fwd_tma_kernel(const __grid_constant__ CU
                     const float v001 = to_f32<TV>(b[C::SP]), v101 = to_f32<TV>(b[C::SP + 1]);
                     const float v011 = to_f32<TV>(b[C::SP + C::FB]);
                     const float v111 = to_f32<TV>(b[C::SP + C::FB + 1]);
-                    const float c00 = fmaf(af, v100 - v000, v000);
-                    const float c10 = fmaf(af, v110 - v010, v010);
-                    const float c01 = fmaf(af, v101 - v001, v001);
-                    const float c11 = fmaf(af, v111 - v011, v011);
-                    const float c0 = fmaf(am, c10 - c00, c00);
-                    const float c1 = fmaf(am, c11 - c01, c01);
+                    const float c0 =
+                        bilinear_value(bilinear_coefficients(v000, v100, v010, v110), af, am);
+                    const float c1 =
+                        bilinear_value(bilinear_coefficients(v001, v101, v011, v111), af, am);
                     acc += fmaf(as, c1 - c0, c0);
                 }
             }

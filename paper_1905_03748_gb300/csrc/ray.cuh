@@ -34,6 +34,31 @@ __device__ __forceinline__ void split_floor(float x, int& i, float& f)
     f = __fsub_rn(x, __fsub_rn(m, 8388608.0f));
 }
 
+// Bilinear interpolation of one cell of a plane, as every forward kernel
+// takes it.  With taps a = (f, m), b = (f+1, m), c = (f, m+1), d = (f+1, m+1),
+// the coefficients are (a, b - a, c - a, (d - c) - (b - a)) and the value at
+// fractions (af, am) is a + af (b - a) + am ((c - a) + af ((d - c) - (b - a))),
+// three FMAs.
+__host__ __device__ __forceinline__ float4 bilinear_coefficients(float a, float b, float c, float d)
+{
+    const float df = b - a;
+    return make_float4(a, df, c - a, (d - c) - df);
+}
+__device__ __forceinline__ float bilinear_value(const float4& e, float af, float am)
+{
+    return fmaf(am, fmaf(af, e.w, e.z), fmaf(af, e.y, e.x));
+}
+
+// The same split with the integer part left biased: b = i + 0x4B000000, the
+// bit pattern of the rounded sum.  An index summed over several axes then
+// removes the biases with one subtraction (modulo 2^32).
+__device__ __forceinline__ void split_bits(float x, uint32_t& b, float& f)
+{
+    const float m = __fadd_rn(x, 8388607.5f);
+    b = (uint32_t)__float_as_int(m);
+    f = __fsub_rn(x, __fsub_rn(m, 8388608.0f));
+}
+
 // One ray in the padded index coordinates of its angle's layout.
 struct Ray {
     float x0[3];  // first sample (f, m, s), padded coordinates
