@@ -16,8 +16,9 @@
 // volume's shadow can reach beyond the detector for this geometry (bounded
 // on the host), so the per-voxel loop has neither clamps nor branches; u is
 // clamped once per column and angle.  In-core launches use a quad buffer:
-// element (r, c) holds the four taps (c, c+1) x (r, r+1) of the bilinear
-// cell, so a voxel-angle pair costs one aligned 16-byte load (8 bytes for
+// element (r, c) holds the bilinear cell (c, c+1) x (r, r+1) (F32: its four
+// bilinear coefficients, so the interpolation is three FMAs; 16-bit: its four
+// taps), and a voxel-angle pair costs one aligned 16-byte load (8 bytes for
 // 16-bit storage) instead of four scalar loads and their addresses (the
 // kernel is bound by instruction issue).  Out-of-core slab launches keep the
 // plain buffer: a thin slab's band of rows spans the cone's spread (hundreds
@@ -56,9 +57,12 @@ struct BpConst {
 };
 
 // 1/sqrt(x) straight from the special-function unit (PTX rsqrt.approx, inputs
-// below the smallest normal flushed to zero).  Used where x is a squared
-// source-voxel distance in mm^2, far inside the normal range, for which it
-// returns what rsqrtf does without rsqrtf's denormal handling.
+// below the smallest normal flushed to zero).  Used where x = (w l)^2, the
+// squared matched weight times source-voxel distance: w l is about
+// (dx dy dz)/(du dv) times the squared magnification (at least 1), so x stays
+// far inside the normal range for any voxel volume per pixel area above
+// 1e-18 mm, and there it returns what rsqrtf does without rsqrtf's denormal
+// handling.
 __device__ __forceinline__ float rsqrt_sfu(float x)
 {
     float r;
@@ -67,22 +71,31 @@ __device__ __forceinline__ float rsqrt_sfu(float x)
 }
 
 
-// The four bilinear taps (c, c+1) x (r, r+1) of the cell at `cell`, from the
-// plain (QUADP false) or the quad (true) zero-bordered projection buffer.
+// The bilinear coefficients (bilinear_coefficients: u along columns, v along
+// rows) of the cell (c, c+1) x (r, r+1) at `cell`, from the plain (QUADP
+// false) or the quad (true) zero-bordered projection buffer.  F32 quads store
+// the coefficients; plain and 16-bit buffers hold taps, whose coefficients are
+// formed after the load in the same FP32 operations.
 template <typename TP, bool QUADP> struct ProjTaps;
 template <typename TP> struct ProjTaps<TP, false> {
     using E = TP;
     static __device__ __forceinline__ float4 load(const E* cell, int PU)
     {
-        return make_float4(to_f32<TP>(__ldg(cell)), to_f32<TP>(__ldg(cell + 1)),
-                           to_f32<TP>(__ldg(cell + PU)), to_f32<TP>(__ldg(cell + PU + 1)));
+        return bilinear_coefficients(to_f32<TP>(__ldg(cell)), to_f32<TP>(__ldg(cell + 1)),
+                                     to_f32<TP>(__ldg(cell + PU)),
+                                     to_f32<TP>(__ldg(cell + PU + 1)));
     }
 };
 template <typename TP> struct ProjTaps<TP, true> {
     using E = typename QuadOf<TP>::type;
     static __device__ __forceinline__ float4 load(const E* cell, int)
     {
-        return load_quad(cell, (TP*)nullptr);
+        if constexpr (sizeof(TP) == 4) {
+            return __ldg(cell);
+        } else {
+            const float4 t = load_quad(cell, (TP*)nullptr);
+            return bilinear_coefficients(t.x, t.y, t.z, t.w);
+        }
     }
 };
 
@@ -144,6 +157,9 @@ __global__ void __launch_bounds__(256, (bp_blocks_per_sm<MODE, SART, QUADP>())) 
     const int64_t PA = (int64_t)PU * c.PV;
     const float pu_hi = (float)c.nu + 0.5f;
     const float pv_off = c.pv_off + (float)c.pv_lo;
+    // a row's element offset from split_bits parts: (b - 0x4B000000) PU, one
+    // multiply-add modulo 2^32
+    const uint32_t row_bias = 0x4B000000u * (uint32_t)PU;
 
     float acc[NZ];
     float nrm[SART ? NZ : 1];
@@ -172,36 +188,39 @@ __global__ void __launch_bounds__(256, (bp_blocks_per_sm<MODE, SART, QUADP>())) 
         if (SART)
             tu = ((unsigned)(ip - kPad) < (unsigned)c.nu ? 1.0f - fu : 0.0f) +
                  ((unsigned)(ip - kPad + 1) < (unsigned)c.nu ? fu : 0.0f);
-        float w, lxy2 = 0.0f;
+        // matched: voxel k's weight w |source - voxel| is taken as
+        // sqrt(u) = u rsqrt(u) with u = (w Z)^2 + w^2 |(ex, ey)|^2, one
+        // multiply fewer per voxel than w (l2 rsqrt(l2))
+        float w, w2lxy = 0.0f, wdz = 0.0f, wZb = 0.0f;
         if (MODE == TIGRE_BP_FDK) {
             const float t = c.DSO * inv_den;
             w = t * t;
         } else {
             const float ex = X - A.srcx, ey = Y - A.srcy;
-            lxy2 = fmaf(ex, ex, ey * ey);
             w = c.wscale * inv_den * inv_den * inv_den;
+            w2lxy = (w * w) * fmaf(ex, ex, ey * ey);
+            wdz = w * c.dz;
+            wZb = w * Zb;
         }
 #pragma unroll
         for (int k = 0; k < NZ; ++k) {
-            int iq;
+            uint32_t bq;
             float fv;
-            split_floor(fmaf((float)k, dpv, pv0), iq, fv);
-            // (a00, a01, a10, a11): columns ip, ip + 1 of rows iq, iq + 1
-            const float4 t = ProjTaps<TP, QUADP>::load(col + iq * PU, PU);
-            const float top = fmaf(fu, t.y - t.x, t.x);
-            const float bot = fmaf(fu, t.w - t.z, t.z);
-            const float val = fmaf(fv, bot - top, top);
+            split_bits(fmaf((float)k, dpv, pv0), bq, fv);
+            // the cell of columns ip, ip + 1 and rows iq, iq + 1 (iq = bq - 0x4B000000)
+            const auto* cell = col + (bq * (uint32_t)PU - row_bias);
+            const float val = bilinear_value(ProjTaps<TP, QUADP>::load(cell, PU), fu, fv);
             float wk = w;
             if (MODE != TIGRE_BP_FDK) {
-                const float Z = fmaf((float)k, c.dz, Zb);
-                const float l2 = fmaf(Z, Z, lxy2);
-                wk = w * (l2 * rsqrt_sfu(l2));
+                const float Zw = fmaf((float)k, wdz, wZb);
+                const float u2 = fmaf(Zw, Zw, w2lxy);
+                wk = u2 * rsqrt_sfu(u2);
             }
             acc[k] = fmaf(wk, val, acc[k]);
             if (SART) {
-                const int qq = iq - c.pv_lo;
-                const float tv = ((unsigned)qq < (unsigned)c.nv ? 1.0f - fv : 0.0f) +
-                                 ((unsigned)(qq + 1) < (unsigned)c.nv ? fv : 0.0f);
+                const uint32_t qq = bq - (0x4B000000u + (uint32_t)c.pv_lo);
+                const float tv = (qq < (unsigned)c.nv ? 1.0f - fv : 0.0f) +
+                                 (qq + 1u < (unsigned)c.nv ? fv : 0.0f);
                 nrm[k] = fmaf(wk, tu * tv, nrm[k]);
             }
         }
@@ -233,8 +252,9 @@ __device__ __forceinline__ TP pix_or_zero(const TP* row, int p, int nu)
 
 // Write the whole zero-bordered buffer of one angle range: with
 // Z(r, c) = y[a][r - pv_lo][c - 2] (zero outside the detector), the plain
-// buffer holds out[a][r][c] = Z(r, c), the quad buffer
-// out[a][r][c] = (Z(r, c), Z(r, c+1), Z(r+1, c), Z(r+1, c+1)).
+// buffer holds out[a][r][c] = Z(r, c), the quad buffer the cell
+// (Z(r, c), Z(r, c+1), Z(r+1, c), Z(r+1, c+1)): its bilinear coefficients for
+// F32, the taps themselves for 16-bit storage.
 template <typename TP, bool QUADP>
 __global__ void pad_proj_kernel(const TP* __restrict__ in,
                                 typename ProjTaps<TP, QUADP>::E* __restrict__ out, int nu, int nv,
@@ -257,7 +277,7 @@ __global__ void pad_proj_kernel(const TP* __restrict__ in,
             const TP a10 = in1 ? pix_or_zero(row1, p, nu) : z;
             const TP a11 = in1 ? pix_or_zero(row1, p + 1, nu) : z;
             if constexpr (sizeof(TP) == 4)
-                dst[col] = pack_quad(a00, a01, a10, a11);
+                dst[col] = bilinear_coefficients(a00, a01, a10, a11);
             else
                 dst[col] = pack_quad16(a00, a01, a10, a11);
         }
