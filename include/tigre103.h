@@ -427,20 +427,21 @@ TIGRE_API tigre_status tigre_geometry_set_brick(tigre_geometry_t geo, int64_t ed
 
 /* Kernel choice for this handle's Sec. 2.1 projector (no counterpart in the
  * paper): 0 = automatic (the quad
- * gather kernel; with 2 angles per warp for full-range calls when the rays of
- * one pixel at paired angles stay within 16 voxels of each other, e.g. 512^3 x
- * 360), 1 = scalar L1 gather kernel, 2 = shared-memory slab kernel
- * (TMA-staged; only for geometries whose ray bundles fit its staging box,
- * otherwise it reports error bit 2 and NaN), 3 = quad gather kernel (two
- * 16-byte loads per sample from a layout holding the four taps of a cell's
- * plane; four times the volume in workspace), 4 = quad gather kernel taking a
+ * gather kernel; with 2 angles per warp when the rays of one pixel at paired
+ * angles stay within 16 voxels of each other, e.g. 512^3 x 360), 1 = scalar
+ * L1 gather kernel, 2 = shared-memory slab kernel (TMA-staged; only for
+ * geometries whose ray bundles fit its staging box, otherwise it reports
+ * error bit 2 and NaN), 3 = quad gather kernel (two 16-byte loads per sample
+ * from a layout holding a cell plane's four taps, as bilinear coefficients for
+ * F32; four times the volume in workspace), 4 = quad gather kernel taking a
  * ray's samples two at a time (both samples' loads issued together), 5 / 6 =
  * quad gather kernel whose warps hold 16 pixels x 2 / 8 pixels x 4 angles
  * (neighbouring angles of one memory layout and march direction, so a warp's
- * gathers share cache lines; full-range calls, other ranges use path 3).
+ * gathers share cache lines; a partial angle range groups its own angles).
  * All compute the same sums in the same order and give identical results.
- * Out-of-core slab projections use the quad kernel, two samples at a time for
- * path 4. */
+ * Out-of-core slab projections use the quad kernel: two samples at a time for
+ * path 4, warps of 2 angles for path 5 and for path 0 when it pairs angles,
+ * one angle per warp otherwise. */
 TIGRE_API tigre_status tigre_geometry_set_forward_path(tigre_geometry_t geo, int path);
 
 /* Scheduling of the Sec. 2.1 projector's threads (no counterpart in the

@@ -498,8 +498,8 @@ __device__ __forceinline__ void cut_axis(const Ray& R, int ax, int lo, int hi, i
 // brick).  With PAIR, the march advances two depth steps at a time and each
 // lane takes up to two samples per step (tri_pair_quad).  With AG > 1 a warp
 // holds 32 / AG pixels of one detector row at AG neighbouring angles (order
-// is then the angle-group table, blockIdx.y the group; full-range, in-core
-// launches only); each ray is marched exactly as with AG = 1.
+// is then the angle-group table, blockIdx.y the group; not with PAIR); each
+// ray is marched exactly as with AG = 1.
 // Occupancy: 6 blocks per SM (40 registers).  With angle pairs: 130.3 ms per
 // 512^3 x 360 projection against 136.7 at 5 blocks and 143.2 at 7 or 8.  One
 // angle per warp in core: 308.0 ms per 1024^3 x 90 against 312.6 at 7 (32
@@ -514,7 +514,7 @@ __global__ void __launch_bounds__(256, 6) fwd_quad_kernel(
     const FwdAngle* __restrict__ params, FwdConst c, int a_first, const int* __restrict__ order,
     SlabRange sr, FwdBatch bt = FwdBatch{})
 {
-    static_assert(AG == 1 || (!SLAB && !PAIR), "angle groups: in-core single-sample march only");
+    static_assert(AG == 1 || !PAIR, "angle groups: single-sample march only");
     using Q = typename QuadOf<TV>::type;
     constexpr int CW = 32 / AG;  // detector columns per warp
     const unsigned full = 0xffffffffu;
@@ -540,9 +540,15 @@ __global__ void __launch_bounds__(256, 6) fwd_quad_kernel(
                   : order ? order[blockIdx.y]
                           : (int)blockIdx.y;
     if (SLAB && sr.prange) {  // uniform per block: all its rays miss the brick
-        const int2 pr = sr.prange[a_first + a];
-        const int p0 = (int)blockIdx.x * 32;
-        if (p0 + 31 < pr.x || p0 > pr.y) return;
+        const int p0 = (int)blockIdx.x * CW;
+        bool hit = false;
+        for (int j = 0; j < AG; ++j) {
+            const int aj = AG > 1 ? order[blockIdx.y * AG + j] : a;
+            if (aj < 0) continue;
+            const int2 pr = sr.prange[a_first + aj];
+            hit = hit || !(p0 + CW - 1 < pr.x || p0 > pr.y);
+        }
+        if (!hit) return;
     }
     const bool inside = p < c.nu && q < c.nv && (AG == 1 || a >= 0);
 
@@ -1054,6 +1060,22 @@ tigre_status forward_slab_impl(tigre_geometry* g, const tigre_geometry_desc& sd,
     const int64_t na_all = (int64_t)g->angles.size();
     auto kern = g->fwd_path == 4 ? fwd_quad_kernel<float, float, true, true>
                                  : fwd_quad_kernel<float, float, true, false>;
+    // Angle pairs where the in-core projection takes them (the automatic
+    // choice or the pair path): group table of the full range (absolute
+    // indices) or of [a0, a0 + na) (indices relative to a0).
+    const int* table = nullptr;
+    int64_t ngroups = 0;
+    int pair_first = 0;
+    if (g->fwd_path == 5 || (g->fwd_path == 0 && g->auto_angle_group == 2)) {
+        if (a0 == 0 && na == na_all) {
+            table = (const int*)g->angle_groups[0].ptr;
+            ngroups = g->n_groups[0];
+        } else {
+            TIGRE_TRY(range_group_table(g, 0, a0, na, &table, &ngroups));
+            pair_first = (int)a0;
+        }
+        if (ngroups > 65535) table = nullptr;
+    }
     ProfScope prof(kProfForward, st);
     for (int64_t by = 0; by < nby; ++by)
         for (int64_t bx = 0; bx < nbx; ++bx) {
@@ -1064,6 +1086,15 @@ tigre_status forward_slab_impl(tigre_geometry* g, const tigre_geometry_desc& sd,
             const int by_hi = by == nby - 1 ? 1000000 : (int)((by + 1) * edge + kPad);
             const int2* brick_pr = pr ? pr + (by * nbx + bx) * na_all : nullptr;
             const SlabRange sr{cell_lo, cell_hi, plane0, q_lo, bx_lo, bx_hi, by_lo, by_hi, brick_pr};
+            if (table) {
+                dim3 grid((unsigned)((c.nu + 15) / 16), (unsigned)ngroups,
+                          (unsigned)((q_hi - q_lo + 7) / 8));
+                fwd_quad_kernel<float, float, true, false, 2><<<grid, dim3(32, 8), 0, st>>>(
+                    quad[0], quad[1], proj, (const FwdAngle*)g->fwd_params.ptr, c, pair_first,
+                    table, sr, FwdBatch{});
+                TIGRE_LAUNCHED("fwd_quad_kernel(slab, pairs)");
+                continue;
+            }
             for (int64_t s = 0; s < na; s += 65535) {
                 const int64_t cnt = std::min<int64_t>(65535, na - s);
                 dim3 grid((unsigned)((c.nu + 31) / 32), (unsigned)cnt,

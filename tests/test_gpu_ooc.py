@@ -87,6 +87,30 @@ def test_forward_ooc_paired_samples_bitwise(tigre):
     assert torch.equal(outs[0], outs[1])
 
 
+@pytest.mark.parametrize("brick", [0, 16])
+@pytest.mark.parametrize("a0,count", [(0, 19), (3, 11)])
+def test_forward_ooc_angle_pairs_bitwise(tigre, brick, a0, count):
+    """Slab projections with warps of two neighbouring angles (the full
+    range's group table, or a partial range's own) add the same samples in
+    the same order as one angle per warp, x-y bricks included."""
+    geo, ang, vol = case()
+    outs = []
+    with tigre.Geometry(geo, ang) as G:
+        if brick:
+            tigre.tigre_geometry_set_brick(G.handle, brick)
+        for path in (tigre.FWD_QUAD, tigre.FWD_QUAD_ANGLES2):
+            tigre.tigre_geometry_set_forward_path(G.handle, path)
+            out = torch.zeros((count, geo["n_det"][1], geo["n_det"][0]), device="cuda")
+            tigre.tigre_forward_ooc(G.handle, torch.from_numpy(vol.copy()), out, a0, count,
+                                    slab_planes=5)
+            outs.append(out)
+        ref = G.forward(torch.from_numpy(vol).cuda(), angle_begin=a0, angle_count=count)
+        assert tigre.tigre_geometry_error_flags(G.handle) == 0
+    assert torch.isfinite(outs[1]).all()
+    assert torch.equal(outs[0], outs[1])
+    assert rel(outs[1].cpu().numpy(), ref.cpu().numpy()) < 1e-6
+
+
 @pytest.mark.parametrize("slab", [1, 5, 23])
 @pytest.mark.parametrize("weight", ["matched", "fdk"])
 def test_backward_ooc_device_projections(tigre, slab, weight):
