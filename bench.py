@@ -35,8 +35,13 @@ METRIC = "Ax/Aᵀy Gvoxel·angles/s and CGLS s/iter at 512³×360"
 UNIT = "Gvoxel*angles/s"
 FLOPS_PER_SAMPLE = 22  # trilinear interpolation: 7 lerps x 3 flops + 1 accumulation
 L1_BYTES_PER_SAMPLE = 32  # the eight FP32 taps a trilinear sample gathers
-KERNEL_SOURCES = ["paper_1905_03748_gb300/csrc/forward.cu", "paper_1905_03748_gb300/csrc/ray.cuh"]
+L1_BYTES_PER_VOXEL_ANGLE = 16  # the four FP32 taps a backprojected voxel-angle gathers
+KERNEL_SOURCES = ["paper_1905_03748_gb300/csrc/forward.cu", "paper_1905_03748_gb300/csrc/ray.cuh",
+                  "paper_1905_03748_gb300/csrc/quad.cuh"]
+BP_SOURCES = ["paper_1905_03748_gb300/csrc/backward.cu", "paper_1905_03748_gb300/csrc/ray.cuh",
+              "paper_1905_03748_gb300/csrc/quad.cuh"]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "fwd_kernel_traffic.json")
+BP_SOL_FILE = os.path.join(ROOT, "profiles", "bp_kernel_sol.json")
 
 
 def parse():
@@ -72,9 +77,9 @@ def config_dict(geo, ang):
             "phantom": "50 seeded random ellipsoids (seed 2), b = A x_true"}
 
 
-def source_hash() -> str:
+def source_hash(sources=KERNEL_SOURCES) -> str:
     h = hashlib.sha256()
-    for p in KERNEL_SOURCES:
+    for p in sources:
         with open(os.path.join(ROOT, p), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -288,6 +293,15 @@ def run_ours(args):
             sol = tr.get("ncu_sol")
     except Exception:
         pass
+    bp_sol = None
+    try:
+        with open(BP_SOL_FILE) as f:
+            tr = json.load(f)
+        if tr.get("source_hash") == source_hash(BP_SOURCES):
+            bp_sol = tr.get("ncu_sol")
+    except Exception:
+        pass
+    bp_l1 = vox_ang * L1_BYTES_PER_VOXEL_ANGLE / (bp_avg / 1e3) / 1e12
 
     out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -314,6 +328,12 @@ def run_ours(args):
                                 "per_unit": f"{FLOPS_PER_SAMPLE} FP32 flops per sample",
                                 "peak_source": f"{n_sm} SMs x 128 FP32 lanes x 2 x "
                                                f"{sm_max_mhz:.0f} MHz (derived)"}},
+           "roofline_backprojector": {"kernel": "bp_voxel_kernel (matched)", "bound": "l1",
+                                      "achieved": bp_l1, "peak": l1_peak, "unit": "TB/s",
+                                      "frac": bp_l1 / l1_peak,
+                                      "per_unit": f"{L1_BYTES_PER_VOXEL_ANGLE} B gathered per "
+                                                  "voxel-angle (four FP32 taps)",
+                                      "ncu_sol": bp_sol},
            "gpu_launches": launches, "clocks": clk.summary(),
            "paper_context": "CGLS 512^3, 15 it in 61 s (4.1 s/iter incl. host copies), "
                             "1x GTX 1080 Ti (Sec. 4); detector/angles not stated"}
