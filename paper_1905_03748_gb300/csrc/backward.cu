@@ -557,11 +557,27 @@ tigre_status launch_voxel_bp(tigre_geometry* g, const TP* proj, TV* vol, int64_t
         c.z_out0 = z_out0;
         bp_slab_band(c, d, z_first, z_end);
     }
-    // In-core launches read quads where they pay, slab launches the plain band.
-    return z_end < 0 && bp_reads_quads(w) ? run_voxel_bp<TP, TV, true>(g, c, proj, vol, a0, na, w, accumulate, st, sart,
-                                                  lambda, nonneg)
-                     : run_voxel_bp<TP, TV, false>(g, c, proj, vol, a0, na, w, accumulate, st,
-                                                   sart, lambda, nonneg);
+    if (!bp_reads_quads(w))
+        return run_voxel_bp<TP, TV, false>(g, c, proj, vol, a0, na, w, accumulate, st, sart,
+                                           lambda, nonneg);
+    if (z_end < 0)
+        return run_voxel_bp<TP, TV, true>(g, c, proj, vol, a0, na, w, accumulate, st, sart, lambda,
+                                          nonneg);
+    // A slab's band of quads for all angles would take four times the plain
+    // band, so slab launches take their angles a quarter at a time (the
+    // later quarters adding into the slab): the band of one quarter fits in
+    // the bytes of the plain band.
+    if (sart || na < 4)
+        return run_voxel_bp<TP, TV, false>(g, c, proj, vol, a0, na, w, accumulate, st, sart,
+                                           lambda, nonneg);
+    const int64_t chunk = na / 4;
+    for (int64_t c0 = 0; c0 < na; c0 += chunk) {
+        const int64_t cnt = std::min(chunk, na - c0);
+        TIGRE_TRY((run_voxel_bp<TP, TV, true>(g, c, proj + c0 * (int64_t)c.nu * c.nv, vol, a0 + c0,
+                                              cnt, w, c0 > 0 ? 1 : accumulate, st, false, 0.0f,
+                                              0)));
+    }
+    return TIGRE_OK;
 }
 
 
