@@ -20,10 +20,10 @@
 // bilinear coefficients, so the interpolation is three FMAs; 16-bit: its four
 // taps), and a voxel-angle pair costs one aligned 16-byte load (8 bytes for
 // 16-bit storage) instead of four scalar loads and their addresses (the
-// kernel is bound by instruction issue).  Out-of-core slab launches keep the
-// plain buffer: a thin slab's band of rows spans the cone's spread (hundreds
-// of rows at 3072^3), and four copies of it would cost device memory that
-// the slabs need.
+// kernel is bound by instruction issue).  Out-of-core slab launches read a
+// band of rows per slab, which spans the cone's spread (hundreds of rows at
+// 3072^3): they build quads of a quarter of the angles at a time, in the
+// bytes a plain band of all angles takes.
 // Grid order: x-tiles fastest, z-chunks slowest, so resident blocks share one
 // band of detector rows per angle in L2.
 //
@@ -440,9 +440,9 @@ size_t bp_slab_pad_bytes(const tigre_geometry_desc& d, int64_t slab, int64_t na)
     return most;
 }
 
-// Whether an in-core backprojection with weight w reads the quad buffer
-// (both voxel-driven weights do, the SART update included; out-of-core slab
-// launches read the plain band).
+// Whether a backprojection with weight w reads quad projections (both
+// voxel-driven weights do, the in-core SART update included; out-of-core
+// slab launches build them a quarter of the angles at a time).
 static bool bp_reads_quads(tigre_bp_weight w)
 {
     return w == TIGRE_BP_MATCHED || w == TIGRE_BP_FDK;
