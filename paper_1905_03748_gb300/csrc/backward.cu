@@ -104,21 +104,23 @@ template <typename TP> struct ProjTaps<TP, true> {
 // interpolation) and finish with vol += lambda * num / den (den > 1e-12),
 // clamped at zero when nonneg.
 // Shape (512^3 x 360, one launch).  Plain buffer, 16 voxels per thread at 5
-// blocks per SM (48 registers): matched 51.2 ms, FDK 46.5 ms.  Quad buffer,
-// matched: 12 voxels at 6 blocks 44.7 ms (8 at 8: 48.1 with spills; 10 at 7:
-// 45.8; 16 at 5: 61.9; 4 at 8: 53.8); FDK: 16 voxels at 4 blocks 36.0 ms (8 at
-// 8: 39.9; 16 at 5: 49.0).  SART form (twice the accumulators): plain 16 at 3
-// blocks 74.2 ms per SIRT pass over 360 angles and 88.1 per OS-SART sweep of
-// 20-angle subsets; quads with 8 voxels at 6 blocks 65.5 and 66.2 ms.
+// blocks per SM (48 registers): matched 51.2 ms, FDK 46.5 ms.  Quad buffer
+// (bilinear coefficients), matched: 16 voxels at 3 blocks 37.4 ms (16 at 4:
+// 37.9; 12 at 6: 41.2; 12 at 5: 40.7; 10 at 6: 39.7; 14 at 5: 44.3; 1024^3 x
+// 180: 142 at 16 / 3 or 4 against 155 at 12 / 6); FDK: 16 voxels at 3 blocks
+// 34.3 ms (16 at 4: 36.5; 12 at 5: 58.0; 8 at 6: 48.5).  SART form (twice the
+// accumulators): plain 16 at 3 blocks 74.2 ms per SIRT pass over 360 angles
+// and 88.1 per OS-SART sweep of 20-angle subsets; quads with 12 voxels at 4
+// blocks 56.4 and 58.9 ms (8 at 6: 58.0 and 61.0; 16 at 3: 57.6 and 61.7).
 template <int MODE, bool SART, bool QUADP>
 constexpr int bp_blocks_per_sm()
 {
-    return !QUADP ? (SART ? 3 : 5) : SART ? 6 : MODE == TIGRE_BP_FDK ? 4 : 6;
+    return !QUADP ? (SART ? 3 : 5) : SART ? 4 : 3;
 }
 template <int MODE, bool SART, bool QUADP>
 constexpr int bp_voxels_per_thread()
 {
-    return !QUADP ? 16 : SART ? 8 : MODE == TIGRE_BP_FDK ? 16 : 12;
+    return !QUADP ? 16 : SART ? 12 : 16;
 }
 static_assert(bp_voxels_per_thread<TIGRE_BP_FDK, false, false>() <= kBpNZ &&
                   bp_voxels_per_thread<TIGRE_BP_MATCHED, false, true>() <= kBpNZ &&
@@ -415,11 +417,13 @@ static BpConst make_bp_const(const tigre_geometry_desc& d)
 }
 
 // A launch over planes [z_first, z_end) pads only the detector rows those
-// planes reach (its last chunk of kBpNZ planes may run past z_end), with two
-// rows of margin on either side for FP32 rounding.
+// planes reach, with two rows of margin on either side for FP32 rounding.
+// Its last chunk of NZ planes may run past z_end (those voxels are computed,
+// and read rows, but not written): for any NZ <= kBpNZ it ends before
+// z_end + kBpNZ - 1, the bound taken here.
 static void bp_slab_band(BpConst& c, const tigre_geometry_desc& d, int z_first, int z_end)
 {
-    const int64_t z_last = z_first + ((int64_t)(z_end - z_first) + kBpNZ - 1) / kBpNZ * kBpNZ - 1;
+    const int64_t z_last = (int64_t)z_end + kBpNZ - 2;
     double lo, hi;
     if (!detector_row_range(d, (double)z_first, (double)z_last, &lo, &hi)) return;
     const int r_lo = (int)std::floor(lo) - 2;
