@@ -126,6 +126,27 @@ def test_backward_ooc_device_projections(tigre, slab, weight):
     assert rel(out.numpy(), ref.numpy()) < 1e-6
 
 
+@pytest.mark.parametrize("n_ang", [4, 16, 21])
+@pytest.mark.parametrize("slab", [5, 16, 23])
+@pytest.mark.parametrize("weight", ["matched", "fdk"])
+def test_backward_ooc_quad_quarters(tigre, n_ang, slab, weight):
+    """Slab backprojections build quad bands a quarter of the angles at a
+    time (angle counts that fill the band buffer exactly and ones that leave
+    a short last quarter; slab thicknesses that are not multiples of the
+    voxels per thread): the same sums as in-core up to FP32 order."""
+    geo, _, vol = case()
+    ang = np.sort(np.random.default_rng(11).uniform(0, 2 * np.pi, n_ang))
+    y = torch.from_numpy(np.random.default_rng(12).random(
+        (n_ang, geo["n_det"][1], geo["n_det"][0])).astype(np.float32)).cuda()
+    with tigre.Geometry(geo, ang) as G:
+        ref = G.backward(y, weight=weight).cpu()
+        out = torch.zeros(G.vol_shape).pin_memory()
+        tigre.tigre_backward_ooc(G.handle, y, out, 0, n_ang, weight=weight, slab_planes=slab)
+        assert tigre.tigre_geometry_error_flags(G.handle) == 0
+    assert torch.isfinite(out).all()
+    assert rel(out.numpy(), ref.numpy()) < 1e-6
+
+
 @pytest.mark.parametrize("chunk", [1, 4, 19])
 def test_backward_ooc_host_projections_in_chunks(tigre, chunk):
     geo, ang, vol = case()
