@@ -422,7 +422,10 @@ TIGRE_API tigre_status tigre_geometry_set_projector(tigre_geometry_t geo, int pr
  * projections cut
  * each z-slab (0 = default 512).  Rays resident on the GPU at one time then
  * read one brick's planes, which stay in L2; at 3072^2 a single quad plane
- * of the slab is larger than L2.  Only the partial sums' order changes. */
+ * of the slab is larger than L2.  In-core projections on the automatic path
+ * (forward path 0, F32 volume and projections) march the same bricks when
+ * the volume is wider than one brick (1024^3 x 720: 11 % faster).  Only the
+ * partial sums' order changes. */
 TIGRE_API tigre_status tigre_geometry_set_brick(tigre_geometry_t geo, int64_t edge);
 
 /* Kernel choice for this handle's Sec. 2.1 projector (no counterpart in the

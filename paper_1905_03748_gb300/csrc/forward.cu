@@ -772,6 +772,20 @@ static void needed_layouts(const tigre_geometry* g, int64_t a0, int64_t na, bool
     for (int64_t a = a0; a < a0 + na; ++a) need[g->layout[(size_t)a]] = true;
 }
 
+static tigre_status brick_pixel_ranges(tigre_geometry* g, const int2** out);
+
+// Whether an in-core projection marches x-y bricks: the automatic path, F32
+// volume, projector interpolated, and a volume wider than one brick.  Its
+// rays then read one brick's planes at a time, which stay in L2 (1024^3 x
+// 720: 1790 vs 2012 ms of kernels); a 512^2 plane is one brick.
+static bool in_core_bricks(const tigre_geometry* g, tigre_dtype vt)
+{
+    const tigre_geometry_desc& d = g->desc;
+    const int64_t e = g->brick;
+    return g->fwd_path == 0 && vt == TIGRE_F32 && g->projector == TIGRE_PROJ_INTERPOLATED &&
+           e > 0 && (d.n_voxel[0] > e || d.n_voxel[1] > e);
+}
+
 tigre_status forward_workspace(tigre_geometry* g, tigre_dtype vt, int64_t a0, int64_t na,
                                cudaStream_t st)
 {
@@ -791,6 +805,10 @@ tigre_status forward_workspace(tigre_geometry* g, tigre_dtype vt, int64_t a0, in
         return tma_workspace(g, dtype_size(vt), need);
     }
     const bool use_quad = !siddon && (g->fwd_path == 0 || g->fwd_path >= 3);
+    if (in_core_bricks(g, vt)) {  // the bricks' pixel ranges, before any capture
+        const int2* pr = nullptr;
+        TIGRE_TRY(brick_pixel_ranges(g, &pr));
+    }
     DeviceBuffer* bufs[2] = {&g->vol_xy, &g->vol_yx};
     DeviceBuffer* qbufs[2] = {&g->vol_qxy, &g->vol_qyx};
     for (int l = 0; l < 2; ++l) {
@@ -862,6 +880,16 @@ tigre_status forward_impl(tigre_geometry* g, const void* vol, tigre_dtype vt, vo
                 return launch_siddon_forward<TV, TP>(g, (const TV*)g->vol_xy.ptr,
                                                      (const TV*)g->vol_yx.ptr, (TP*)proj, a0, na,
                                                      order, st);
+            if constexpr (std::is_same<TV, float>::value && std::is_same<TP, float>::value) {
+                if (in_core_bricks(g, vt) && pt == TIGRE_F32) {
+                    // the whole volume as one slab, marched brick by brick;
+                    // the bricks' partial sums add into zeroed projections
+                    TIGRE_CUDA(cudaMemsetAsync(proj, 0, sizeof(float) * (size_t)na * c.nu * c.nv, st));
+                    float4* const quads[2] = {(float4*)g->vol_qxy.ptr, (float4*)g->vol_qyx.ptr};
+                    return forward_slab_impl(g, d, quads, (float*)proj, a0, na, -1000000, 1000000,
+                                             0, st);
+                }
+            }
             ProfScope prof(kProfForward, st);
             const int ag = g->fwd_path == 5   ? 2
                            : g->fwd_path == 6 ? 4
