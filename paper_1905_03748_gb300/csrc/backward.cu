@@ -16,11 +16,10 @@
 // volume's shadow can reach beyond the detector for this geometry (bounded
 // on the host), so the per-voxel loop has neither clamps nor branches; u is
 // clamped once per column and angle.  In-core launches use a quad buffer:
-// element (r, c) holds the bilinear cell (c, c+1) x (r, r+1) (F32: its four
-// bilinear coefficients, so the interpolation is three FMAs; 16-bit: its four
-// taps), and a voxel-angle pair costs one aligned 16-byte load (8 bytes for
-// 16-bit storage) instead of four scalar loads and their addresses (the
-// kernel is bound by instruction issue).  Out-of-core slab launches read a
+// element (r, c) holds the four FP32 bilinear coefficients of the cell
+// (c, c+1) x (r, r+1) for every storage type, so a voxel-angle pair costs one
+// aligned 16-byte load and three FMAs instead of four scalar loads, their
+// addresses and three lerps (the kernel is bound by instruction issue).  Out-of-core slab launches read a
 // band of rows per slab, which spans the cone's spread (hundreds of rows at
 // 3072^3): they build quads of a quarter of the angles at a time, in the
 // bytes a plain band of all angles takes.
@@ -73,9 +72,9 @@ __device__ __forceinline__ float rsqrt_sfu(float x)
 
 // The bilinear coefficients (bilinear_coefficients: u along columns, v along
 // rows) of the cell (c, c+1) x (r, r+1) at `cell`, from the plain (QUADP
-// false) or the quad (true) zero-bordered projection buffer.  F32 quads store
-// the coefficients; plain and 16-bit buffers hold taps, whose coefficients are
-// formed after the load in the same FP32 operations.
+// false) or the quad (true) zero-bordered projection buffer.  Quads store the
+// coefficients; the plain buffer holds taps, whose coefficients are formed
+// after the load in the same FP32 operations.
 template <typename TP, bool QUADP> struct ProjTaps;
 template <typename TP> struct ProjTaps<TP, false> {
     using E = TP;
@@ -88,15 +87,7 @@ template <typename TP> struct ProjTaps<TP, false> {
 };
 template <typename TP> struct ProjTaps<TP, true> {
     using E = typename QuadOf<TP>::type;
-    static __device__ __forceinline__ float4 load(const E* cell, int)
-    {
-        if constexpr (sizeof(TP) == 4) {
-            return __ldg(cell);
-        } else {
-            const float4 t = load_quad(cell, (TP*)nullptr);
-            return bilinear_coefficients(t.x, t.y, t.z, t.w);
-        }
-    }
+    static __device__ __forceinline__ float4 load(const E* cell, int) { return load_quad(cell); }
 };
 
 // SART == true: also accumulate the backprojection of the all-ones
@@ -258,9 +249,8 @@ __device__ __forceinline__ TP pix_or_zero(const TP* row, int p, int nu)
 
 // Write the whole zero-bordered buffer of one angle range: with
 // Z(r, c) = y[a][r - pv_lo][c - 2] (zero outside the detector), the plain
-// buffer holds out[a][r][c] = Z(r, c), the quad buffer the cell
-// (Z(r, c), Z(r, c+1), Z(r+1, c), Z(r+1, c+1)): its bilinear coefficients for
-// F32, the taps themselves for 16-bit storage.
+// buffer holds out[a][r][c] = Z(r, c), the quad buffer the FP32 bilinear
+// coefficients of the cell (Z(r, c), Z(r, c+1), Z(r+1, c), Z(r+1, c+1)).
 template <typename TP, bool QUADP>
 __global__ void pad_proj_kernel(const TP* __restrict__ in,
                                 typename ProjTaps<TP, QUADP>::E* __restrict__ out, int nu, int nv,
@@ -282,10 +272,8 @@ __global__ void pad_proj_kernel(const TP* __restrict__ in,
             const TP a01 = in0 ? pix_or_zero(row0, p + 1, nu) : z;
             const TP a10 = in1 ? pix_or_zero(row1, p, nu) : z;
             const TP a11 = in1 ? pix_or_zero(row1, p + 1, nu) : z;
-            if constexpr (sizeof(TP) == 4)
-                dst[col] = bilinear_coefficients(a00, a01, a10, a11);
-            else
-                dst[col] = pack_quad16(a00, a01, a10, a11);
+            dst[col] = bilinear_coefficients(to_f32<TP>(a00), to_f32<TP>(a01), to_f32<TP>(a10),
+                                             to_f32<TP>(a11));
         }
     }
 }
@@ -469,7 +457,7 @@ tigre_status backward_workspace(tigre_geometry* g, tigre_dtype pt, tigre_bp_weig
         return TIGRE_OK;
     }
     const BpConst c = make_bp_const(d);
-    const size_t elem = (bp_reads_quads(w) ? 4 : 1) * dtype_size(pt);
+    const size_t elem = bp_reads_quads(w) ? sizeof(float4) : dtype_size(pt);
     return g->proj_pad.ensure((size_t)na * (size_t)c.PU * (size_t)c.PV * elem);
 }
 
@@ -481,7 +469,8 @@ static tigre_status run_voxel_bp(tigre_geometry* g, const BpConst& c, const TP* 
                                  int batch = 1, void* ws = nullptr)
 {
     using Q = typename ProjTaps<TP, QUADP>::E;
-    static_assert(sizeof(Q) == (QUADP ? 4 : 1) * sizeof(TP), "a quad is four elements");
+    static_assert(sizeof(Q) == (QUADP ? 4 * sizeof(float) : sizeof(TP)),
+                  "a quad is four FP32 coefficients");
     const size_t pelems = (size_t)na * (size_t)c.PU * (size_t)c.PV;
     Q* pp = (Q*)ws;
     if (!pp) {
@@ -588,7 +577,8 @@ tigre_status launch_voxel_bp(tigre_geometry* g, const TP* proj, TV* vol, int64_t
 size_t backward_batch_workspace_bytes(const tigre_geometry* g, tigre_dtype dt)
 {
     const BpConst c = make_bp_const(g->desc);
-    return (size_t)g->angles.size() * (size_t)c.PU * (size_t)c.PV * 4 * dtype_size(dt);
+    (void)dt;  // quads hold FP32 coefficients for every storage type
+    return (size_t)g->angles.size() * (size_t)c.PU * (size_t)c.PV * sizeof(float4);
 }
 
 tigre_status backward_batch_impl(tigre_geometry* g, const void* projs, void* vols, int batch,

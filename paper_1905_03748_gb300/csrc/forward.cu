@@ -292,18 +292,11 @@ __global__ void __launch_bounds__(256) fwd_l1_kernel(const TV* __restrict__ vxy,
 // zero-padded layout P.  A trilinear sample is then two aligned loads (planes
 // s and s+1) instead of eight scalar ones (element types: quad.cuh).
 //
-// F32 elements hold the cell's bilinear coefficients (bilinear_coefficients)
-// instead of its taps, so a plane's bilinear value is three FMAs
-// (bilinear_value).  16-bit elements hold the taps (a coefficient stored in 16
-// bits would be rounded again); their coefficients are formed after the load,
-// in the same FP32 operations, as the scalar kernels form theirs.
-__device__ __forceinline__ float4 load_fquad(const float4* p, float*) { return __ldg(p); }
-template <typename T16>
-__device__ __forceinline__ float4 load_fquad(const uint2* p, T16* t)
-{
-    const float4 v = load_quad(p, t);
-    return bilinear_coefficients(v.x, v.y, v.z, v.w);
-}
+// Elements hold the cell's bilinear coefficients (bilinear_coefficients) in
+// FP32 for every storage type, formed from the taps converted to FP32 in the
+// same operations the scalar kernels use, so a plane's bilinear value is three
+// FMAs (bilinear_value) after one load.
+__device__ __forceinline__ float4 load_fquad(const float4* p) { return load_quad(p); }
 
 // Build the quad volume of one layout straight from the caller's volume (no
 // padded copy): with P(s, m, f) the zero-bordered layout (vol[s-2][m-2][f-2]
@@ -348,10 +341,7 @@ __global__ void __launch_bounds__(256) quad_from_vol_kernel(const T* __restrict_
         const T a = tile[i][threadIdx.x], b = tile[i][threadIdx.x + 1];
         const T c = tile[i + 1][threadIdx.x], d = tile[i + 1][threadIdx.x + 1];
         typename QuadOf<T>::type* o = out + ((int64_t)s * PM + m) * PF + f;
-        if constexpr (sizeof(T) == 4)
-            *o = bilinear_coefficients(a, b, c, d);
-        else
-            *o = pack_quad16(a, b, c, d);
+        *o = bilinear_coefficients(to_f32<T>(a), to_f32<T>(b), to_f32<T>(c), to_f32<T>(d));
     }
 }
 
@@ -389,8 +379,8 @@ __device__ __forceinline__ float tri_sample_quad(const typename QuadOf<TV>::type
     split_bits(fmaf(kf, R.d[2], R.x0[2]), b_s, as);
     const uint32_t e = b_s * (uint32_t)PFM + b_m * (uint32_t)PF + b_f - bias;
     const typename QuadOf<TV>::type* b = qv + e;
-    const float c0 = bilinear_value(load_fquad(b, (TV*)nullptr), af, am);        // plane s
-    const float c1 = bilinear_value(load_fquad(b + PFM, (TV*)nullptr), af, am);  // plane s+1
+    const float c0 = bilinear_value(load_fquad(b), af, am);        // plane s
+    const float c1 = bilinear_value(load_fquad(b + PFM), af, am);  // plane s+1
     return fmaf(as, c1 - c0, c0);
 }
 
@@ -416,10 +406,10 @@ __device__ __forceinline__ void tri_pair_quad(const typename QuadOf<TV>::type* _
     split_bits(fmaf(kf1, R.d[2], R.x0[2]), z1, as1);
     const Q* b0 = t0 ? qv + (z0 * (uint32_t)PFM + m0 * (uint32_t)PF + f0 - bias) : qv;
     const Q* b1 = t1 ? qv + (z1 * (uint32_t)PFM + m1 * (uint32_t)PF + f1 - bias) : qv;
-    const float4 lo0 = load_fquad(b0, (TV*)nullptr);
-    const float4 hi0 = load_fquad(b0 + PFM, (TV*)nullptr);
-    const float4 lo1 = load_fquad(b1, (TV*)nullptr);
-    const float4 hi1 = load_fquad(b1 + PFM, (TV*)nullptr);
+    const float4 lo0 = load_fquad(b0);
+    const float4 hi0 = load_fquad(b0 + PFM);
+    const float4 lo1 = load_fquad(b1);
+    const float4 hi1 = load_fquad(b1 + PFM);
     {
         const float c0 = bilinear_value(lo0, af0, am0), c1 = bilinear_value(hi0, af0, am0);
         if (t0) acc += fmaf(as0, c1 - c0, c0);
@@ -816,7 +806,7 @@ tigre_status forward_workspace(tigre_geometry* g, tigre_dtype vt, int64_t a0, in
         // the quad paths build their quads from the volume itself; the
         // scalar and Siddon paths read the zero-bordered layouts
         if (use_quad)
-            TIGRE_TRY(qbufs[l]->ensure(padded_elems(d) * 4 * dtype_size(vt)));  // 4 elements
+            TIGRE_TRY(qbufs[l]->ensure(padded_elems(d) * sizeof(float4)));  // 4 FP32 coefficients
         else
             TIGRE_TRY(ensure_padded(*bufs[l], d, dtype_size(vt), l, st));
     }
@@ -866,7 +856,7 @@ tigre_status forward_impl(tigre_geometry* g, const void* vol, tigre_dtype vt, vo
         using Q = typename QuadOf<TV>::type;
         DeviceBuffer* bufs[2] = {&g->vol_xy, &g->vol_yx};
         DeviceBuffer* qbufs[2] = {&g->vol_qxy, &g->vol_qyx};
-        static_assert(sizeof(Q) == 4 * sizeof(TV), "a quad is four elements");
+        static_assert(sizeof(Q) == 4 * sizeof(float), "a quad is four FP32 coefficients");
         for (int l = 0; l < 2; ++l) {
             if (!need[l]) continue;
             if (use_quad)

@@ -736,7 +736,7 @@ tigre_status batch_init(Batch* S, int hist_cap, bool x0_zero)
     bool need[2] = {false, false};
     for (int l : S->g->layout) need[l] = true;
     for (int l = 0; l < 2; ++l)
-        if (need[l]) TIGRE_TRY(dalloc((unsigned char**)&S->quad[l], B * (size_t)S->pe * 4 * e, S->st));
+        if (need[l]) TIGRE_TRY(dalloc((unsigned char**)&S->quad[l], B * (size_t)S->pe * sizeof(float4), S->st));
     TIGRE_TRY(dalloc((unsigned char**)&S->bpws, B * backward_batch_workspace_bytes(S->g, S->dt),
                      S->st));
     TIGRE_TRY(dalloc(&S->sc, B * batch_scalar_count(), S->st));

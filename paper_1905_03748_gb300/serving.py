@@ -55,20 +55,20 @@ class Result:
 
 
 def footprint_bytes(geo: dict, n_angles: int, elem: int = 4) -> int:
-    """HBM one member of a batched CGLS keeps resident, in elem-byte values:
-    x, p, s (volume-sized), b, r, q (projection-sized), the forward
-    projector's quad copies of the two zero-bordered layouts (4 padded
-    volumes each), the backprojector's quad copy of the zero-bordered projections
-    (4 values per pixel; two border columns a side, and the rows the volume's
-    shadow reaches beyond the detector, taken as 10 % + 8), plus 64 MiB of
-    slack."""
+    """HBM one member of a batched CGLS keeps resident: x, p, s
+    (volume-sized) and b, r, q (projection-sized) in elem-byte values; the
+    forward projector's quads of the two zero-bordered layouts and the
+    backprojector's quads of the zero-bordered projections (two border
+    columns a side, and the rows the volume's shadow reaches beyond the
+    detector, taken as 10 % + 8), four FP32 coefficients (16 bytes) per
+    padded voxel or pixel whatever elem is; plus 64 MiB of slack."""
     nx, ny, nz = geo["n_voxel"]
     nu, nv = geo["n_det"]
     vol = elem * nx * ny * nz
-    padded = elem * (nx + 4) * (ny + 4) * (nz + 4)
+    vol_quads = 2 * 16 * (nx + 4) * (ny + 4) * (nz + 4)
     proj = elem * nu * nv * n_angles
-    proj_quads = 4 * elem * n_angles * (nu + 4) * (nv + nv // 10 + 8)
-    return 3 * vol + 3 * proj + proj_quads + 8 * padded + (64 << 20)
+    proj_quads = 16 * n_angles * (nu + 4) * (nv + nv // 10 + 8)
+    return 3 * vol + 3 * proj + proj_quads + vol_quads + (64 << 20)
 
 
 _STORAGE = (torch.float32, torch.bfloat16, torch.float16)

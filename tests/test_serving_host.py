@@ -22,12 +22,13 @@ def request(serving, rid, n, na=30, dtype=torch.float32, arrival=0.0, n_iter=15)
 
 def test_footprint_counts_six_vectors_layouts_and_slack(serving):
     geo, ang = synth.workload("small_64")
-    # x, p, s: 3 x 64^3; b, r, q: 3 x 100 x 128^2; the backprojector's quad
-    # projections: 4 x 100 x (128 + 4) x (128 + 12 + 8); quad copies of the
-    # two zero-bordered layouts: 8 x 68^3; 64 MiB slack
-    want = 4 * (3 * 64 ** 3 + 3 * 100 * 128 ** 2 + 4 * 100 * 132 * 148 + 8 * 68 ** 3) + (64 << 20)
-    assert serving.footprint_bytes(geo, len(ang)) == want
-    assert serving.footprint_bytes(geo, len(ang), 2) == want // 2 + (32 << 20)
+    # x, p, s: 3 x 64^3 and b, r, q: 3 x 100 x 128^2 values of the storage
+    # type; 16-byte quads: the backprojector's 100 x (128 + 4) x (128 + 12 + 8)
+    # and the two zero-bordered layouts' 2 x 68^3; 64 MiB slack
+    vectors = 3 * 64 ** 3 + 3 * 100 * 128 ** 2
+    quads = 16 * (100 * 132 * 148 + 2 * 68 ** 3)
+    assert serving.footprint_bytes(geo, len(ang)) == 4 * vectors + quads + (64 << 20)
+    assert serving.footprint_bytes(geo, len(ang), 2) == 2 * vectors + quads + (64 << 20)
 
 
 def test_storage_type_follows_the_projections(serving):
