@@ -14,7 +14,7 @@ K = ceil(len / step).  Frame: source DSO (cos t, sin t, 0), detector centre
 -(DSD - DSO) (cos t, sin t, 0), e_u = (-sin t, cos t, 0), e_v = (0, 0, 1); the
 layout of an angle is y-fastest when |cos t| > |sin t|.
 
-    python -m paper_1905_03748_gb300.march_replay --workload cgls_512 --warps 400
+    python -m paper_1905_03748_gb300.march_replay --workload cgls_512 --warps 400 [--variants]
 """
 import argparse
 import json
@@ -70,9 +70,16 @@ def rays(geo: dict, t: float, pixels: np.ndarray, row: int):
 
 
 def replay(geo: dict, angles: np.ndarray, ag: int = 2, order: str = "interleaved",
-           n_warps: int = 400, seed: int = 0) -> dict:
+           n_warps: int = 400, seed: int = 0, tile=(8, 1), march: str = "slabs") -> dict:
     """Replay n_warps random warps; lines per load request, whole warp and
-    summed over 16-lane halves, and lanes taking a sample per request."""
+    summed over 16-lane halves, and lanes taking a sample per request.
+
+    tile = (tf, tm): a 128-byte line holds tf x tm quads of a plane ((8, 1):
+    the row-major layout; (4, 2), (2, 4): tiled alternatives).  march =
+    "slabs" (the kernel's slabs of width D from the first sample) or "rows"
+    (slabs aligned to the depth axis's unit rows, every lane taking its
+    samples in the row one request at a time, so a request's lanes share a
+    row)."""
     rng = np.random.default_rng(seed)
     nx, ny, _ = geo["n_voxel"]
     nu, nv = geo["n_det"]
@@ -108,20 +115,38 @@ def replay(geo: dict, angles: np.ndarray, ag: int = 2, order: str = "interleaved
         Y0 = y0[act].min()
         Y1 = (y0 + (K - 1) * dy)[act].max()
         k = np.zeros(len(K), int)
-        for j in range(1, int((Y1 - Y0) / D) + 2):
-            take = act & (k < K) & (y0 + k * dy < Y0 + j * D)
-            if not take.any():
-                continue
+        tf, tm = tile
+
+        def request(take):
+            nonlocal requests, lanes, warp_lines, half_lines
             cell = np.floor(x0[take] + k[take][:, None] * dx[take]).astype(np.int64)
-            addr = ((cell[:, 2] * pm + cell[:, 1]) * pf + cell[:, 0]) * QUAD
-            ln = addr // LINE
+            if (tf, tm) == (8, 1):
+                ln = ((cell[:, 2] * pm + cell[:, 1]) * pf + cell[:, 0]) * QUAD // LINE
+            else:  # lines of tf x tm quads
+                ptf, ptm = (pf + tf - 1) // tf, (pm + tm - 1) // tm
+                ln = (cell[:, 2] * ptm + cell[:, 1] // tm) * ptf + cell[:, 0] // tf
             half = lane[take] // 16
             requests += 1
             lanes += int(take.sum())
             warp_lines += len(np.unique(ln))
             half_lines += sum(len(np.unique(ln[half == h])) for h in np.unique(half))
             k[take] += 1
-    return {"ag": ag, "order": order, "requests": requests,
+
+        if march == "slabs":
+            for j in range(1, int((Y1 - Y0) / D) + 2):
+                take = act & (k < K) & (y0 + k * dy < Y0 + j * D)
+                if take.any():
+                    request(take)
+        else:
+            bound = np.floor(Y0)
+            while bound <= Y1:
+                bound += 1.0
+                while True:
+                    take = act & (k < K) & (y0 + k * dy < bound)
+                    if not take.any():
+                        break
+                    request(take)
+    return {"ag": ag, "order": order, "tile": list(tile), "march": march, "requests": requests,
             "lines_per_request": warp_lines / max(requests, 1),
             "halfwarp_lines_per_request": half_lines / max(requests, 1),
             "lanes_per_request": lanes / max(requests, 1)}
@@ -134,10 +159,16 @@ def main():
     ap.add_argument("--workload", default="cgls_512")
     ap.add_argument("--warps", type=int, default=400)
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--variants", action="store_true",
+                    help="also tiled quad lines and row-aligned marching")
     a = ap.parse_args()
     geo, ang = synth.workload(a.workload)
     for ag, order in ((1, "blocked"), (2, "blocked"), (2, "interleaved")):
         print(json.dumps(replay(geo, ang, ag, order, a.warps, a.seed)))
+    if a.variants:
+        for tile in ((4, 2), (2, 4)):
+            print(json.dumps(replay(geo, ang, 2, "interleaved", a.warps, a.seed, tile=tile)))
+        print(json.dumps(replay(geo, ang, 2, "interleaved", a.warps, a.seed, march="rows")))
 
 
 if __name__ == "__main__":
