@@ -326,8 +326,8 @@ TIGRE_API tigre_status tigre_cgls_end(tigre_cgls_t state);
  *        interpolated projector and the automatic forward path; bp_weight
  *        MATCHED or FDK.  Workspaces (owned by the batch, stream-ordered on
  *        opts->cuda_stream): per member 4 iterate vectors, a quad copy of the
- *        zero-bordered volume per layout (4 values per voxel), and a quad copy of the padded
- *        projections.  Otherwise as tigre_cgls_begin; TIGRE_ERR_UNSUPPORTED for
+ *        zero-bordered volume per layout and one of the padded projections
+ *        (16 bytes of FP32 coefficients per padded voxel or pixel).  Otherwise as tigre_cgls_begin; TIGRE_ERR_UNSUPPORTED for
  *        other flags, projectors or weights.
  * iterate: enqueues n_iter iterations of every member (no host sync).
  * history: the first n residual norms of member member_index (synchronises).
@@ -435,8 +435,9 @@ TIGRE_API tigre_status tigre_geometry_set_brick(tigre_geometry_t geo, int64_t ed
  * L1 gather kernel, 2 = shared-memory slab kernel (TMA-staged; only for
  * geometries whose ray bundles fit its staging box, otherwise it reports
  * error bit 2 and NaN), 3 = quad gather kernel (two 16-byte loads per sample
- * from a layout holding a cell plane's four taps, as bilinear coefficients for
- * F32; four times the volume in workspace), 4 = quad gather kernel taking a
+ * from a layout holding each cell plane's four bilinear coefficients in FP32,
+ * whatever the volume's storage type; 16 bytes per padded voxel and memory
+ * layout in workspace), 4 = quad gather kernel taking a
  * ray's samples two at a time (both samples' loads issued together), 5 / 6 =
  * quad gather kernel whose warps hold 16 pixels x 2 / 8 pixels x 4 angles
  * (neighbouring angles of one memory layout and march direction, so a warp's
